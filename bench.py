@@ -1,0 +1,436 @@
+#!/usr/bin/env python
+"""Throughput of one mapping iteration of pixel-aligned Gaussian splatting on GB300.
+
+Workload: 8 keyframes at 640x480 (2,457,600 Gaussians, one per pixel) in a seeded
+synthetic box room, splatted into 8 neighbouring views (<= 5 cm / <= 2 degrees from the
+keyframes, fx = fy = 600). One step is the whole hot path: forward splatting
+(projection, binning, key emission, per-tile sort, compositing), the L1 colour +
+0.1 L1 depth loss gradient, the adjoint (reverse compositing and the chain rule into
+offset, colour, opacity logit and scale) and an Adam step on all four parameter
+groups. Metric: Mpix/s = rendered view pixels per second (8 x 640 x 480 per step).
+
+Timing: W warm-up steps, then K steps timed with CUDA events on the launching stream,
+bracketed by a barrier and a device synchronise, L2 flushed (256 MB write) before every
+step and excluded from the timed events; max over ranks. With --gpus N > 1 (torchrun),
+every rank maps its own independent keyframe window (weak scaling, no collective on
+the data path).
+
+`--impl reference` times the FP64 CPU oracle (the correctness reference; there is no
+reference implementation of the paper's code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd splat Mpix/s at 640x480x8 views; mapping secs to PSNR 30 dB vs plain"
+UNIT = "Mpix/s"
+WORKLOAD = "room8x640x480: 8 keyframes x 640x480 (2,457,600 Gaussians) -> 8 views 640x480, fx=600"
+LR = dict(offset=0.01, rgb=0.0025, logit=0.05, scale=0.005)   # Supp. A learning rates
+# Algorithmic work per contributing (pixel, entry) pair, counted from the formulas:
+# forward 29 FP32 flops + 1 exp; backward 73 flops + 1 exp + 1 reciprocal.
+FLOPS_FWD_PAIR = 30.0
+FLOPS_BWD_PAIR = 75.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--json-out", default="")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(",") for r in self.file.read().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def file_hash(*paths):
+    h = hashlib.sha1()
+    for p in paths:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None when the
+    summary is absent or the kernel's source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = [os.path.join(ROOT, "paper_2603_21055_gb300", "csrc", s) for s in e["sources"]]
+    if file_hash(*src) != e["source_hash"]:
+        return None
+    return e
+
+
+# ----------------------------------------------------------------------- our arm
+
+class Mapper:
+    """Device state of one mapping iteration over a keyframe window."""
+
+    def __init__(self, scene):
+        import torch
+        from paper_2603_21055_gb300 import splat
+        self.torch = torch
+        self.scene = scene
+        self.views = scene.views
+        self.sp = splat.Splatter()
+        self.kfs = splat.upload_keyframes(scene)
+        self.trgb, self.tdep = splat.upload_targets(scene)
+        self.images = splat.alloc_images(self.views)
+        self.d_rgb = [torch.empty_like(im["rgb"]) for im in self.images]
+        self.d_dep = [torch.empty_like(im["depth"]) for im in self.images]
+        self.loss = torch.zeros(1, device="cuda")
+        self.valid = torch.zeros(len(self.views), dtype=torch.int32, device="cuda")
+        self.grads = [dict(d_offset=torch.empty_like(k.offset), d_rgb=torch.empty_like(k.rgb),
+                           d_logit=torch.empty_like(k.logit), d_scale=torch.empty_like(k.scale)) for k in self.kfs]
+        self.moments = [{n: (torch.zeros_like(getattr(k, n)), torch.zeros_like(getattr(k, n)))
+                         for n in ("offset", "rgb", "logit", "scale")} for k in self.kfs]
+        self.t = 0
+        self.n_keys = self.sp.plan(self.kfs, self.views, slack=1.3)
+
+    def step(self):
+        from paper_2603_21055_gb300 import binding as B
+        sp = self.sp
+        sp.forward(self.kfs, self.views, self.images)
+        self.loss.zero_()
+        sp.l1_loss_grad(self.views, self.images, self.trgb, self.tdep, self.scene.rgb_weight,
+                        self.scene.depth_weight, self.d_rgb, self.d_dep, self.loss, self.valid)
+        gin = [dict(rgb=r, depth=d) for r, d in zip(self.d_rgb, self.d_dep)]
+        sp.backward(self.kfs, self.views, gin, self.grads)
+        self.t += 1
+        st = sp.stream()
+        for k, g, mo in zip(self.kfs, self.grads, self.moments):
+            for n, gn in (("offset", "d_offset"), ("rgb", "d_rgb"), ("logit", "d_logit"), ("scale", "d_scale")):
+                p = getattr(k, n)
+                m, v = mo[n]
+                B.sgad_adam_step(p.numel(), p.data_ptr(), g[gn].data_ptr(), m.data_ptr(), v.data_ptr(), LR[n],
+                                 0.9, 0.999, 1e-15, self.t, st)
+
+    def launches_per_step(self):
+        # forward: project_count, scan, emit, sort, composite_fwd; loss: 2 per view;
+        # backward: composite_bwd, finalize; Adam: 4 per keyframe
+        return 5 + 2 * len(self.views) + 2 + 4 * len(self.kfs)
+
+    def ensure_capacity(self):
+        s, nk, need = self.sp.check()
+        if s != 0:
+            self.sp.reserve(self.kfs, self.views, int(need * 1.3) + 4096)
+            return False
+        return True
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2603_21055_gb300 import synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    scene = synth.config2_room(seed=args.seed + rank)
+    mp = Mapper(scene)
+    n_pix = scene.n_pixels
+    for _ in range(args.warmup):
+        mp.step()
+    torch.cuda.synchronize()
+    if not mp.ensure_capacity():
+        for _ in range(2):
+            mp.step()
+        torch.cuda.synchronize()
+        assert mp.ensure_capacity(), "key capacity could not be met"
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")    # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        mp.step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ok = mp.ensure_capacity()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = n_pix * world * args.steps / (total_ms / 1e3) / 1e6
+
+    # per-stage times (separate, profiled pass) and work counters
+    mp.sp.profile(True)
+    stages = {}
+    nprof = min(args.steps, 8)
+    for _ in range(nprof):
+        flush.zero_()
+        mp.step()
+        for k, v in mp.sp.stage_ms().items():
+            stages[k] = stages.get(k, 0.0) + v / nprof
+    mp.sp.profile(False)
+    stats = mp.sp.stats()
+
+    # end to end through the public API: pinned host inputs in, updated parameters out
+    e2e = run_e2e(mp, min(args.steps, 10), stream, flush)
+
+    peaks, peak_src = measured_peaks()
+    roof = roofline(stages, stats, scene, peaks, peak_src)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pixels_per_step": n_pix, "gaussians": scene.n_gaussians,
+                   "keys": stats["n_keys"], "contributing_pairs": stats["n_pairs"],
+                   "evaluated_pairs": stats["n_evals"], "tile": "16x16",
+                   "step": "forward + L1 loss grad + backward + Adam (all four parameter groups)",
+                   "l2": "flushed (256 MB write) before every step, outside the timed events",
+                   "parallelism": "independent keyframe window per GPU" if world > 1 else "1 GPU",
+                   "capacity_ok": ok},
+        "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": mp.launches_per_step() * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene)
+    if rank == 0:
+        out = json.dumps(line)
+        print(out, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(out + "\n")
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(mp, steps, stream, flush):
+    """Same metric through the public API with host buffers: each step copies the keyframe
+    parameter planes and the targets from pinned host memory, runs the iteration, and
+    reads the updated parameters and the loss back."""
+    import torch
+    host_in, dev_in = [], []
+    for k in mp.kfs:
+        for n in ("depth", "offset", "rgb", "logit", "scale"):
+            t = getattr(k, n)
+            host_in.append(t.detach().cpu().pin_memory())
+            dev_in.append(t)
+    for t in mp.trgb + mp.tdep:
+        host_in.append(t.detach().cpu().pin_memory())
+        dev_in.append(t)
+    dev_out = [getattr(k, n) for k in mp.kfs for n in ("offset", "rgb", "logit", "scale")] + [mp.loss]
+    host_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in dev_out]
+    bi = sum(t.numel() * t.element_size() for t in host_in)
+    bo = sum(t.numel() * t.element_size() for t in host_out)
+    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        s_ev[i].record(stream)
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        mp.step()
+        for d, h in zip(dev_out, host_out):
+            h.copy_(d, non_blocking=True)
+        e_ev[i].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(s.elapsed_time(e) for s, e in zip(s_ev, e_ev)) / steps
+    return {"value": round(mp.scene.n_pixels / (ms / 1e3) / 1e6, 2), "unit": UNIT,
+            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": round(ms, 4)}
+
+
+def roofline(stages, stats, scene, peaks, src):
+    """Roofline of the dominant kernel. The compositing kernels are bound by FP32
+    arithmetic (peak = SMs x 128 FP32 lanes x 2 flop x max SM clock); the rest by HBM."""
+    if not stages:
+        return None
+    name = max(stages, key=stages.get)
+    ms = stages[name]
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    ng, nk = scene.n_gaussians, stats["n_keys"]
+    kernel_of = {"composite_bwd": "k_composite_bwd", "composite_fwd": "k_composite_fwd", "sort": "k_sort_tiles",
+                 "emit": "k_emit", "binning": "k_project_count", "finalize": "k_finalize"}
+    if name in ("composite_fwd", "composite_bwd"):
+        per = FLOPS_FWD_PAIR if name == "composite_fwd" else FLOPS_BWD_PAIR
+        work = stats["n_pairs"] * per
+        achieved = work / (ms / 1e3) / 1e12
+        bound, unit, peak = "alu", "TFLOP/s", fp32_tflops
+        peak_note = "FP32 CUDA-core peak derived: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz
+    else:
+        # algorithmic bytes of the HBM-bound stages
+        byts = {"sort": nk * 16, "emit": ng * 40 + nk * 8, "binning": ng * 60,
+                "finalize": ng * (32 + 12 + 24)}[name]
+        work = byts
+        achieved = byts / (ms / 1e3) / 1e9
+        bound, unit, peak = "hbm", "GB/s", float(peaks["hbm_gbs"])
+        peak_note = "HBM copy bandwidth (%s)" % src
+    tr = ncu_traffic(kernel_of[name])
+    return {"kernel": kernel_of[name], "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2),
+            "unit": unit, "frac": round(achieved / peak, 4), "peak_source": peak_note,
+            "traffic": (tr["dram_bytes_per_launch"] if tr else None), "avg_ms": round(ms, 4)}
+
+
+def cpu_baseline(scene):
+    """The FP64 oracle, as it stands, on one full 640x480 view of the same window (all
+    8 keyframes): forward + L1 loss gradient + adjoint."""
+    import oracle
+    from paper_2603_21055_gb300 import synth
+    sub = synth.Scene(scene.keyframes, scene.views[:1], scene.target_rgb[:1], scene.target_depth[:1],
+                      scene.depth_weight)
+    t0 = time.perf_counter()
+    ref = oracle.render(sub)
+    _, g = oracle.l1_loss(sub, ref)
+    oracle.backward(sub, g)
+    dt = time.perf_counter() - t0
+    return {"value": round(sub.n_pixels / dt / 1e6, 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "1 of the 8 views (640x480, all 8 keyframes): FP64 forward + L1 grad + adjoint, %.1f s" % dt}
+
+
+# ----------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 CPU oracle timed on the machine's host cores, one bounded sample per step
+    (a 320x240 window of one view with all 8 keyframes, cycling through the views)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2603_21055_gb300 import synth
+    scene = synth.config2_room(seed=args.seed)
+
+    def sample(i):
+        return synth.crop_scene(scene, (0, 0, 640, 480), (160, 120, 320, 240), n_views=len(scene.views)), i % 8
+
+    def one(i):
+        sc, v = sample(i)
+        sub = synth.Scene(sc.keyframes, [sc.views[v]], [sc.target_rgb[v]], [sc.target_depth[v]], sc.depth_weight)
+        ref = oracle.render(sub)
+        _, g = oracle.l1_loss(sub, ref)
+        oracle.backward(sub, g)
+        return sub.n_pixels
+
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    px = 0
+    for i in range(args.steps):
+        px += one(i)
+    dt = time.perf_counter() - t0
+    value = px / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "320x240 window of one view per step, all 8 keyframes"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "320x240 window of one view per step (all 8 keyframes), FP64 forward + "
+                                       "L1 grad + adjoint"},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * sgad.h - C ABI of the GB300 (sm_103a) splatting library for pixel-aligned Gaussians
+ * at adjusted depth (SGAD-SLAM mapping, CVPR 2026).
+ *
+ * The library renders keyframes of pixel-aligned Gaussians into camera views and
+ * back-propagates image-space gradients into the Gaussians' parameters:
+ *
+ *   Sec. 3.1  each Gaussian carries a colour (3), one isotropic variance ("radius"), an
+ *             opacity and a depth offset delta;
+ *   Sec. 3.2  Gaussian j of keyframe i lies on the ray of pixel j at the adjusted depth
+ *             |D_i(j) + delta_i(j)|, and (V'_k, D'_k) = splat(G_i, p_k) renders colour
+ *             and depth into view k; Eq. 1 fits them to the observations, with only the
+ *             current keyframe learnable (neighbours fixed);
+ *   Supp. A   radius initialised to D/F; Adam learning rates per attribute.
+ *
+ * The splatting itself follows the 3DGS conventions the paper builds on (the paper
+ * prints no formulas): EWA projection of the isotropic 3D Gaussian with a 0.3 px
+ * dilation, square bounds of ceil(3 sqrt(lambda_max)) px, tiles of tile_w x tile_h
+ * pixels, per-tile lists sorted front to back by (view-space depth rounded to f32,
+ * global Gaussian index), alpha = min(0.99, sigmoid(logit) e^power), entries with
+ * alpha < 1/255 skipped, the walk stopped before transmittance drops below 1e-4. Pixel
+ * (u, v) has its centre at integer coordinates; the ray through it is
+ * ((u - cx)/fx, (v - cy)/fy, 1); depth maps hold z-depth; Gaussians with view depth
+ * <= 0.2 are culled. Depth is composited without normalisation: D' = sum_i w_i z_i.
+ *
+ * Conventions of this ABI
+ *   - Every buffer argument is a DEVICE pointer owned by the caller unless stated. The
+ *     library allocates no device memory: the caller passes one workspace buffer sized
+ *     by sgad_workspace_size().
+ *   - Float data is FP32. Images and per-keyframe planes are row-major [H][W]; colour is
+ *     planar [3][H][W].
+ *   - Poses are row-major 3x4 [R | t]: keyframes cam->world, views world->cam.
+ *   - Global Gaussian index: keyframe-major (keyframe 0's pixels first), then the pixel
+ *     index y * W + x inside the keyframe.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as void*, NULL =
+ *     the legacy default stream) and never synchronise, except where stated
+ *     (sgad_count_keys, sgad_check).
+ *   - Inputs are validated on the host; a bad argument returns SGAD_ERR_INVALID_ARG and
+ *     launches nothing. Failures found on the device (more keys than the workspace holds,
+ *     a bounded wait that gave up) are recorded in the workspace and reported by
+ *     sgad_check(). No call traps or aborts; sgad_last_error() gives a message for the
+ *     last failing call on the calling thread.
+ */
+#ifndef SGAD_H
+#define SGAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sgad_status;
+
+#define SGAD_OK 0
+#define SGAD_ERR_INVALID_ARG (-1)          /* a host-side argument check failed */
+#define SGAD_ERR_CUDA (-2)                 /* a CUDA runtime call or launch failed */
+#define SGAD_ERR_WORKSPACE_TOO_SMALL (-3)  /* ws_bytes below sgad_workspace_size() */
+#define SGAD_ERR_KEY_OVERFLOW (-4)         /* device: more (tile, Gaussian) keys than key_capacity */
+#define SGAD_ERR_TIMEOUT (-5)              /* device: a bounded wait gave up */
+#define SGAD_ERR_UNSUPPORTED (-6)          /* option combination not supported */
+#define SGAD_ERR_NO_FORWARD (-7)           /* backward on a workspace without a forward */
+
+#define SGAD_MAX_KEYFRAMES 32
+#define SGAD_MAX_VIEWS 64
+
+/* Pinhole camera. pose: row-major 3x4 [R | t]. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float pose[12];
+} sgad_camera;
+
+/* One keyframe's Gaussians, one per pixel (Sec. 3.1, 3.2). All planes [H][W] device
+ * FP32 (rgb [3][H][W]); cam.pose is cam->world. learnable = 0 marks a fixed neighbour
+ * keyframe (Sec. 3.2: only the current frame's Gaussians are optimised): it is rendered
+ * but receives no gradient. */
+typedef struct {
+    const float *depth;          /* D: observed z-depth */
+    const float *offset;         /* delta: learnable depth offset */
+    const float *rgb;            /* colour, planar */
+    const float *opacity_logit;  /* opacity = sigmoid(logit) */
+    const float *scale;          /* s: isotropic standard deviation in metres */
+    sgad_camera cam;
+    int32_t learnable;
+} sgad_keyframe;
+
+/* Rendered images of one view (device, caller-owned, fully overwritten). */
+typedef struct {
+    float *rgb;                  /* [3][H][W] V' */
+    float *depth;                /* [H][W] D' = sum_i w_i z_i */
+    float *alpha;                /* [H][W] A = sum_i w_i */
+} sgad_images;
+
+/* d loss / d (rgb, depth, alpha) of one view (device). A NULL plane means zero. */
+typedef struct {
+    const float *d_rgb;
+    const float *d_depth;
+    const float *d_alpha;
+} sgad_image_grads;
+
+/* Gradients of one keyframe's parameters (device, caller-owned). For learnable
+ * keyframes every element is overwritten; fixed keyframes' pointers may be NULL and
+ * are never touched. */
+typedef struct {
+    float *d_offset;
+    float *d_rgb;                /* [3][H][W] */
+    float *d_opacity_logit;
+    float *d_scale;
+} sgad_keyframe_grads;
+
+/* Options fixed at sgad_create(). */
+typedef struct {
+    int32_t tile_w, tile_h;      /* 16x16 (default), 8x32 or 32x8 */
+    float bg[3];                 /* background colour (default black) */
+    int32_t sort_smem_cap;       /* tiles with more entries than this are sorted through
+                                    global memory; 0 = default (6144); >= 64 */
+    int32_t freeze_offset;       /* 1: delta is held fixed (Table 9 "Mode3"): d_offset is
+                                    written as zeros */
+    int32_t reserved[4];         /* must be zero */
+} sgad_options;
+
+typedef struct sgad_ctx sgad_ctx;
+
+/* Fill *opt with the defaults above. */
+sgad_status sgad_default_options(sgad_options *opt);
+
+/* Create a context (host memory only). opt == NULL selects the defaults. */
+sgad_status sgad_create(sgad_ctx **out, const sgad_options *opt);
+void sgad_destroy(sgad_ctx *ctx);
+
+/* Message describing the last failing call on this thread ("" if none). */
+const char *sgad_last_error(void);
+
+/* Bytes of workspace needed for a problem of this shape holding up to key_capacity
+ * (tile, Gaussian) keys. Host arithmetic only. The workspace holds the per-Gaussian
+ * world records and gradient accumulators (64 B per Gaussian), per-tile offsets, the
+ * per-pixel state kept for the backward pass (8 B per view pixel), and two key arrays
+ * (16 B per key). */
+sgad_status sgad_workspace_size(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
+                                const sgad_camera *views, int32_t n_views, int64_t key_capacity,
+                                size_t *bytes);
+
+/* Exact number of (tile, Gaussian) keys the forward pass will emit for these inputs.
+ * Runs the projection and binning on `stream`, then SYNCHRONISES the stream. The
+ * workspace must be at least sgad_workspace_size(..., key_capacity = 0). Not capturable
+ * in a CUDA graph. */
+sgad_status sgad_count_keys(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
+                            const sgad_camera *views, int32_t n_views, void *workspace,
+                            size_t ws_bytes, int64_t *n_keys, void *stream);
+
+/* Forward splatting (Sec. 3.2, splat(G, p_k)) of all keyframes into all views:
+ * projection and tile binning of every (Gaussian, view) pair, a per-tile sort by
+ * (depth, index), and front-to-back compositing of colour, depth and alpha.
+ * out[k] receives view k. The per-pixel final transmittance and contributor count and
+ * the sorted tile lists are kept in the workspace for sgad_backward(). If the keys do
+ * not fit in key_capacity the outputs are left untouched and sgad_check() reports
+ * SGAD_ERR_KEY_OVERFLOW together with the count needed. */
+sgad_status sgad_forward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
+                         const sgad_camera *views, int32_t n_views, sgad_images *out,
+                         void *workspace, size_t ws_bytes, int64_t key_capacity, void *stream);
+
+/* Adjoint of the last sgad_forward() on this workspace (same kfs, views and options):
+ * walks every pixel's list back to front, recomputing transmittance by division from
+ * the saved final value, and accumulates d loss / d (offset, colour, opacity logit,
+ * scale) of every learnable keyframe, summed over views. */
+sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
+                          const sgad_camera *views, int32_t n_views,
+                          const sgad_image_grads *grad_in, sgad_keyframe_grads *grads_out,
+                          void *workspace, size_t ws_bytes, int64_t key_capacity, void *stream);
+
+/* Synchronise `stream`, then read the device-side status of the workspace: SGAD_OK,
+ * SGAD_ERR_KEY_OVERFLOW (with *keys_needed set to the count the last forward needed) or
+ * SGAD_ERR_TIMEOUT. Clears the recorded error. keys_needed and n_keys may be NULL;
+ * *n_keys receives the key count of the last forward. */
+sgad_status sgad_check(sgad_ctx *ctx, void *workspace, size_t ws_bytes, int64_t *n_keys,
+                       int64_t *keys_needed, void *stream);
+
+/* Device views into the workspace after a forward, for inspection and tests. All
+ * pointers are device pointers inside the workspace; lengths follow from the problem
+ * shape: tile_offsets has n_tiles + 1 uint32 entries (tile t's sorted list is
+ * entries[tile_offsets[t] .. tile_offsets[t+1])); each entry is
+ * (f32 bits of the view depth << 32) | global Gaussian index; t_final and n_contrib
+ * hold one value per view pixel, views concatenated. */
+typedef struct {
+    const uint32_t *tile_offsets;
+    const uint64_t *entries;
+    const float *t_final;
+    const uint32_t *n_contrib;
+    int32_t n_tiles;
+    int64_t n_pixels;
+} sgad_state_view;
+
+sgad_status sgad_state(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
+                       const sgad_camera *views, int32_t n_views, void *workspace,
+                       size_t ws_bytes, int64_t key_capacity, sgad_state_view *out);
+
+/* Work counters of the last forward on this workspace (synchronises `stream`): keys
+ * emitted, keys needed, (pixel, entry) pairs composited (the contributors: alpha >= 1/255
+ * before the stop) and pairs whose alpha was evaluated. Host memory out. */
+typedef struct {
+    int64_t n_keys;
+    int64_t keys_needed;
+    int64_t n_pairs;
+    int64_t n_evals;
+} sgad_stats;
+
+sgad_status sgad_read_stats(sgad_ctx *ctx, void *workspace, size_t ws_bytes, sgad_stats *out,
+                            void *stream);
+
+/* Per-stage timing. When enabled, sgad_forward / sgad_backward record CUDA events on
+ * their stream between stages; sgad_profile_read waits for them and returns the last
+ * call's stage times in milliseconds, in this order:
+ *   0 projection + binning count + scan   1 key emission   2 per-tile sort
+ *   3 forward compositing                 4 backward compositing (incl. clearing the
+ *                                           gradient accumulators)
+ *   5 gradient finalisation (d delta, d logit)
+ * A stage of a call that was not made reads 0. */
+#define SGAD_NUM_STAGES 6
+sgad_status sgad_profile_enable(sgad_ctx *ctx, int32_t enable);
+sgad_status sgad_profile_read(sgad_ctx *ctx, float *ms /* [SGAD_NUM_STAGES] */);
+
+/* L1 terms of the mapping loss Eq. 1 (the SSIM term is not included), per view:
+ *   rgb_weight   * mean over pixels and channels |V' - V|
+ * + depth_weight * mean over pixels with target depth > 0 of |D' - D|,
+ * summed over views. Writes d loss / d V' into d_rgb[k] ([3][H][W]) and d loss / d D'
+ * into d_depth[k] ([H][W]) with sign(0) = 0, and adds the loss value to *loss_accum (one
+ * device float, zeroed by the caller; may be NULL). target_depth and d_depth may be NULL
+ * when depth_weight == 0. valid_count is caller-owned device scratch of n_views uint32
+ * (the valid-depth pixel count U_k per view; overwritten), required when depth_weight
+ * != 0. */
+sgad_status sgad_l1_loss_grad(int32_t n_views, const sgad_camera *views,
+                              const sgad_images *rendered, const float *const *target_rgb,
+                              const float *const *target_depth, float rgb_weight,
+                              float depth_weight, float *const *d_rgb, float *const *d_depth,
+                              float *loss_accum, uint32_t *valid_count, void *stream);
+
+/* One bias-corrected Adam step (PyTorch convention) on `n` FP32 parameters in place:
+ *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
+ *   p <- p - lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * Supp. A gives the learning rates: colour 0.0025, radius 0.005, opacity 0.05,
+ * offset 0.01. */
+sgad_status sgad_adam_step(int64_t n, float *param, const float *grad, float *m, float *v,
+                           float lr, float beta1, float beta2, float eps, int32_t step,
+                           void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGAD_H */

@@ -117,8 +117,8 @@ static void project_one(const orc_kf *kf, int64_t j, const orc_cam *view, const 
     P->zf = (double)(float)P->t[2];
 
     const double tz = P->t[2];
-    if (rel_gap(tz, NEAR_PLANE) < opt->margin) P->near = 1;
-    if (round_gap(tz) < Z_ROUND_MARGIN) P->near = 1;
+    if (rel_gap(tz, NEAR_PLANE) < opt->margin) P->near |= ORC_NEAR_PLANE;
+    if (round_gap(tz) < Z_ROUND_MARGIN) P->near |= ORC_NEAR_Z;
     if (!(tz > 0.0)) return;                      /* behind the camera: nothing to project */
 
     const double fx = view->fx, fy = view->fy;
@@ -140,15 +140,15 @@ static void project_one(const orc_kf *kf, int64_t j, const orc_cam *view, const 
     const double lam = mid + sqrt(fmax(0.1, mid * mid - det));
     const double r3 = 3.0 * sqrt(lam);
     P->rho = ceil(r3);
-    if (fabs(r3 - nearbyint(r3)) / r3 < opt->margin) P->near = 1;
+    if (fabs(r3 - nearbyint(r3)) / r3 < opt->margin) P->near |= ORC_NEAR_RHO;
 
     /* pixel rectangle [floor(p - rho), floor(p + rho)] clipped to the image */
     const double bx[2] = {P->p[0] - P->rho, P->p[0] + P->rho};
     const double by[2] = {P->p[1] - P->rho, P->p[1] + P->rho};
-    for (int e = 0; e < 2; ++e) {
-        if (bound_gap(bx[e], opt->tile_w, view->width) < opt->margin) P->near = 1;
-        if (bound_gap(by[e], opt->tile_h, view->height) < opt->margin) P->near = 1;
-    }
+    if (bound_gap(bx[0], opt->tile_w, view->width) < opt->margin) P->near |= ORC_NEAR_X0;
+    if (bound_gap(bx[1], opt->tile_w, view->width) < opt->margin) P->near |= ORC_NEAR_X1;
+    if (bound_gap(by[0], opt->tile_h, view->height) < opt->margin) P->near |= ORC_NEAR_Y0;
+    if (bound_gap(by[1], opt->tile_h, view->height) < opt->margin) P->near |= ORC_NEAR_Y1;
     double xlo = floor(bx[0]), xhi = floor(bx[1]), ylo = floor(by[0]), yhi = floor(by[1]);
     xlo = fmax(xlo, 0.0); ylo = fmax(ylo, 0.0);
     xhi = fmin(xhi, (double)view->width - 1.0); yhi = fmin(yhi, (double)view->height - 1.0);
@@ -375,29 +375,51 @@ static void walk_pixel(const orc_proj *proj, const list_entry *list, int64_t n, 
     out->hash = h;
 }
 
-/* Pixels where a Gaussian with a near binning decision could be listed or not: every
- * pixel of the tiles around its rectangle at which its alpha would pass the floor. */
+/* Tile range [t0, t1] (clipped; t0 > t1 when empty) of the pixel interval
+ * [floor(lo), floor(hi)] clipped to [0, size - 1]. */
+static void tile_span(double lo, double hi, int32_t size, int32_t tile, int32_t *t0, int32_t *t1)
+{
+    double a = floor(lo), b = floor(hi);
+    if (b < 0.0 || a > size - 1.0) { *t0 = 1; *t1 = 0; return; }
+    a = fmax(a, 0.0);
+    b = fmin(b, size - 1.0);
+    *t0 = (int32_t)a / tile;
+    *t1 = (int32_t)b / tile;
+}
+
+/* Pixels whose result depends on a binning decision that FP32 may take differently:
+ * the tiles that lie in the largest rectangle the near decisions allow (radius + 1 when
+ * the ceil is near, near edges moved outwards by half a pixel) but not in the smallest
+ * one (radius - 1, near edges moved inwards; nothing when the near-plane cull is near),
+ * and there only the pixels at which this Gaussian's alpha passes the floor. */
 static void mark_binning_near(const orc_proj *proj, int64_t nG, const orc_cam *view,
                               const orc_opts *opt, uint8_t *near)
 {
     const int32_t W = view->width, H = view->height;
-    const int32_t ntx = tiles_x(view, opt), nty = tiles_y(view, opt);
+    const int bin_bits = ORC_NEAR_PLANE | ORC_NEAR_RHO | ORC_NEAR_X0 | ORC_NEAR_X1 | ORC_NEAR_Y0 | ORC_NEAR_Y1;
     for (int64_t g = 0; g < nG; ++g) {
         const orc_proj *P = &proj[g];
-        if (!P->near || !(P->t[2] > 0.0) || P->rho <= 0.0) continue;
-        int32_t x0 = (int32_t)floor(P->p[0] - P->rho), x1 = (int32_t)floor(P->p[0] + P->rho);
-        int32_t y0 = (int32_t)floor(P->p[1] - P->rho), y1 = (int32_t)floor(P->p[1] + P->rho);
-        int32_t tx0 = (int32_t)floor((double)x0 / opt->tile_w) - 1, tx1 = (int32_t)floor((double)x1 / opt->tile_w) + 1;
-        int32_t ty0 = (int32_t)floor((double)y0 / opt->tile_h) - 1, ty1 = (int32_t)floor((double)y1 / opt->tile_h) + 1;
-        if (tx0 < 0) tx0 = 0;
-        if (ty0 < 0) ty0 = 0;
-        if (tx1 >= ntx) tx1 = ntx - 1;
-        if (ty1 >= nty) ty1 = nty - 1;
-        for (int32_t y = ty0 * opt->tile_h; y < (ty1 + 1) * opt->tile_h && y < H; ++y)
-            for (int32_t x = tx0 * opt->tile_w; x < (tx1 + 1) * opt->tile_w && x < W; ++x) {
-                const double dx = P->p[0] - x, dy = P->p[1] - y;
-                const double power = -0.5 * (P->conic[0] * dx * dx + P->conic[2] * dy * dy) - P->conic[1] * dx * dy;
-                if (P->o * exp(power) >= ALPHA_FLOOR * (1.0 - opt->margin)) near[(int64_t)y * W + x] = 1;
+        if (!(P->near & bin_bits) || !(P->t[2] > 0.0) || P->rho <= 0.0) continue;
+        const double dr = (P->near & ORC_NEAR_RHO) ? 1.0 : 0.0;
+        const double ex0 = (P->near & ORC_NEAR_X0) ? 0.5 : 0.0, ex1 = (P->near & ORC_NEAR_X1) ? 0.5 : 0.0;
+        const double ey0 = (P->near & ORC_NEAR_Y0) ? 0.5 : 0.0, ey1 = (P->near & ORC_NEAR_Y1) ? 0.5 : 0.0;
+        const double rmax = P->rho + dr, rmin = P->rho - dr;
+        int32_t ax0, ax1, ay0, ay1, ix0, ix1, iy0, iy1;
+        tile_span(P->p[0] - rmax - ex0, P->p[0] + rmax + ex1, W, opt->tile_w, &ax0, &ax1);
+        tile_span(P->p[1] - rmax - ey0, P->p[1] + rmax + ey1, H, opt->tile_h, &ay0, &ay1);
+        tile_span(P->p[0] - rmin + ex0, P->p[0] + rmin - ex1, W, opt->tile_w, &ix0, &ix1);
+        tile_span(P->p[1] - rmin + ey0, P->p[1] + rmin - ey1, H, opt->tile_h, &iy0, &iy1);
+        const int inner_empty = (P->near & ORC_NEAR_PLANE) || ix0 > ix1 || iy0 > iy1;
+        for (int32_t ty = ay0; ty <= ay1; ++ty)
+            for (int32_t tx = ax0; tx <= ax1; ++tx) {
+                if (!inner_empty && tx >= ix0 && tx <= ix1 && ty >= iy0 && ty <= iy1) continue;
+                for (int32_t y = ty * opt->tile_h; y < (ty + 1) * opt->tile_h && y < H; ++y)
+                    for (int32_t x = tx * opt->tile_w; x < (tx + 1) * opt->tile_w && x < W; ++x) {
+                        const double dx = P->p[0] - x, dy = P->p[1] - y;
+                        const double power =
+                            -0.5 * (P->conic[0] * dx * dx + P->conic[2] * dy * dy) - P->conic[1] * dx * dy;
+                        if (P->o * exp(power) >= ALPHA_FLOOR * (1.0 - opt->margin)) near[(int64_t)y * W + x] = 1;
+                    }
             }
     }
 }

@@ -59,12 +59,24 @@ typedef struct {
     double margin;              /* relative margin below which a decision is "near" */
 } orc_opts;
 
+/* Decisions of the binning of one (Gaussian, view) pair that lie within the margin of
+ * their threshold: the near-plane cull, the ceil of the radius, each of the four edges of
+ * the tile rectangle (lower/upper x, lower/upper y), and the f32 rounding of the depth
+ * key (which changes the key bits but, short of an exact depth tie, not the order). */
+#define ORC_NEAR_PLANE 1
+#define ORC_NEAR_RHO 2
+#define ORC_NEAR_X0 4
+#define ORC_NEAR_X1 8
+#define ORC_NEAR_Y0 16
+#define ORC_NEAR_Y1 32
+#define ORC_NEAR_Z 64
+
 /* Projection of one Gaussian into one view. */
 typedef struct {
     int32_t visible;            /* passed the near plane (t_z > 0.2) */
     int32_t tx0, tx1, ty0, ty1; /* inclusive tile rectangle; empty when tx0 > tx1 */
     int32_t ntiles;
-    int32_t near;               /* a binning decision or the key rounding is near */
+    int32_t near;               /* bit mask of decisions within the margin (ORC_NEAR_*) */
     int32_t pad_;
     double mu[3];               /* world-space centre */
     double t[3];                /* view-space centre */

@@ -1,0 +1,221 @@
+"""ctypes binding of the C ABI in include/sgad.h (libsgad.so).
+
+Argument marshalling only: every step of the splatting path runs in the CUDA library.
+Importing this module loads libsgad.so (building it with nvcc first if it is missing or
+stale) and raises if that fails; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+SGAD_OK = 0
+SGAD_ERR_INVALID_ARG = -1
+SGAD_ERR_CUDA = -2
+SGAD_ERR_WORKSPACE_TOO_SMALL = -3
+SGAD_ERR_KEY_OVERFLOW = -4
+SGAD_ERR_TIMEOUT = -5
+SGAD_ERR_UNSUPPORTED = -6
+SGAD_ERR_NO_FORWARD = -7
+SGAD_MAX_KEYFRAMES = 32
+SGAD_MAX_VIEWS = 64
+
+EXPORTS = ["sgad_default_options", "sgad_create", "sgad_destroy", "sgad_last_error", "sgad_workspace_size",
+           "sgad_count_keys", "sgad_forward", "sgad_backward", "sgad_check", "sgad_state", "sgad_read_stats",
+           "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_adam_step"]
+SGAD_NUM_STAGES = 6
+STAGE_NAMES = ["binning", "emit", "sort", "composite_fwd", "composite_bwd", "finalize"]
+
+
+class SgadError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("sgad status %d: %s" % (status, message))
+        self.status = status
+
+
+class sgad_camera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("pose", C.c_float * 12)]
+
+
+class sgad_keyframe(C.Structure):
+    _fields_ = [("depth", C.c_void_p), ("offset", C.c_void_p), ("rgb", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("scale", C.c_void_p), ("cam", sgad_camera),
+                ("learnable", C.c_int32)]
+
+
+class sgad_images(C.Structure):
+    _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("alpha", C.c_void_p)]
+
+
+class sgad_image_grads(C.Structure):
+    _fields_ = [("d_rgb", C.c_void_p), ("d_depth", C.c_void_p), ("d_alpha", C.c_void_p)]
+
+
+class sgad_keyframe_grads(C.Structure):
+    _fields_ = [("d_offset", C.c_void_p), ("d_rgb", C.c_void_p), ("d_opacity_logit", C.c_void_p),
+                ("d_scale", C.c_void_p)]
+
+
+class sgad_options(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("bg", C.c_float * 3),
+                ("sort_smem_cap", C.c_int32), ("freeze_offset", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class sgad_state_view(C.Structure):
+    _fields_ = [("tile_offsets", C.c_void_p), ("entries", C.c_void_p), ("t_final", C.c_void_p),
+                ("n_contrib", C.c_void_p), ("n_tiles", C.c_int32), ("n_pixels", C.c_int64)]
+
+
+class sgad_stats(C.Structure):
+    _fields_ = [("n_keys", C.c_int64), ("keys_needed", C.c_int64), ("n_pairs", C.c_int64),
+                ("n_evals", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True) -> C.CDLL:
+    """Load libsgad.so (compiling it first when needed). Raises on any failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError("libsgad.so is missing; run paper_2603_21055_gb300.build.build()")
+    l = C.CDLL(_build.LIB)
+    P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+    st = C.c_int32
+    sig = {
+        "sgad_default_options": (st, [P]),
+        "sgad_create": (st, [P, P]),
+        "sgad_destroy": (None, [P]),
+        "sgad_last_error": (C.c_char_p, []),
+        "sgad_workspace_size": (st, [P, P, I32, P, I32, I64, P]),
+        "sgad_count_keys": (st, [P, P, I32, P, I32, P, C.c_size_t, P, P]),
+        "sgad_forward": (st, [P, P, I32, P, I32, P, P, C.c_size_t, I64, P]),
+        "sgad_backward": (st, [P, P, I32, P, I32, P, P, P, C.c_size_t, I64, P]),
+        "sgad_check": (st, [P, P, C.c_size_t, P, P, P]),
+        "sgad_state": (st, [P, P, I32, P, I32, P, C.c_size_t, I64, P]),
+        "sgad_read_stats": (st, [P, P, C.c_size_t, P, P]),
+        "sgad_profile_enable": (st, [P, I32]),
+        "sgad_profile_read": (st, [P, P]),
+        "sgad_l1_loss_grad": (st, [I32, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P]),
+        "sgad_adam_step": (st, [I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I32, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(l, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = l
+    return l
+
+
+def last_error() -> str:
+    return load().sgad_last_error().decode()
+
+
+def check(status: int) -> None:
+    if status != SGAD_OK:
+        raise SgadError(status, last_error())
+
+
+def _call(name, *args):
+    check(getattr(load(), name)(*args))
+
+
+# Same names as the C ABI; arguments are ctypes objects / integers (device addresses).
+
+def sgad_default_options() -> sgad_options:
+    o = sgad_options()
+    _call("sgad_default_options", C.byref(o))
+    return o
+
+
+def sgad_create(opt: sgad_options | None = None) -> C.c_void_p:
+    ctx = C.c_void_p()
+    _call("sgad_create", C.byref(ctx), C.byref(opt) if opt is not None else None)
+    return ctx
+
+
+def sgad_destroy(ctx) -> None:
+    load().sgad_destroy(ctx)
+
+
+def sgad_workspace_size(ctx, kfs, views, key_capacity: int) -> int:
+    n = C.c_size_t()
+    _call("sgad_workspace_size", ctx, kfs, len(kfs), views, len(views), int(key_capacity), C.byref(n))
+    return n.value
+
+
+def sgad_count_keys(ctx, kfs, views, workspace: int, ws_bytes: int, stream: int) -> int:
+    n = C.c_int64()
+    _call("sgad_count_keys", ctx, kfs, len(kfs), views, len(views), workspace, ws_bytes, C.byref(n), stream)
+    return n.value
+
+
+def sgad_forward(ctx, kfs, views, out, workspace: int, ws_bytes: int, key_capacity: int, stream: int) -> None:
+    _call("sgad_forward", ctx, kfs, len(kfs), views, len(views), out, workspace, ws_bytes, int(key_capacity), stream)
+
+
+def sgad_backward(ctx, kfs, views, grad_in, grads_out, workspace: int, ws_bytes: int, key_capacity: int,
+                  stream: int) -> None:
+    _call("sgad_backward", ctx, kfs, len(kfs), views, len(views), grad_in, grads_out, workspace, ws_bytes,
+          int(key_capacity), stream)
+
+
+def sgad_check(ctx, workspace: int, ws_bytes: int, stream: int):
+    """Returns (status, n_keys, keys_needed) without raising."""
+    n, need = C.c_int64(), C.c_int64()
+    s = load().sgad_check(ctx, workspace, ws_bytes, C.byref(n), C.byref(need), stream)
+    return s, n.value, need.value
+
+
+def sgad_state(ctx, kfs, views, workspace: int, ws_bytes: int, key_capacity: int) -> sgad_state_view:
+    out = sgad_state_view()
+    _call("sgad_state", ctx, kfs, len(kfs), views, len(views), workspace, ws_bytes, int(key_capacity),
+          C.byref(out))
+    return out
+
+
+def sgad_read_stats(ctx, workspace: int, ws_bytes: int, stream: int) -> sgad_stats:
+    out = sgad_stats()
+    _call("sgad_read_stats", ctx, workspace, ws_bytes, C.byref(out), stream)
+    return out
+
+
+def sgad_profile_enable(ctx, enable: bool) -> None:
+    _call("sgad_profile_enable", ctx, int(bool(enable)))
+
+
+def sgad_profile_read(ctx):
+    ms = (C.c_float * SGAD_NUM_STAGES)()
+    _call("sgad_profile_read", ctx, ms)
+    return list(ms)
+
+
+def sgad_l1_loss_grad(views, rendered, target_rgb, target_depth, rgb_weight, depth_weight, d_rgb, d_depth,
+                      loss_accum: int, valid_count: int, stream: int) -> None:
+    _call("sgad_l1_loss_grad", len(views), views, rendered, target_rgb, target_depth, float(rgb_weight),
+          float(depth_weight), d_rgb, d_depth, loss_accum, valid_count, stream)
+
+
+def sgad_adam_step(n: int, param: int, grad: int, m: int, v: int, lr: float, beta1: float, beta2: float,
+                   eps: float, step: int, stream: int) -> None:
+    _call("sgad_adam_step", int(n), param, grad, m, v, float(lr), float(beta1), float(beta2), float(eps),
+          int(step), stream)
+
+
+def ptr_array(ptrs):
+    """A C array of device pointers (void *) from a list of integers (0 -> NULL)."""
+    arr = (C.c_void_p * max(1, len(ptrs)))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p or None
+    return arr

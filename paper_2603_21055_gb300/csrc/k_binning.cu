@@ -1,0 +1,198 @@
+// Projection and tile binning (forward steps a1-a4).
+//
+//   k_project_count : per Gaussian, the world centre mu = R_i (|D + delta| r) + t_i
+//                     (Sec. 3.2), opacity sigmoid(logit), the view-independent record,
+//                     and for every view the tile rectangle of its 3-sigma square;
+//                     per-tile counts with warp-aggregated atomics.
+//   k_scan_tiles    : exclusive scan of the per-tile counts -> list offsets; flags a
+//                     key overflow.
+//   k_emit          : per Gaussian and view, one 8-byte entry (f32 depth bits << 32 |
+//                     Gaussian index) per tile of the rectangle, written into the tile's
+//                     bucket. The depth is evaluated in double-float so the key is the
+//                     exactly-rounded f32 of the view depth.
+#include "sgad_device.cuh"
+
+namespace sgad {
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void __launch_bounds__(256) k_project_count(const __grid_constant__ Scene sc, World *__restrict__ world,
+                                                       uint32_t *__restrict__ tile_cnt)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = g < sc.n_gauss;
+    float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        const KfDev &k = sc.kf[find_kf(sc, g)];
+        const uint32_t j = g - k.gbase;
+        const int u = (int)(j % (uint32_t)k.W), v = (int)(j / (uint32_t)k.W);
+        const size_t hw = (size_t)k.W * k.H;
+        const float D = k.depth[j], delta = k.offset[j];
+        const float d = fabsf(__fadd_rn(D, delta));
+        const float rx = __fdiv_rn(__fsub_rn((float)u, k.cx), k.fx);
+        const float ry = __fdiv_rn(__fsub_rn((float)v, k.cy), k.fy);
+        const float qx = __fmul_rn(d, rx), qy = __fmul_rn(d, ry);
+        w0.x = __fmaf_rn(k.R[0], qx, __fmaf_rn(k.R[1], qy, __fmaf_rn(k.R[2], d, k.t[0])));
+        w0.y = __fmaf_rn(k.R[3], qx, __fmaf_rn(k.R[4], qy, __fmaf_rn(k.R[5], d, k.t[1])));
+        w0.z = __fmaf_rn(k.R[6], qx, __fmaf_rn(k.R[7], qy, __fmaf_rn(k.R[8], d, k.t[2])));
+        w0.w = k.scale[j];
+        const float o = 1.0f / (1.0f + expf(-k.logit[j]));
+        World w;
+        w.w0 = w0;
+        w.w1 = make_float4(o, k.rgb[j], k.rgb[hw + j], k.rgb[2 * hw + j]);
+        world[g] = w;
+    }
+    const unsigned full = 0xffffffffu;
+    for (int vi = 0; vi < sc.n_views; ++vi) {
+        const ViewDev &v = sc.view[vi];
+        Rect r;
+        int n = 0;
+        if (valid) n = bin_rect(project(w0, v), v, sc.tw_log2, sc.th_log2, r);
+        const int maxn = __reduce_max_sync(full, n);
+        for (int i = 0; i < maxn; ++i) {
+            uint32_t tile = kInvalidTile;
+            if (i < n) {
+                const int ty = r.ty0 + i / r.nx, tx = r.tx0 + i % r.nx;
+                tile = (uint32_t)(v.tile_base + ty * v.tiles_x + tx);
+            }
+            const uint32_t peers = __match_any_sync(full, tile);
+            if (tile != kInvalidTile && (threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAdd(&tile_cnt[tile], (uint32_t)__popc(peers));
+        }
+    }
+}
+
+// Single-CTA exclusive scan of the per-tile counts (1024 threads, 4 tiles per thread per
+// round). Also resets the counts to serve as emission cursors.
+__global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t *__restrict__ cnt, uint32_t *__restrict__ off, int n_tiles,
+                                                     uint64_t key_cap, WsHeader *hdr)
+{
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint64_t carry_s;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < n_tiles; base += 4096) {
+        uint32_t c[4];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = base + threadIdx.x * 4 + q;
+            c[q] = i < n_tiles ? cnt[i] : 0u;
+            sum += c[q];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sums[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t ws = warp_sums[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += y;
+            }
+            warp_sums[lane] = ws;       // inclusive over warps
+        }
+        __syncthreads();
+        const uint64_t carry = carry_s;
+        uint64_t run = carry + (wid > 0 ? warp_sums[wid - 1] : 0u) + (incl - sum);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = base + threadIdx.x * 4 + q;
+            if (i < n_tiles) {
+                off[i] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
+                cnt[i] = 0u;
+            }
+            run += c[q];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s = carry + warp_sums[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const uint64_t total = carry_s;
+        off[n_tiles] = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
+        hdr->n_keys = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
+        hdr->needed = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
+        hdr->overflow = total > key_cap ? 1u : 0u;
+        if (total > key_cap) record_error(hdr, SGAD_ERR_KEY_OVERFLOW);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Scene sc, const World *__restrict__ world,
+                                              const uint32_t *__restrict__ off, uint32_t *__restrict__ cursor,
+                                              uint64_t *__restrict__ entries, WsHeader *hdr)
+{
+    if (hdr->overflow) return;
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = g < sc.n_gauss;
+    float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    dvec3 m = {};
+    if (valid) {
+        w0 = world[g].w0;
+        const KfDev &k = sc.kf[find_kf(sc, g)];
+        const uint32_t j = g - k.gbase;
+        m = df_world_point(k, (int)(j % (uint32_t)k.W), (int)(j / (uint32_t)k.W), k.depth[j], k.offset[j]);
+    }
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (int vi = 0; vi < sc.n_views; ++vi) {
+        const ViewDev &v = sc.view[vi];
+        Rect r;
+        int n = 0;
+        if (valid) n = bin_rect(project(w0, v), v, sc.tw_log2, sc.th_log2, r);
+        const int maxn = __reduce_max_sync(full, n);
+        if (maxn == 0) continue;
+        uint64_t key = 0;
+        if (n > 0) key = ((uint64_t)__float_as_uint(df_view_depth(m, v)) << 32) | g;
+        for (int i = 0; i < maxn; ++i) {
+            uint32_t tile = kInvalidTile;
+            if (i < n) {
+                const int ty = r.ty0 + i / r.nx, tx = r.tx0 + i % r.nx;
+                tile = (uint32_t)(v.tile_base + ty * v.tiles_x + tx);
+            }
+            const uint32_t peers = __match_any_sync(full, tile);
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0;
+            if (tile != kInvalidTile && lane == leader) base = atomicAdd(&cursor[tile], (uint32_t)__popc(peers));
+            base = __shfl_sync(full, base, leader);
+            if (tile != kInvalidTile) {
+                const uint32_t slot = off[tile] + base + __popc(peers & lanemask_lt());
+                if (slot < off[tile + 1])
+                    entries[slot] = key;
+                else
+                    atomicExch(&hdr->emit_overrun, 1u);
+            }
+        }
+    }
+}
+
+void launch_project_count(const Scene &sc, World *world, uint32_t *tile_cnt, cudaStream_t st)
+{
+    const unsigned blocks = (sc.n_gauss + 255) / 256;
+    if (blocks) k_project_count<<<blocks, 256, 0, st>>>(sc, world, tile_cnt);
+}
+
+void launch_scan_tiles(uint32_t *cnt, uint32_t *off, int n_tiles, uint64_t key_cap, WsHeader *hdr, cudaStream_t st)
+{
+    k_scan_tiles<<<1, 1024, 0, st>>>(cnt, off, n_tiles, key_cap, hdr);
+}
+
+void launch_emit(const Scene &sc, const World *world, const uint32_t *off, uint32_t *cursor, uint64_t *entries,
+                 WsHeader *hdr, cudaStream_t st)
+{
+    const unsigned blocks = (sc.n_gauss + 255) / 256;
+    if (blocks) k_emit<<<blocks, 256, 0, st>>>(sc, world, off, cursor, entries, hdr);
+}
+
+}  // namespace sgad

@@ -1,0 +1,494 @@
+// C ABI entry points (include/sgad.h): argument checks, the workspace layout, and the
+// launch sequence of each call. No device memory is allocated here.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sgad_device.cuh"
+
+namespace sgad {
+void launch_project_count(const Scene &, World *, uint32_t *, cudaStream_t);
+void launch_scan_tiles(uint32_t *, uint32_t *, int, uint64_t, WsHeader *, cudaStream_t);
+void launch_emit(const Scene &, const World *, const uint32_t *, uint32_t *, uint64_t *, WsHeader *, cudaStream_t);
+cudaError_t launch_sort_tiles(const uint32_t *, uint64_t *, uint64_t *, int, int, const WsHeader *, cudaStream_t);
+void launch_composite(bool, const Scene &, const World *, const uint32_t *, const uint64_t *, float *, uint32_t *,
+                      float4 *, WsHeader *, cudaStream_t);
+void launch_finalize(const Scene &, const World *, const float4 *, cudaStream_t);
+void launch_l1(const float *, const float *, const float *, const float *, size_t, float, float, uint32_t *, float *,
+               float *, float *, cudaStream_t);
+void launch_adam(int64_t, float *, const float *, float *, float *, float, float, float, float, float, float,
+                 cudaStream_t);
+}  // namespace sgad
+
+using namespace sgad;
+
+struct sgad_ctx {
+    sgad_options opt;
+    int sort_cap;
+    // per-stage events: [0..4] forward boundaries, [5..7] backward boundaries
+    bool profile = false;
+    bool fwd_recorded = false, bwd_recorded = false;
+    cudaEvent_t ev[8] = {};
+};
+
+namespace {
+inline void mark(sgad_ctx *ctx, int i, cudaStream_t st)
+{
+    if (ctx->profile) cudaEventRecord(ctx->ev[i], st);
+}
+}  // namespace
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+sgad_status fail(sgad_status code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+sgad_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(SGAD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ilog2_exact(int x)
+{
+    int l = 0;
+    while ((1 << l) < x) ++l;
+    return (1 << l) == x ? l : -1;
+}
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
+
+bool valid_camera(const sgad_camera &c)
+{
+    if (c.width <= 0 || c.height <= 0 || c.width > 16384 || c.height > 16384) return false;
+    if (!finite_pos(c.fx) || !finite_pos(c.fy) || !std::isfinite(c.cx) || !std::isfinite(c.cy)) return false;
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(c.pose[i])) return false;
+    return true;
+}
+
+void set_cam(const sgad_camera &c, float &fx, float &fy, float &cx, float &cy, float *R, float *t)
+{
+    fx = c.fx;
+    fy = c.fy;
+    cx = c.cx;
+    cy = c.cy;
+    for (int r = 0; r < 3; ++r) {
+        for (int q = 0; q < 3; ++q) R[3 * r + q] = c.pose[4 * r + q];
+        t[r] = c.pose[4 * r + 3];
+    }
+}
+
+// Fills the launch parameters; checks shapes. Pointers are checked by the callers
+// according to what each call reads and writes.
+sgad_status build_scene(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf, const sgad_camera *views,
+                        int32_t n_views, Scene &sc, uint64_t &n_pix)
+{
+    if (!ctx) return fail(SGAD_ERR_INVALID_ARG, "ctx is NULL");
+    if (!kfs || n_kf < 1 || n_kf > SGAD_MAX_KEYFRAMES)
+        return fail(SGAD_ERR_INVALID_ARG, "n_kf must be in [1, %d] with kfs non-NULL", SGAD_MAX_KEYFRAMES);
+    if (!views || n_views < 1 || n_views > SGAD_MAX_VIEWS)
+        return fail(SGAD_ERR_INVALID_ARG, "n_views must be in [1, %d] with views non-NULL", SGAD_MAX_VIEWS);
+    std::memset(&sc, 0, sizeof(sc));
+    sc.n_kf = n_kf;
+    sc.n_views = n_views;
+    sc.tile_w = ctx->opt.tile_w;
+    sc.tile_h = ctx->opt.tile_h;
+    sc.tw_log2 = ilog2_exact(sc.tile_w);
+    sc.th_log2 = ilog2_exact(sc.tile_h);
+    for (int c = 0; c < 3; ++c) sc.bg[c] = ctx->opt.bg[c];
+    sc.freeze_offset = ctx->opt.freeze_offset;
+    uint64_t ng = 0;
+    for (int i = 0; i < n_kf; ++i) {
+        const sgad_keyframe &k = kfs[i];
+        if (!valid_camera(k.cam)) return fail(SGAD_ERR_INVALID_ARG, "keyframe %d: invalid camera", i);
+        KfDev &d = sc.kf[i];
+        d.depth = k.depth;
+        d.offset = k.offset;
+        d.rgb = k.rgb;
+        d.logit = k.opacity_logit;
+        d.scale = k.scale;
+        set_cam(k.cam, d.fx, d.fy, d.cx, d.cy, d.R, d.t);
+        d.W = k.cam.width;
+        d.H = k.cam.height;
+        d.gbase = (uint32_t)ng;
+        d.learnable = k.learnable ? 1 : 0;
+        ng += (uint64_t)k.cam.width * k.cam.height;
+        if (ng >= 0xffffffffull) return fail(SGAD_ERR_INVALID_ARG, "more than 2^32 - 1 Gaussians");
+    }
+    sc.n_gauss = (uint32_t)ng;
+    uint64_t nt = 0;
+    n_pix = 0;
+    for (int i = 0; i < n_views; ++i) {
+        if (!valid_camera(views[i])) return fail(SGAD_ERR_INVALID_ARG, "view %d: invalid camera", i);
+        ViewDev &v = sc.view[i];
+        set_cam(views[i], v.fx, v.fy, v.cx, v.cy, v.R, v.t);
+        v.W = views[i].width;
+        v.H = views[i].height;
+        v.tiles_x = (v.W + sc.tile_w - 1) / sc.tile_w;
+        v.tiles_y = (v.H + sc.tile_h - 1) / sc.tile_h;
+        v.tile_base = (int32_t)nt;
+        v.pix_base = (uint32_t)n_pix;
+        nt += (uint64_t)v.tiles_x * v.tiles_y;
+        n_pix += (uint64_t)v.W * v.H;
+        if (nt >= (1ull << 30) || n_pix >= 0xffffffffull) return fail(SGAD_ERR_INVALID_ARG, "too many pixels");
+    }
+    sc.n_tiles = (int32_t)nt;
+    return SGAD_OK;
+}
+
+struct Ws {
+    Layout L;
+    char *base;
+    WsHeader *hdr() const { return reinterpret_cast<WsHeader *>(base + L.header); }
+    World *world() const { return reinterpret_cast<World *>(base + L.world); }
+    float4 *gacc() const { return reinterpret_cast<float4 *>(base + L.gacc); }
+    uint32_t *tile_off() const { return reinterpret_cast<uint32_t *>(base + L.tile_off); }
+    uint32_t *tile_cnt() const { return reinterpret_cast<uint32_t *>(base + L.tile_cnt); }
+    float *pix_t() const { return reinterpret_cast<float *>(base + L.pix_t); }
+    uint32_t *pix_n() const { return reinterpret_cast<uint32_t *>(base + L.pix_n); }
+    uint64_t *keys() const { return reinterpret_cast<uint64_t *>(base + L.keys); }
+    uint64_t *keys_alt() const { return reinterpret_cast<uint64_t *>(base + L.keys_alt); }
+};
+
+sgad_status get_ws(const Scene &sc, uint64_t n_pix, void *workspace, size_t ws_bytes, int64_t key_cap, Ws &ws)
+{
+    if (key_cap < 0 || key_cap >= 0xffffffffll) return fail(SGAD_ERR_INVALID_ARG, "key_capacity out of range");
+    ws.L = make_layout(sc.n_gauss, (uint64_t)sc.n_tiles, n_pix, (uint64_t)key_cap);
+    if (!workspace) return fail(SGAD_ERR_INVALID_ARG, "workspace is NULL");
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return fail(SGAD_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < ws.L.total)
+        return fail(SGAD_ERR_WORKSPACE_TOO_SMALL, "workspace holds %zu bytes, %zu needed", ws_bytes, ws.L.total);
+    ws.base = static_cast<char *>(workspace);
+    return SGAD_OK;
+}
+
+sgad_status check_kf_inputs(const sgad_keyframe *kfs, int n_kf)
+{
+    for (int i = 0; i < n_kf; ++i)
+        if (!kfs[i].depth || !kfs[i].offset || !kfs[i].rgb || !kfs[i].opacity_logit || !kfs[i].scale)
+            return fail(SGAD_ERR_INVALID_ARG, "keyframe %d: a parameter plane is NULL", i);
+    return SGAD_OK;
+}
+
+sgad_status last_launch(const char *what)
+{
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SGAD_OK : cuda_fail(e, what);
+}
+
+// Projection, binning count and scan: the part shared by sgad_count_keys and sgad_forward.
+sgad_status run_binning_count(const Scene &sc, const Ws &ws, int64_t key_cap, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(ws.hdr(), 0, sizeof(WsHeader), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.tile_cnt(), 0, ((size_t)sc.n_tiles + 1) * 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    launch_project_count(sc, ws.world(), ws.tile_cnt(), st);
+    launch_scan_tiles(ws.tile_cnt(), ws.tile_off(), sc.n_tiles, (uint64_t)key_cap, ws.hdr(), st);
+    return last_launch("binning");
+}
+
+}  // namespace
+
+extern "C" {
+
+sgad_status sgad_default_options(sgad_options *opt)
+{
+    if (!opt) return fail(SGAD_ERR_INVALID_ARG, "opt is NULL");
+    std::memset(opt, 0, sizeof(*opt));
+    opt->tile_w = 16;
+    opt->tile_h = 16;
+    opt->sort_smem_cap = 0;
+    opt->freeze_offset = 0;
+    return SGAD_OK;
+}
+
+sgad_status sgad_create(sgad_ctx **out, const sgad_options *opt)
+{
+    if (!out) return fail(SGAD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    sgad_options o;
+    if (opt)
+        o = *opt;
+    else
+        sgad_default_options(&o);
+    const bool shape_ok = (o.tile_w == 16 && o.tile_h == 16) || (o.tile_w == 8 && o.tile_h == 32) ||
+                          (o.tile_w == 32 && o.tile_h == 8);
+    if (!shape_ok) return fail(SGAD_ERR_UNSUPPORTED, "tile shape %dx%d not supported", o.tile_w, o.tile_h);
+    for (int i = 0; i < 4; ++i)
+        if (o.reserved[i] != 0) return fail(SGAD_ERR_INVALID_ARG, "reserved options must be zero");
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(o.bg[c])) return fail(SGAD_ERR_INVALID_ARG, "background must be finite");
+    const int cap = o.sort_smem_cap == 0 ? 6144 : o.sort_smem_cap;
+    if (cap < 64 || cap > 12288) return fail(SGAD_ERR_INVALID_ARG, "sort_smem_cap must be in [64, 12288]");
+    sgad_ctx *c = new (std::nothrow) sgad_ctx;
+    if (!c) return fail(SGAD_ERR_INVALID_ARG, "out of host memory");
+    c->opt = o;
+    c->sort_cap = cap;
+    *out = c;
+    return SGAD_OK;
+}
+
+void sgad_destroy(sgad_ctx *ctx)
+{
+    if (!ctx) return;
+    for (cudaEvent_t &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+sgad_status sgad_profile_enable(sgad_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return fail(SGAD_ERR_INVALID_ARG, "ctx is NULL");
+    if (enable && !ctx->ev[0]) {
+        for (cudaEvent_t &e : ctx->ev) {
+            const cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_fail(r, "cudaEventCreate");
+        }
+    }
+    ctx->profile = enable != 0;
+    ctx->fwd_recorded = ctx->bwd_recorded = false;
+    return SGAD_OK;
+}
+
+sgad_status sgad_profile_read(sgad_ctx *ctx, float *ms)
+{
+    if (!ctx || !ms) return fail(SGAD_ERR_INVALID_ARG, "bad arguments to sgad_profile_read");
+    for (int i = 0; i < SGAD_NUM_STAGES; ++i) ms[i] = 0.0f;
+    if (ctx->fwd_recorded) {
+        cudaError_t r = cudaEventSynchronize(ctx->ev[4]);
+        for (int i = 0; i < 4 && r == cudaSuccess; ++i) r = cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]);
+        if (r != cudaSuccess) return cuda_fail(r, "sgad_profile_read");
+    }
+    if (ctx->bwd_recorded) {
+        cudaError_t r = cudaEventSynchronize(ctx->ev[7]);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&ms[4], ctx->ev[5], ctx->ev[6]);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&ms[5], ctx->ev[6], ctx->ev[7]);
+        if (r != cudaSuccess) return cuda_fail(r, "sgad_profile_read");
+    }
+    return SGAD_OK;
+}
+
+sgad_status sgad_read_stats(sgad_ctx *ctx, void *workspace, size_t ws_bytes, sgad_stats *out, void *stream)
+{
+    if (!ctx || !workspace || !out || ws_bytes < sizeof(WsHeader)) return fail(SGAD_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    WsHeader h;
+    cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "sgad_read_stats");
+    out->n_keys = h.n_keys;
+    out->keys_needed = h.needed;
+    out->n_pairs = (int64_t)h.n_pairs;
+    out->n_evals = (int64_t)h.n_evals;
+    return SGAD_OK;
+}
+
+const char *sgad_last_error(void) { return g_err; }
+
+sgad_status sgad_workspace_size(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
+                                const sgad_camera *views, int32_t n_views, int64_t key_capacity, size_t *bytes)
+{
+    if (!bytes) return fail(SGAD_ERR_INVALID_ARG, "bytes is NULL");
+    Scene sc;
+    uint64_t n_pix;
+    sgad_status s = build_scene(ctx, kfs, n_kf, views, n_views, sc, n_pix);
+    if (s) return s;
+    if (key_capacity < 0 || key_capacity >= 0xffffffffll)
+        return fail(SGAD_ERR_INVALID_ARG, "key_capacity out of range");
+    *bytes = make_layout(sc.n_gauss, (uint64_t)sc.n_tiles, n_pix, (uint64_t)key_capacity).total;
+    return SGAD_OK;
+}
+
+sgad_status sgad_count_keys(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf, const sgad_camera *views,
+                            int32_t n_views, void *workspace, size_t ws_bytes, int64_t *n_keys, void *stream)
+{
+    if (!n_keys) return fail(SGAD_ERR_INVALID_ARG, "n_keys is NULL");
+    Scene sc;
+    uint64_t n_pix;
+    Ws ws;
+    sgad_status s = build_scene(ctx, kfs, n_kf, views, n_views, sc, n_pix);
+    if (!s) s = check_kf_inputs(kfs, n_kf);
+    if (!s) s = get_ws(sc, n_pix, workspace, ws_bytes, 0, ws);
+    if (s) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s = run_binning_count(sc, ws, 0xfffffffell, st);
+    if (s) return s;
+    WsHeader h;
+    cudaError_t e = cudaMemcpyAsync(&h, ws.hdr(), sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "sgad_count_keys");
+    *n_keys = (int64_t)h.needed;
+    return SGAD_OK;
+}
+
+sgad_status sgad_forward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf, const sgad_camera *views,
+                         int32_t n_views, sgad_images *out, void *workspace, size_t ws_bytes, int64_t key_capacity,
+                         void *stream)
+{
+    Scene sc;
+    uint64_t n_pix;
+    Ws ws;
+    sgad_status s = build_scene(ctx, kfs, n_kf, views, n_views, sc, n_pix);
+    if (!s) s = check_kf_inputs(kfs, n_kf);
+    if (!s) s = get_ws(sc, n_pix, workspace, ws_bytes, key_capacity, ws);
+    if (s) return s;
+    if (!out) return fail(SGAD_ERR_INVALID_ARG, "out is NULL");
+    for (int i = 0; i < n_views; ++i) {
+        if (!out[i].rgb || !out[i].depth || !out[i].alpha)
+            return fail(SGAD_ERR_INVALID_ARG, "view %d: an output image is NULL", i);
+        sc.view[i].rgb = out[i].rgb;
+        sc.view[i].depth = out[i].depth;
+        sc.view[i].alpha = out[i].alpha;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    mark(ctx, 0, st);
+    s = run_binning_count(sc, ws, key_capacity, st);
+    if (s) return s;
+    mark(ctx, 1, st);
+    launch_emit(sc, ws.world(), ws.tile_off(), ws.tile_cnt(), ws.keys(), ws.hdr(), st);
+    mark(ctx, 2, st);
+    cudaError_t e = launch_sort_tiles(ws.tile_off(), ws.keys(), ws.keys_alt(), sc.n_tiles, ctx->sort_cap, ws.hdr(), st);
+    if (e != cudaSuccess) return cuda_fail(e, "sort launch");
+    mark(ctx, 3, st);
+    launch_composite(true, sc, ws.world(), ws.tile_off(), ws.keys(), ws.pix_t(), ws.pix_n(), nullptr, ws.hdr(), st);
+    mark(ctx, 4, st);
+    ctx->fwd_recorded = ctx->profile;
+    return last_launch("sgad_forward");
+}
+
+sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf, const sgad_camera *views,
+                          int32_t n_views, const sgad_image_grads *grad_in, sgad_keyframe_grads *grads_out,
+                          void *workspace, size_t ws_bytes, int64_t key_capacity, void *stream)
+{
+    Scene sc;
+    uint64_t n_pix;
+    Ws ws;
+    sgad_status s = build_scene(ctx, kfs, n_kf, views, n_views, sc, n_pix);
+    if (!s) s = check_kf_inputs(kfs, n_kf);
+    if (!s) s = get_ws(sc, n_pix, workspace, ws_bytes, key_capacity, ws);
+    if (s) return s;
+    if (!grad_in || !grads_out) return fail(SGAD_ERR_INVALID_ARG, "grad_in / grads_out is NULL");
+    for (int i = 0; i < n_views; ++i) {
+        sc.view[i].g_rgb = grad_in[i].d_rgb;
+        sc.view[i].g_depth = grad_in[i].d_depth;
+        sc.view[i].g_alpha = grad_in[i].d_alpha;
+    }
+    for (int i = 0; i < n_kf; ++i) {
+        KfDev &d = sc.kf[i];
+        d.d_offset = grads_out[i].d_offset;
+        d.d_rgb = grads_out[i].d_rgb;
+        d.d_logit = grads_out[i].d_opacity_logit;
+        d.d_scale = grads_out[i].d_scale;
+        if (d.learnable && (!d.d_offset || !d.d_rgb || !d.d_logit || !d.d_scale))
+            return fail(SGAD_ERR_INVALID_ARG, "keyframe %d is learnable but a gradient plane is NULL", i);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    mark(ctx, 5, st);
+    cudaError_t e = cudaMemsetAsync(ws.gacc(), 0, (size_t)sc.n_gauss * 32, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    launch_composite(false, sc, ws.world(), ws.tile_off(), ws.keys(), ws.pix_t(), ws.pix_n(), ws.gacc(), ws.hdr(), st);
+    mark(ctx, 6, st);
+    launch_finalize(sc, ws.world(), ws.gacc(), st);
+    mark(ctx, 7, st);
+    ctx->bwd_recorded = ctx->profile;
+    return last_launch("sgad_backward");
+}
+
+sgad_status sgad_check(sgad_ctx *ctx, void *workspace, size_t ws_bytes, int64_t *n_keys, int64_t *keys_needed,
+                       void *stream)
+{
+    if (!ctx || !workspace || ws_bytes < sizeof(WsHeader)) return fail(SGAD_ERR_INVALID_ARG, "bad workspace");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    WsHeader h;
+    cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "sgad_check");
+    if (n_keys) *n_keys = h.n_keys;
+    if (keys_needed) *keys_needed = h.needed;
+    if (h.err != 0 || h.emit_overrun != 0) {
+        const int zero = 0;
+        e = cudaMemcpyAsync(reinterpret_cast<char *>(workspace) + offsetof(WsHeader, err), &zero, sizeof(zero),
+                            cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "sgad_check");
+        if (h.emit_overrun) return fail(SGAD_ERR_CUDA, "internal: binning count and key emission disagree");
+        if (h.err == SGAD_ERR_KEY_OVERFLOW)
+            return fail(SGAD_ERR_KEY_OVERFLOW, "forward needed %u keys, more than the workspace capacity", h.needed);
+        return fail(h.err, "device reported error %d", h.err);
+    }
+    return SGAD_OK;
+}
+
+sgad_status sgad_state(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf, const sgad_camera *views,
+                       int32_t n_views, void *workspace, size_t ws_bytes, int64_t key_capacity, sgad_state_view *out)
+{
+    if (!out) return fail(SGAD_ERR_INVALID_ARG, "out is NULL");
+    Scene sc;
+    uint64_t n_pix;
+    Ws ws;
+    sgad_status s = build_scene(ctx, kfs, n_kf, views, n_views, sc, n_pix);
+    if (!s) s = get_ws(sc, n_pix, workspace, ws_bytes, key_capacity, ws);
+    if (s) return s;
+    out->tile_offsets = ws.tile_off();
+    out->entries = ws.keys();
+    out->t_final = ws.pix_t();
+    out->n_contrib = ws.pix_n();
+    out->n_tiles = sc.n_tiles;
+    out->n_pixels = (int64_t)n_pix;
+    return SGAD_OK;
+}
+
+sgad_status sgad_l1_loss_grad(int32_t n_views, const sgad_camera *views, const sgad_images *rendered,
+                              const float *const *target_rgb, const float *const *target_depth, float rgb_weight,
+                              float depth_weight, float *const *d_rgb, float *const *d_depth, float *loss_accum,
+                              uint32_t *valid_count, void *stream)
+{
+    if (n_views < 1 || !views || !rendered || !target_rgb || !d_rgb)
+        return fail(SGAD_ERR_INVALID_ARG, "bad arguments to sgad_l1_loss_grad");
+    if (!std::isfinite(rgb_weight) || !std::isfinite(depth_weight))
+        return fail(SGAD_ERR_INVALID_ARG, "loss weights must be finite");
+    const bool use_depth = depth_weight != 0.0f;
+    if (use_depth && (!target_depth || !d_depth || !valid_count))
+        return fail(SGAD_ERR_INVALID_ARG, "depth term needs target_depth, d_depth and valid_count");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (use_depth) {
+        cudaError_t e = cudaMemsetAsync(valid_count, 0, sizeof(uint32_t) * (size_t)n_views, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    for (int i = 0; i < n_views; ++i) {
+        if (!valid_camera(views[i])) return fail(SGAD_ERR_INVALID_ARG, "view %d: invalid camera", i);
+        if (!rendered[i].rgb || !target_rgb[i] || !d_rgb[i] || (use_depth && (!rendered[i].depth || !target_depth[i])))
+            return fail(SGAD_ERR_INVALID_ARG, "view %d: NULL image", i);
+        const size_t hw = (size_t)views[i].width * views[i].height;
+        launch_l1(rendered[i].rgb, rendered[i].depth, target_rgb[i], use_depth ? target_depth[i] : nullptr, hw,
+                  rgb_weight, depth_weight, use_depth ? valid_count + i : nullptr, d_rgb[i],
+                  d_depth ? d_depth[i] : nullptr, loss_accum, st);
+    }
+    return last_launch("sgad_l1_loss_grad");
+}
+
+sgad_status sgad_adam_step(int64_t n, float *param, const float *grad, float *m, float *v, float lr, float beta1,
+                           float beta2, float eps, int32_t step, void *stream)
+{
+    if (n < 0 || (n > 0 && (!param || !grad || !m || !v)) || step < 1)
+        return fail(SGAD_ERR_INVALID_ARG, "bad arguments to sgad_adam_step");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !std::isfinite(lr) || !(eps >= 0.0f))
+        return fail(SGAD_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+    const float c1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+    const float c2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+    launch_adam(n, param, grad, m, v, lr, beta1, beta2, eps, c1, c2, static_cast<cudaStream_t>(stream));
+    return last_launch("sgad_adam_step");
+}
+
+}  // extern "C"

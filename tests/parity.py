@@ -1,0 +1,136 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI and the
+FP64 oracle on the same float32 inputs, and compare them."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+IMAGE_ATOL = 1e-4          # spec tolerance for rendered images
+GRAD_RTOL = 1e-3           # spec tolerance for gradients (relative)
+
+
+def gpu_run(scene, grads_in=None, tile=(16, 16), sort_smem_cap=0, freeze_offset=False, bg=(0.0, 0.0, 0.0)):
+    """Forward (and backward when grads_in is given) through libsgad. Returns a dict of
+    numpy results plus the raw forward state."""
+    import torch
+    from paper_2603_21055_gb300 import splat
+    sp = splat.Splatter(tile=tile, sort_smem_cap=sort_smem_cap, freeze_offset=freeze_offset, bg=bg)
+    kfs = splat.upload_keyframes(scene)
+    n_keys = sp.plan(kfs, scene.views)
+    images = splat.alloc_images(scene.views)
+    sp.forward(kfs, scene.views, images)
+    status, nk, need = sp.check()
+    assert status == 0, (status, nk, need)
+    offs, entries, t_final, n_contrib = sp.state(kfs, scene.views)
+    res = dict(images=[{k: v.cpu().numpy() for k, v in im.items()} for im in images],
+               offsets=offs.cpu().numpy().astype(np.int64) & 0xffffffff,
+               entries=entries.cpu().numpy().view(np.uint64), t_final=t_final.cpu().numpy(),
+               n_contrib=n_contrib.cpu().numpy(), n_keys=nk, planned=n_keys)
+    if grads_in is not None:
+        gin = [{k: torch.as_tensor(np.ascontiguousarray(v, np.float32)).cuda() for k, v in g.items()}
+               for g in grads_in]
+        gout = []
+        for k in kfs:
+            if k.learnable:
+                gout.append(dict(d_offset=torch.full_like(k.offset, np.nan), d_rgb=torch.full_like(k.rgb, np.nan),
+                                 d_logit=torch.full_like(k.logit, np.nan), d_scale=torch.full_like(k.scale, np.nan)))
+            else:
+                gout.append(None)
+        sp.backward(kfs, scene.views, gin, gout)
+        torch.cuda.synchronize()
+        res["grads"] = [None if g is None else {k: v.cpu().numpy() for k, v in g.items()} for g in gout]
+    return res
+
+
+def gpu_key_list(res, scene):
+    """(keys, vals) of the GPU's sorted tile lists in the oracle's key format."""
+    offs, ent = res["offsets"], res["entries"]
+    tiles = np.repeat(np.arange(len(offs) - 1, dtype=np.uint64), np.diff(offs).astype(np.int64))
+    keys = (tiles << np.uint64(32)) | (ent >> np.uint64(32))
+    vals = (ent & np.uint64(0xffffffff)).astype(np.uint32)
+    return keys, vals
+
+
+def near_pairs(scene, o=None):
+    """Per view, the set of Gaussians whose binning or key rounding is near a threshold."""
+    out = []
+    for k in range(len(scene.views)):
+        P = oracle.project(scene, k, o)
+        out.append(set(np.nonzero(P["near"])[0].tolist()))
+    return out
+
+
+def compare_keys(res, scene, o=None):
+    """Keys and values must match the oracle's brute-force list exactly, after setting
+    aside entries of (view, Gaussian) pairs with a near decision. Returns the number of
+    entries set aside."""
+    ok, ov, onear = oracle.keys(scene, o)
+    gk, gv = gpu_key_list(res, scene)
+    tw, th = (o.tile_w, o.tile_h) if o is not None else (16, 16)
+    counts = [((v.width + tw - 1) // tw) * ((v.height + th - 1) // th) for v in scene.views]
+    tile_view = np.repeat(np.arange(len(counts)), counts)
+    near = near_pairs(scene, o)
+
+    def keep_mask(keys, vals):
+        t = (keys >> np.uint64(32)).astype(np.int64)
+        vw = tile_view[t]
+        return np.array([int(g) not in near[int(w)] for w, g in zip(vw, vals)], bool) if len(keys) else np.zeros(0, bool)
+
+    mo, mg = keep_mask(ok, ov), keep_mask(gk, gv)
+    np.testing.assert_array_equal(gk[mg], ok[mo])
+    np.testing.assert_array_equal(gv[mg], ov[mo])
+    return int((~mo).sum())
+
+
+def compare_images(res, ref, atol=IMAGE_ATOL):
+    """Images within atol and contributor counts exact on pixels without a near
+    decision. Returns (max error on clean pixels, number of near pixels)."""
+    worst, n_near = 0.0, 0
+    base = 0
+    for k, (g, r) in enumerate(zip(res["images"], ref)):
+        clean = r["near"] == 0
+        n_near += int((~clean).sum())
+        for q in ("rgb", "depth", "alpha"):
+            d = np.abs(g[q].astype(np.float64) - r[q])
+            d = d[:, clean] if q == "rgb" else d[clean]
+            worst = max(worst, float(d.max()) if d.size else 0.0)
+            assert d.size == 0 or d.max() <= atol, (k, q, float(d.max()))
+        hw = r["n_contrib"].size
+        nc = res["n_contrib"][base:base + hw].reshape(r["n_contrib"].shape)
+        tf = res["t_final"][base:base + hw].reshape(r["n_contrib"].shape)
+        np.testing.assert_array_equal(nc[clean], r["n_contrib"][clean])
+        assert np.abs(tf[clean] - r["t_final"][clean]).max() <= atol
+        base += hw
+    return worst, n_near
+
+
+def grad_error(g_gpu, g_ref, rtol=GRAD_RTOL, floor=1e-6):
+    """Max over entries of |gpu - ref| / (rtol |ref| + floor * max|ref|) (<= 1 passes)."""
+    scale = np.abs(g_ref).max()
+    den = rtol * np.abs(g_ref) + floor * max(scale, 1e-30)
+    return float((np.abs(g_gpu.astype(np.float64) - g_ref) / den).max())
+
+
+def compare_grads(res, ref_grads, rtol=GRAD_RTOL, floor=1e-6, quantile=1.0):
+    """Per keyframe and attribute, the error ratio of grad_error; returns the worst."""
+    worst = 0.0
+    for g, r in zip(res["grads"], ref_grads):
+        if g is None:
+            continue
+        for q in ("d_offset", "d_rgb", "d_logit", "d_scale"):
+            gq, rq = g[q], r[q]
+            assert np.all(np.isfinite(gq)), q
+            if quantile < 1.0:
+                scale = np.abs(rq).max()
+                den = rtol * np.abs(rq) + floor * max(scale, 1e-30)
+                e = float(np.quantile(np.abs(gq - rq) / den, quantile))
+            else:
+                e = grad_error(gq, rq, rtol, floor)
+            worst = max(worst, e)
+    return worst
+
+
+def l1_grads(scene, renders):
+    loss, g = oracle.l1_loss(scene, renders)
+    return loss, [dict(rgb=x["rgb"].astype(np.float32), depth=x["depth"].astype(np.float32)) for x in g]

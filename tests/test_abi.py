@@ -1,0 +1,89 @@
+"""CPU-side checks of the C ABI: the library builds and loads, exports every function
+include/sgad.h declares, and the host-only calls validate their arguments. No call here
+touches a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2603_21055_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "sgad.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sgad_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function():
+    lib = B.load()
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(B.EXPORTS) == names
+
+
+def test_default_options_and_create():
+    o = B.sgad_default_options()
+    assert (o.tile_w, o.tile_h) == (16, 16) and o.freeze_offset == 0
+    ctx = B.sgad_create(o)
+    B.sgad_destroy(ctx)
+    for w, h in ((8, 32), (32, 8)):
+        o.tile_w, o.tile_h = w, h
+        B.sgad_destroy(B.sgad_create(o))
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("tile_w", 12, B.SGAD_ERR_UNSUPPORTED),
+    ("sort_smem_cap", 8, B.SGAD_ERR_INVALID_ARG),
+])
+def test_create_rejects_bad_options(field, value, status):
+    o = B.sgad_default_options()
+    setattr(o, field, value)
+    with pytest.raises(B.SgadError) as e:
+        B.sgad_create(o)
+    assert e.value.status == status
+    assert B.last_error()
+
+
+def _cam(w=64, h=48):
+    c = B.sgad_camera(w, h, 60.0, 60.0, 32.0, 24.0)
+    for i, v in enumerate([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0]):
+        c.pose[i] = v
+    return c
+
+
+def test_workspace_size_arithmetic():
+    """Workspace = header + 64 B per Gaussian + tile offsets/counters + 8 B per view pixel
+    + 16 B per key, each section rounded to 256 B."""
+    ctx = B.sgad_create()
+    kfs = (B.sgad_keyframe * 1)()
+    kfs[0].cam = _cam()
+    views = (B.sgad_camera * 2)(_cam(), _cam(100, 70))
+    n0 = B.sgad_workspace_size(ctx, kfs, views, 0)
+    n1 = B.sgad_workspace_size(ctx, kfs, views, 1000)
+    assert n1 - n0 == 2 * ((1000 * 8 + 255) // 256 * 256)
+    ng, npx = 64 * 48, 64 * 48 + 100 * 70
+    assert n0 >= 256 + 64 * ng + 8 * npx
+    B.sgad_destroy(ctx)
+
+
+def test_host_validation_without_gpu():
+    ctx = B.sgad_create()
+    lib = B.load()
+    kfs = (B.sgad_keyframe * 1)()
+    kfs[0].cam = _cam()
+    views = (B.sgad_camera * 1)(_cam())
+    n = C.c_size_t()
+    assert lib.sgad_workspace_size(ctx, kfs, 0, views, 1, 0, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
+    assert lib.sgad_workspace_size(ctx, kfs, 1, views, 65, 0, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
+    bad = (B.sgad_camera * 1)(_cam())
+    bad[0].fx = -1.0
+    assert lib.sgad_workspace_size(ctx, kfs, 1, bad, 1, 0, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
+    assert lib.sgad_workspace_size(ctx, kfs, 1, views, 1, -5, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
+    assert lib.sgad_adam_step(10, None, None, None, None, 0.1, 0.9, 0.999, 1e-15, 1, None) == B.SGAD_ERR_INVALID_ARG
+    B.sgad_destroy(ctx)
