@@ -170,10 +170,13 @@ sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                           const sgad_image_grads *grad_in, sgad_keyframe_grads *grads_out,
                           void *workspace, size_t ws_bytes, int64_t key_capacity, void *stream);
 
-/* Synchronise `stream`, then read the device-side status of the workspace: SGAD_OK,
- * SGAD_ERR_KEY_OVERFLOW (with *keys_needed set to the count the last forward needed) or
- * SGAD_ERR_TIMEOUT. Clears the recorded error. keys_needed and n_keys may be NULL;
- * *n_keys receives the key count of the last forward. */
+/* Synchronise `stream`, then read the device-side status of the workspace: the first
+ * error recorded by any forward since the previous sgad_check() (SGAD_OK,
+ * SGAD_ERR_KEY_OVERFLOW or SGAD_ERR_TIMEOUT), and clear it. *keys_needed receives the
+ * largest key count a forward needed since then, *n_keys the key count of the last
+ * forward (both may be NULL). The status block is the first 256 bytes of the workspace:
+ * sgad_count_keys() zeroes it; a workspace used without it must start with those bytes
+ * zeroed. */
 sgad_status sgad_check(sgad_ctx *ctx, void *workspace, size_t ws_bytes, int64_t *n_keys,
                        int64_t *keys_needed, void *stream);
 
@@ -240,10 +243,34 @@ sgad_status sgad_l1_loss_grad(int32_t n_views, const sgad_camera *views,
  *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
  *   p <- p - lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
  * Supp. A gives the learning rates: colour 0.0025, radius 0.005, opacity 0.05,
- * offset 0.01. */
+ * offset 0.01. With mode SGAD_ADAM_LOG the array holds s = exp(p) > 0 (the scale): the
+ * step is taken on p = log s with gradient s * d/ds, and s = exp(p) is written back,
+ * which is the parameterisation the radius learning rate refers to. */
+#define SGAD_ADAM_PLAIN 0
+#define SGAD_ADAM_LOG 1
 sgad_status sgad_adam_step(int64_t n, float *param, const float *grad, float *m, float *v,
                            float lr, float beta1, float beta2, float eps, int32_t step,
-                           void *stream);
+                           int32_t mode, void *stream);
+
+/* One tensor of a multi-tensor Adam step (device pointers, n elements each). */
+typedef struct {
+    float *param;
+    const float *grad;
+    float *m;
+    float *v;
+    int64_t n;
+    float lr;
+    int32_t mode;                /* SGAD_ADAM_PLAIN or SGAD_ADAM_LOG */
+} sgad_adam_tensor;
+
+#define SGAD_ADAM_MAX_TENSORS 256
+
+/* The Adam step above over up to SGAD_ADAM_MAX_TENSORS tensors in one launch. The step
+ * number lives in device memory: *step_counter (a device int32, 0 before the first step)
+ * counts the steps taken; this call uses step = *step_counter + 1 and then increments
+ * it, so the call can be captured once in a CUDA graph and replayed. */
+sgad_status sgad_adam_step_multi(int32_t n_tensors, const sgad_adam_tensor *tensors, float beta1,
+                                 float beta2, float eps, int32_t *step_counter, void *stream);
 
 #ifdef __cplusplus
 }

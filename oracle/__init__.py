@@ -101,14 +101,14 @@ def lib():
             l.orc_render.argtypes = [P, C.c_int32, P, C.c_int32, P, P]
             l.orc_render_pixels.argtypes = [P, C.c_int32, P, C.c_int32, P, C.c_int64, P, P, P, P, P, P,
                                             P, P, P]
-            l.orc_backward.argtypes = [P, C.c_int32, P, C.c_int32, P, P, P]
-            l.orc_backward_gaussians.argtypes = [P, C.c_int32, P, C.c_int32, P, P, C.c_int64, P, P]
+            l.orc_backward.argtypes = [P, C.c_int32, P, C.c_int32, P, P, P, P]
+            l.orc_backward_gaussians.argtypes = [P, C.c_int32, P, C.c_int32, P, P, C.c_int64, P, P, P]
             l.orc_decision_hash.restype = C.c_uint64
             l.orc_decision_hash.argtypes = [P, C.c_int32, P, C.c_int32, P]
             l.orc_l1_loss.restype = C.c_double
             l.orc_l1_loss.argtypes = [C.c_int32, P, P, P, P, P, C.c_double, C.c_double, P, P]
             l.orc_adam.argtypes = [C.c_int64, P, P, P, P, C.c_double, C.c_double, C.c_double,
-                                   C.c_double, C.c_int32]
+                                   C.c_double, C.c_int32, C.c_int32]
             _lib = l
     return _lib
 
@@ -217,7 +217,8 @@ def _image_grads(scene, grads_in):
 def backward(scene, grads_in, o: Opts = None):
     """Adjoint of the render. grads_in: per view dict with 'rgb' (3,H,W), 'depth',
     'alpha' (missing entries are zero). Returns per keyframe dict d_offset, d_rgb,
-    d_logit, d_scale (zeros for fixed keyframes)."""
+    d_logit, d_scale (zeros for fixed keyframes) and 'near' (H, W): Gaussians reached by a
+    pixel with a near decision, whose gradient FP32 may legitimately change."""
     o = o or opts()
     inp = _Inputs(scene)
     gi, keep = _image_grads(scene, grads_in)
@@ -228,23 +229,30 @@ def backward(scene, grads_in, o: Opts = None):
                  d_scale=np.zeros((h, w)))
         outs.append(d)
         gk[i] = KfGrads(*[_ptr(d[q]) for q in ("d_offset", "d_rgb", "d_logit", "d_scale")])
-    lib().orc_backward(inp.kfs, inp.n_kf, inp.views, inp.n_views, C.byref(o), gi, gk)
+    near = np.zeros(num_gaussians(scene), np.uint8)
+    lib().orc_backward(inp.kfs, inp.n_kf, inp.views, inp.n_views, C.byref(o), gi, gk, _ptr(near))
+    base = 0
+    for d, k in zip(outs, scene.keyframes):
+        n = k.cam.width * k.cam.height
+        d["near"] = near[base:base + n].reshape(k.cam.height, k.cam.width).astype(bool)
+        base += n
     del keep
     return outs
 
 
-def backward_gaussians(scene, grads_in, sel, o: Opts = None) -> np.ndarray:
-    """Adjoint for selected global Gaussian indices: (n, 6) array of (d_offset, d_r, d_g,
-    d_b, d_logit, d_scale)."""
+def backward_gaussians(scene, grads_in, sel, o: Opts = None):
+    """Adjoint for selected global Gaussian indices: ((n, 6) array of (d_offset, d_r, d_g,
+    d_b, d_logit, d_scale), (n,) bool near flags as in backward())."""
     o = o or opts()
     inp = _Inputs(scene)
     gi, keep = _image_grads(scene, grads_in)
     s = np.ascontiguousarray(sel, np.int64)
     out = np.zeros((s.shape[0], 6))
+    near = np.zeros(s.shape[0], np.uint8)
     lib().orc_backward_gaussians(inp.kfs, inp.n_kf, inp.views, inp.n_views, C.byref(o), gi, s.shape[0],
-                                 _ptr(s), _ptr(out))
+                                 _ptr(s), _ptr(out), _ptr(near))
     del keep
-    return out
+    return out, near.astype(bool)
 
 
 def decision_hash(scene, o: Opts = None) -> int:
@@ -276,9 +284,10 @@ def l1_loss(scene, renders):
     return loss, grads
 
 
-def adam(param, grad, m, v, lr, beta1=0.9, beta2=0.999, eps=1e-15, step=1):
-    """One FP64 Adam step in place on float64 arrays."""
+def adam(param, grad, m, v, lr, beta1=0.9, beta2=0.999, eps=1e-15, step=1, log_param=False):
+    """One FP64 Adam step in place on float64 arrays (log_param: param holds exp(p))."""
     arrs = [param, grad, m, v]
     for a in arrs:
         assert a.dtype == np.float64 and a.flags.c_contiguous
-    lib().orc_adam(param.size, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), lr, beta1, beta2, eps, step)
+    lib().orc_adam(param.size, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), lr, beta1, beta2, eps, step,
+                   int(bool(log_param)))

@@ -313,6 +313,7 @@ typedef struct {
     int32_t n_contrib;
     int32_t near;
     int32_t n_rec;
+    int32_t end;        /* list position where the walk ended (the stop entry, or the length) */
     uint64_t hash;
 } walk_out;
 
@@ -332,8 +333,9 @@ static void walk_pixel(const orc_proj *proj, const list_entry *list, int64_t n, 
     const double m = opt->margin;
     double T = 1.0, C[3] = {0, 0, 0}, Dp = 0.0, A = 0.0;
     int32_t last = -1, near = 0, nrec = 0;
+    int64_t i;
     uint64_t h = 1469598103934665603ull;
-    for (int64_t i = 0; i < n; ++i) {
+    for (i = 0; i < n; ++i) {
         const orc_proj *P = &proj[list[i].g];
         const double dx = P->p[0] - qx, dy = P->p[1] - qy;
         const double qa = 0.5 * (P->conic[0] * dx * dx + P->conic[2] * dy * dy);
@@ -372,6 +374,7 @@ static void walk_pixel(const orc_proj *proj, const list_entry *list, int64_t n, 
     out->n_contrib = last + 1;
     out->near = near;
     out->n_rec = nrec;
+    out->end = (int32_t)i;
     out->hash = h;
 }
 
@@ -601,7 +604,8 @@ static void chain_params(const orc_kf *kf, int64_t j, const orc_cam *view, const
  * per-entry contributions are merged in tile order, so the sum is deterministic. */
 static void view_adjoint_tiles(const orc_proj *proj, const tile_lists *L, const orc_cam *view,
                                const orc_opts *opt, const orc_image_grads *gi, const int32_t *tiles,
-                               int32_t n_tiles, const int64_t *slot, double (*g2d)[G_N])
+                               int32_t n_tiles, const int64_t *slot, double (*g2d)[G_N],
+                               const uint8_t *near_img, uint8_t *near_out)
 {
     const int32_t W = view->width, H = view->height;
     const int64_t hw = (int64_t)W * H;
@@ -609,12 +613,14 @@ static void view_adjoint_tiles(const orc_proj *proj, const tile_lists *L, const 
     for (int32_t c0 = 0; c0 < n_tiles; c0 += chunk) {
         const int32_t c1 = c0 + chunk < n_tiles ? c0 + chunk : n_tiles;
         double (**acc)[G_N] = (double (**)[G_N])calloc((size_t)(c1 - c0), sizeof(*acc));
+        uint8_t **nacc = (uint8_t **)calloc((size_t)(c1 - c0), sizeof(*nacc));
 #pragma omp parallel for schedule(dynamic, 1)
         for (int32_t ci = c0; ci < c1; ++ci) {
             const int32_t t = tiles[ci];
             const int64_t n = L->off[t + 1] - L->off[t];
             const list_entry *list = L->e + L->off[t];
             double (*a)[G_N] = (double (*)[G_N])calloc((size_t)(n + 1), sizeof(*a));
+            uint8_t *nf = (uint8_t *)calloc((size_t)(n + 1), 1);
             double (*pa)[G_N] = (double (*)[G_N])calloc((size_t)(n + 1), sizeof(*pa));
             walk_rec *rec = (walk_rec *)malloc(sizeof(walk_rec) * (size_t)(n + 1));
             const int32_t tx = t % L->ntx, ty = t / L->ntx;
@@ -628,10 +634,22 @@ static void view_adjoint_tiles(const orc_proj *proj, const tile_lists *L, const 
                     pixel_adjoint(proj, rec, o.n_rec, o.T, gC, gi->d_depth[pix], gi->d_alpha[pix], opt, pa);
                     for (int32_t r = 0; r < o.n_rec; ++r)
                         for (int q = 0; q < G_N; ++q) a[rec[r].pos][q] += pa[r][q];
+                    if (o.near || (near_img && near_img[pix])) {
+                        /* entries up to the stop whose alpha is at or near the floor here */
+                        const int64_t end = o.end < n ? o.end + 1 : n;
+                        for (int64_t i = 0; i < end; ++i) {
+                            const orc_proj *P = &proj[list[i].g];
+                            const double dx = P->p[0] - x, dy = P->p[1] - y;
+                            const double power =
+                                -0.5 * (P->conic[0] * dx * dx + P->conic[2] * dy * dy) - P->conic[1] * dx * dy;
+                            if (P->o * exp(power) >= ALPHA_FLOOR * (1.0 - opt->margin)) nf[i] = 1;
+                        }
+                    }
                 }
             free(rec);
             free(pa);
             acc[ci - c0] = a;
+            nacc[ci - c0] = nf;
         }
         for (int32_t ci = c0; ci < c1; ++ci) {
             const int32_t t = tiles[ci];
@@ -641,20 +659,25 @@ static void view_adjoint_tiles(const orc_proj *proj, const tile_lists *L, const 
                 const int64_t s = slot ? slot[list[i].g] : (int64_t)list[i].g;
                 if (s < 0) continue;
                 for (int q = 0; q < G_N; ++q) g2d[s][q] += acc[ci - c0][i][q];
+                if (near_out && nacc[ci - c0][i]) near_out[s] = 1;
             }
             free(acc[ci - c0]);
+            free(nacc[ci - c0]);
         }
         free(acc);
+        free(nacc);
     }
 }
 
 int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int32_t n_views,
-                     const orc_opts *opt, const orc_image_grads *grad_in, orc_kf_grads *grads)
+                     const orc_opts *opt, const orc_image_grads *grad_in, orc_kf_grads *grads,
+                     uint8_t *near_gauss)
 {
     const int64_t nG = orc_num_gaussians(kfs, n_kf);
     orc_proj *proj = (orc_proj *)malloc(sizeof(orc_proj) * (size_t)nG);
     double (*g2d)[G_N] = (double (*)[G_N])malloc(sizeof(*g2d) * (size_t)nG);
     double (*gp)[6] = (double (*)[6])calloc((size_t)nG, sizeof(*gp));
+    if (near_gauss) memset(near_gauss, 0, (size_t)nG);
     for (int32_t k = 0; k < n_views; ++k) {
         orc_project(kfs, n_kf, &views[k], opt, proj);
         tile_lists L;
@@ -662,8 +685,11 @@ int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int3
         const int32_t nt = L.ntx * L.nty;
         int32_t *tiles = (int32_t *)malloc(sizeof(int32_t) * (size_t)nt);
         for (int32_t t = 0; t < nt; ++t) tiles[t] = t;
+        uint8_t *near_img = (uint8_t *)calloc((size_t)views[k].width * views[k].height, 1);
+        mark_binning_near(proj, nG, &views[k], opt, near_img);
         memset(g2d, 0, sizeof(*g2d) * (size_t)nG);
-        view_adjoint_tiles(proj, &L, &views[k], opt, &grad_in[k], tiles, nt, NULL, g2d);
+        view_adjoint_tiles(proj, &L, &views[k], opt, &grad_in[k], tiles, nt, NULL, g2d, near_img, near_gauss);
+        free(near_img);
         for (int64_t g = 0; g < nG; ++g) {
             if (!(proj[g].ntiles > 0)) continue;
             int64_t j;
@@ -700,8 +726,9 @@ int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int3
 int32_t orc_backward_gaussians(const orc_kf *kfs, int32_t n_kf, const orc_cam *views,
                                int32_t n_views, const orc_opts *opt,
                                const orc_image_grads *grad_in, int64_t n_sel,
-                               const int64_t *sel, double *out)
+                               const int64_t *sel, double *out, uint8_t *near_sel)
 {
+    if (near_sel) memset(near_sel, 0, (size_t)n_sel);
     const int64_t nG = orc_num_gaussians(kfs, n_kf);
     orc_proj *proj = (orc_proj *)malloc(sizeof(orc_proj) * (size_t)nG);
     int64_t *slot = (int64_t *)malloc(sizeof(int64_t) * (size_t)nG);
@@ -726,7 +753,10 @@ int32_t orc_backward_gaussians(const orc_kf *kfs, int32_t n_kf, const orc_cam *v
         for (int32_t t = 0; t < nt; ++t)
             if (want[t]) tiles[nw++] = t;
         memset(g2d, 0, sizeof(*g2d) * (size_t)(n_sel + 1));
-        view_adjoint_tiles(proj, &L, &views[k], opt, &grad_in[k], tiles, nw, slot, g2d);
+        uint8_t *near_img = (uint8_t *)calloc((size_t)views[k].width * views[k].height, 1);
+        mark_binning_near(proj, nG, &views[k], opt, near_img);
+        view_adjoint_tiles(proj, &L, &views[k], opt, &grad_in[k], tiles, nw, slot, g2d, near_img, near_sel);
+        free(near_img);
         for (int64_t s = 0; s < n_sel; ++s) {
             const int64_t g = sel[s];
             if (!(proj[g].ntiles > 0)) continue;
@@ -814,12 +844,15 @@ double orc_l1_loss(int32_t n_views, const orc_cam *views, const double *const *r
 /* m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;
  * p <- p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps) */
 void orc_adam(int64_t n, double *param, const double *grad, double *m, double *v, double lr,
-              double beta1, double beta2, double eps, int32_t step)
+              double beta1, double beta2, double eps, int32_t step, int32_t log_param)
 {
     const double c1 = 1.0 - pow(beta1, step), c2 = 1.0 - pow(beta2, step);
     for (int64_t i = 0; i < n; ++i) {
-        m[i] = beta1 * m[i] + (1.0 - beta1) * grad[i];
-        v[i] = beta2 * v[i] + (1.0 - beta2) * grad[i] * grad[i];
-        param[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+        const double g = log_param ? grad[i] * param[i] : grad[i];
+        m[i] = beta1 * m[i] + (1.0 - beta1) * g;
+        v[i] = beta2 * v[i] + (1.0 - beta2) * g * g;
+        const double p = log_param ? log(param[i]) : param[i];
+        const double q = p - lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+        param[i] = log_param ? exp(q) : q;
     }
 }

@@ -143,17 +143,22 @@ int32_t orc_render_pixels(const orc_kf *kfs, int32_t n_kf, const orc_cam *views,
 
 /* Adjoint: gradients of L = sum_views <grad_in, (rgb, depth, alpha)> with respect to the
  * offset, colour, opacity logit and scale of every learnable keyframe. Overwrites the
- * gradient arrays of learnable keyframes; fixed keyframes are not touched. */
+ * gradient arrays of learnable keyframes; fixed keyframes are not touched.
+ * near_gauss (optional, one byte per Gaussian, global index) is set to 1 for every
+ * Gaussian whose alpha passes (or nearly passes) the floor at a pixel with a near
+ * decision: its gradient includes a term FP32 may legitimately drop or add. */
 int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int32_t n_views,
-                     const orc_opts *opt, const orc_image_grads *grad_in, orc_kf_grads *grads);
+                     const orc_opts *opt, const orc_image_grads *grad_in, orc_kf_grads *grads,
+                     uint8_t *near_gauss);
 
 /* Adjoint restricted to a list of Gaussians (global indices): out[n][6] =
  * (d_offset, d_r, d_g, d_b, d_logit, d_scale). Only the tiles these Gaussians touch are
- * walked, so it runs on full-size scenes. */
+ * walked, so it runs on full-size scenes. near_sel (optional, n bytes) as near_gauss
+ * above for the selected Gaussians. */
 int32_t orc_backward_gaussians(const orc_kf *kfs, int32_t n_kf, const orc_cam *views,
                                int32_t n_views, const orc_opts *opt,
                                const orc_image_grads *grad_in, int64_t n_sel,
-                               const int64_t *sel, double *out);
+                               const int64_t *sel, double *out, uint8_t *near_sel);
 
 /* Fingerprint of every discrete decision of a forward pass (binning and, per pixel, the
  * accepted entries and the stopping point). Two parameter sets with equal fingerprints
@@ -169,9 +174,11 @@ double orc_l1_loss(int32_t n_views, const orc_cam *views, const double *const *r
                    const double *const *target_depth, double rgb_w, double depth_w,
                    double *const *d_rgb, double *const *d_depth);
 
-/* One Adam step (PyTorch convention, bias-corrected) on n parameters, in FP64. */
+/* One Adam step (PyTorch convention, bias-corrected) on n parameters, in FP64. With
+ * log_param != 0 the array holds s = exp(p): the step is taken on p = log s with
+ * gradient s * grad, and exp(p) is written back. */
 void orc_adam(int64_t n, double *param, const double *grad, double *m, double *v, double lr,
-              double beta1, double beta2, double eps, int32_t step);
+              double beta1, double beta2, double eps, int32_t step, int32_t log_param);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,8 @@ SGAD_MAX_VIEWS = 64
 
 EXPORTS = ["sgad_default_options", "sgad_create", "sgad_destroy", "sgad_last_error", "sgad_workspace_size",
            "sgad_count_keys", "sgad_forward", "sgad_backward", "sgad_check", "sgad_state", "sgad_read_stats",
-           "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_adam_step"]
+           "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_adam_step",
+           "sgad_adam_step_multi"]
 SGAD_NUM_STAGES = 6
 STAGE_NAMES = ["binning", "emit", "sort", "composite_fwd", "composite_bwd", "finalize"]
 
@@ -69,6 +70,11 @@ class sgad_state_view(C.Structure):
                 ("n_contrib", C.c_void_p), ("n_tiles", C.c_int32), ("n_pixels", C.c_int64)]
 
 
+class sgad_adam_tensor(C.Structure):
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p),
+                ("n", C.c_int64), ("lr", C.c_float), ("mode", C.c_int32)]
+
+
 class sgad_stats(C.Structure):
     _fields_ = [("n_keys", C.c_int64), ("keys_needed", C.c_int64), ("n_pairs", C.c_int64),
                 ("n_evals", C.c_int64)]
@@ -108,7 +114,8 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         "sgad_profile_enable": (st, [P, I32]),
         "sgad_profile_read": (st, [P, P]),
         "sgad_l1_loss_grad": (st, [I32, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P]),
-        "sgad_adam_step": (st, [I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I32, P]),
+        "sgad_adam_step": (st, [I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I32, I32, P]),
+        "sgad_adam_step_multi": (st, [I32, P, C.c_float, C.c_float, C.c_float, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(l, name)
@@ -207,10 +214,14 @@ def sgad_l1_loss_grad(views, rendered, target_rgb, target_depth, rgb_weight, dep
           float(depth_weight), d_rgb, d_depth, loss_accum, valid_count, stream)
 
 
+SGAD_ADAM_PLAIN = 0
+SGAD_ADAM_LOG = 1
+
+
 def sgad_adam_step(n: int, param: int, grad: int, m: int, v: int, lr: float, beta1: float, beta2: float,
-                   eps: float, step: int, stream: int) -> None:
+                   eps: float, step: int, mode: int, stream: int) -> None:
     _call("sgad_adam_step", int(n), param, grad, m, v, float(lr), float(beta1), float(beta2), float(eps),
-          int(step), stream)
+          int(step), int(mode), stream)
 
 
 def ptr_array(ptrs):
@@ -219,3 +230,9 @@ def ptr_array(ptrs):
     for i, p in enumerate(ptrs):
         arr[i] = p or None
     return arr
+
+
+def sgad_adam_step_multi(tensors, beta1: float, beta2: float, eps: float, step_counter: int, stream: int) -> None:
+    """tensors: a ctypes array of sgad_adam_tensor; step_counter: device int32 address."""
+    _call("sgad_adam_step_multi", len(tensors), tensors, float(beta1), float(beta2), float(eps), step_counter,
+          stream)

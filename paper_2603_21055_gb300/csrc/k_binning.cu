@@ -125,7 +125,10 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t *__restrict__ cnt,
         hdr->n_keys = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
         hdr->needed = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
         hdr->overflow = total > key_cap ? 1u : 0u;
-        if (total > key_cap) record_error(hdr, SGAD_ERR_KEY_OVERFLOW);
+        if (total > key_cap) {
+            record_error(hdr, SGAD_ERR_KEY_OVERFLOW);
+            atomicMax(&hdr->sticky_needed, (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull));
+        }
     }
 }
 
@@ -168,10 +171,12 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Scene sc, 
             base = __shfl_sync(full, base, leader);
             if (tile != kInvalidTile) {
                 const uint32_t slot = off[tile] + base + __popc(peers & lanemask_lt());
-                if (slot < off[tile + 1])
+                if (slot < off[tile + 1]) {
                     entries[slot] = key;
-                else
+                } else {
                     atomicExch(&hdr->emit_overrun, 1u);
+                    atomicExch(&hdr->sticky_overrun, 1u);
+                }
             }
         }
     }

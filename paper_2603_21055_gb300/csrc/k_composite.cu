@@ -136,12 +136,24 @@ __global__ void __launch_bounds__(kBlock) k_composite_fwd(const __grid_constant_
     }
 }
 
-// Butterfly sum over the warp; every lane ends with the total.
-__device__ __forceinline__ float warp_sum(float x)
+// Reduce-scatter of 16 per-lane values over the warp in 16 shuffles (instead of 80 for
+// 16 butterfly all-reductions): at each level a lane sends the half of its slots its
+// partner keeps and adds the partner's copy of the half it keeps. Afterwards every lane
+// returns the warp total of slot (lane >> 1).
+__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
+    for (int lvl = 0; lvl < 4; ++lvl) {
+        const int half = 8 >> lvl, mask = 16 >> lvl;
+        const bool upper = (lane & mask) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? v[i] : v[i + half];
+            const float keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, mask);
+        }
+    }
+    return v[0] + __shfl_xor_sync(kFull, v[0], 1);
 }
 
 template <int TW, int TH>
@@ -225,9 +237,9 @@ __global__ void __launch_bounds__(kBlock) k_composite_bwd(const __grid_constant_
                     const int bit = 31 - __clz(mask);
                     mask &= ~(1u << bit);
                     const int jj = c0 + bit;
-                    float val[10];
+                    float val[16];
 #pragma unroll
-                    for (int q = 0; q < 10; ++q) val[q] = 0.f;
+                    for (int q = 0; q < 16; ++q) val[q] = 0.f;
                     bool contrib = false;
                     if (b0 + jj < nc) {
                         const Staged st = sm[jj];
@@ -262,15 +274,9 @@ __global__ void __launch_bounds__(kBlock) k_composite_bwd(const __grid_constant_
                         }
                     }
                     if (__any_sync(kFull, contrib)) {
-#pragma unroll
-                        for (int q = 0; q < 10; ++q) val[q] = warp_sum(val[q]);
-                        if (lane < 10) {
-                            float mine = val[0];
-#pragma unroll
-                            for (int q = 1; q < 10; ++q)
-                                if (lane == q) mine = val[q];
-                            atomicAdd(&acc[jj][lane], mine);
-                        }
+                        const float total = warp_reduce_scatter16(val, lane);
+                        const int slot = lane >> 1;
+                        if ((lane & 1) == 0 && slot < 10) atomicAdd(&acc[jj][slot], total);
                     }
                 }
             }

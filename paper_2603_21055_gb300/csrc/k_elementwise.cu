@@ -56,41 +56,69 @@ __device__ __forceinline__ float block_sum(float x, float *red)
     return t;
 }
 
-__global__ void k_count_valid(const float *__restrict__ td, size_t hw, uint32_t *count)
+// All views of one loss call; every view owns a contiguous range of CTAs.
+constexpr int kLossChunk = 4096;    // pixels per CTA
+
+struct LossView {
+    const float *rgb, *depth, *trgb, *tdep;
+    float *drgb, *ddep;
+    uint32_t *nvalid;
+    uint32_t hw;
+    uint32_t block0;
+};
+
+struct LossBatch {
+    int32_t n;
+    float wrgb, wdep;
+    LossView v[SGAD_MAX_VIEWS];
+};
+
+__device__ __forceinline__ int loss_view(const LossBatch &B)
 {
-    __shared__ float red[32];
-    float c = 0.f;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < hw; i += (size_t)gridDim.x * blockDim.x)
-        c += td[i] > 0.0f ? 1.0f : 0.0f;
-    const float t = block_sum(c, red);
-    if (threadIdx.x == 0 && t > 0.f) atomicAdd(count, (uint32_t)t);
+    int k = 0;
+    for (int i = 1; i < B.n; ++i)
+        if (B.v[i].block0 <= blockIdx.x) k = i;
+    return k;
 }
 
-__global__ void k_l1_grad(const float *__restrict__ rgb, const float *__restrict__ depth,
-                          const float *__restrict__ trgb, const float *__restrict__ tdep, size_t hw, float wrgb,
-                          float wdep, const uint32_t *__restrict__ nvalid, float *__restrict__ d_rgb,
-                          float *__restrict__ d_depth, float *loss)
+__global__ void __launch_bounds__(256) k_count_valid(const __grid_constant__ LossBatch B)
 {
     __shared__ float red[32];
-    const float inv_rgb = wrgb / (3.0f * (float)hw);
-    const uint32_t nv = nvalid ? *nvalid : 0u;
-    const float inv_dep = nv > 0 ? wdep / (float)nv : 0.0f;
+    const LossView &v = B.v[loss_view(B)];
+    const size_t base = (size_t)(blockIdx.x - v.block0) * kLossChunk;
+    const size_t end = base + kLossChunk < v.hw ? base + kLossChunk : v.hw;
+    float c = 0.f;
+    for (size_t i = base + threadIdx.x; i < end; i += blockDim.x) c += v.tdep[i] > 0.0f ? 1.0f : 0.0f;
+    const float t = block_sum(c, red);
+    if (threadIdx.x == 0 && t > 0.f) atomicAdd(v.nvalid, (uint32_t)t);
+}
+
+__global__ void __launch_bounds__(256) k_l1_grad(const __grid_constant__ LossBatch B, float *loss)
+{
+    __shared__ float red[32];
+    const LossView &v = B.v[loss_view(B)];
+    const size_t hw = v.hw;
+    const size_t base = (size_t)(blockIdx.x - v.block0) * kLossChunk;
+    const size_t end = base + kLossChunk < hw ? base + kLossChunk : hw;
+    const float inv_rgb = B.wrgb / (3.0f * (float)hw);
+    const uint32_t nv = v.nvalid ? *v.nvalid : 0u;
+    const float inv_dep = nv > 0 ? B.wdep / (float)nv : 0.0f;
     float l = 0.f;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < hw; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = base + threadIdx.x; i < end; i += blockDim.x) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float d = rgb[c * hw + i] - trgb[c * hw + i];
+            const float d = v.rgb[c * hw + i] - v.trgb[c * hw + i];
             l += fabsf(d) * inv_rgb;
-            d_rgb[c * hw + i] = sgnf(d) * inv_rgb;
+            v.drgb[c * hw + i] = sgnf(d) * inv_rgb;
         }
-        if (d_depth) {
+        if (v.ddep) {
             float gd = 0.f;
-            if (tdep && tdep[i] > 0.0f && inv_dep > 0.0f) {
-                const float d = depth[i] - tdep[i];
+            if (v.tdep && v.tdep[i] > 0.0f && inv_dep > 0.0f) {
+                const float d = v.depth[i] - v.tdep[i];
                 l += fabsf(d) * inv_dep;
                 gd = sgnf(d) * inv_dep;
             }
-            d_depth[i] = gd;
+            v.ddep[i] = gd;
         }
     }
     if (loss) {
@@ -99,38 +127,137 @@ __global__ void k_l1_grad(const float *__restrict__ rgb, const float *__restrict
     }
 }
 
-void launch_l1(const float *rgb, const float *depth, const float *trgb, const float *tdep, size_t hw, float wrgb,
-               float wdep, uint32_t *nvalid, float *d_rgb, float *d_depth, float *loss, cudaStream_t st)
+// views: per view (rgb, depth, target rgb, target depth or NULL, d_rgb, d_depth or NULL,
+// valid counter or NULL, pixel count).
+void launch_l1_batch(int n, const float *const *rgb, const float *const *depth, const float *const *trgb,
+                     const float *const *tdep, float *const *drgb, float *const *ddep, uint32_t *nvalid,
+                     const uint32_t *hw, float wrgb, float wdep, float *loss, cudaStream_t st)
 {
-    const int threads = 256;
-    int blocks = (int)((hw + threads - 1) / threads);
-    if (blocks > 4 * 152) blocks = 4 * 152;
-    if (blocks < 1) blocks = 1;
-    const bool use_depth = tdep && d_depth && wdep != 0.0f;
-    if (use_depth) k_count_valid<<<blocks, threads, 0, st>>>(tdep, hw, nvalid);
-    k_l1_grad<<<blocks, threads, 0, st>>>(rgb, depth, trgb, use_depth ? tdep : nullptr, hw, wrgb, wdep,
-                                          use_depth ? nvalid : nullptr, d_rgb, d_depth, loss);
+    LossBatch B;
+    B.n = n;
+    B.wrgb = wrgb;
+    B.wdep = wdep;
+    uint32_t blocks = 0;
+    const bool use_depth = wdep != 0.0f && tdep && ddep && nvalid;
+    for (int i = 0; i < n; ++i) {
+        LossView &v = B.v[i];
+        v.rgb = rgb[i];
+        v.depth = depth ? depth[i] : nullptr;
+        v.trgb = trgb[i];
+        v.tdep = use_depth ? tdep[i] : nullptr;
+        v.drgb = drgb[i];
+        v.ddep = ddep ? ddep[i] : nullptr;
+        v.nvalid = use_depth ? nvalid + i : nullptr;
+        v.hw = hw[i];
+        v.block0 = blocks;
+        blocks += (hw[i] + kLossChunk - 1) / kLossChunk;
+    }
+    if (use_depth) k_count_valid<<<blocks, 256, 0, st>>>(B);
+    k_l1_grad<<<blocks, 256, 0, st>>>(B, loss);
 }
 
+template <bool kLog>
 __global__ void k_adam(int64_t n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                        float *__restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
+        const float pi = p[i];
+        const float gi = kLog ? g[i] * pi : g[i];     // d/d(log s) = s d/ds
         const float mi = b1 * m[i] + (1.0f - b1) * gi;
         const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
         m[i] = mi;
         v[i] = vi;
-        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        const float step = lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = kLog ? expf(logf(pi) - step) : pi - step;
     }
 }
 
+// ---------------------------------------------------------- multi-tensor Adam
+
+constexpr int kAdamChunk = 4096;    // elements per CTA
+
+struct AdamDesc {
+    float *p;
+    const float *g;
+    float *m, *v;
+    int64_t n;
+    float lr;
+    int32_t mode;
+    int64_t block0;                 // first CTA of this tensor
+};
+
+struct AdamBatch {
+    int32_t n;
+    float b1, b2, eps;
+    AdamDesc t[SGAD_ADAM_MAX_TENSORS];
+};
+
+__global__ void __launch_bounds__(256) k_adam_multi(const __grid_constant__ AdamBatch B, const int32_t *step)
+{
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {                 // last tensor whose first CTA <= blockIdx.x
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.t[mid].block0 <= (int64_t)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const AdamDesc &d = B.t[lo];
+    const float s = (float)(*step + 1);
+    const float c1 = 1.0f - powf(B.b1, s), c2 = 1.0f - powf(B.b2, s);
+    const int64_t base = ((int64_t)blockIdx.x - d.block0) * kAdamChunk;
+    const int64_t end = base + kAdamChunk < d.n ? base + kAdamChunk : d.n;
+    for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x) {
+        const float pi = d.p[i];
+        const float gi = d.mode == SGAD_ADAM_LOG ? d.g[i] * pi : d.g[i];
+        const float mi = B.b1 * d.m[i] + (1.0f - B.b1) * gi;
+        const float vi = B.b2 * d.v[i] + (1.0f - B.b2) * gi * gi;
+        d.m[i] = mi;
+        d.v[i] = vi;
+        const float stp = d.lr * (mi / c1) / (sqrtf(vi / c2) + B.eps);
+        d.p[i] = d.mode == SGAD_ADAM_LOG ? expf(logf(pi) - stp) : pi - stp;
+    }
+}
+
+__global__ void k_increment(int32_t *c) { *c += 1; }
+
+cudaError_t launch_adam_multi(int n_t, const sgad_adam_tensor *t, float b1, float b2, float eps, int32_t *step,
+                              cudaStream_t st)
+{
+    AdamBatch B;
+    B.n = n_t;
+    B.b1 = b1;
+    B.b2 = b2;
+    B.eps = eps;
+    int64_t blocks = 0;
+    for (int i = 0; i < n_t; ++i) {
+        AdamDesc &d = B.t[i];
+        d.p = t[i].param;
+        d.g = t[i].grad;
+        d.m = t[i].m;
+        d.v = t[i].v;
+        d.n = t[i].n;
+        d.lr = t[i].lr;
+        d.mode = t[i].mode;
+        d.block0 = blocks;
+        blocks += (t[i].n + kAdamChunk - 1) / kAdamChunk;
+    }
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    if (blocks > 0) k_adam_multi<<<(unsigned)blocks, 256, 0, st>>>(B, step);
+    k_increment<<<1, 1, 0, st>>>(step);
+    return cudaGetLastError();
+}
+
 void launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
-                 float c1, float c2, cudaStream_t st)
+                 float c1, float c2, bool log_mode, cudaStream_t st)
 {
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks > 0) k_adam<<<(unsigned)blocks, 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2);
+    if (blocks <= 0) return;
+    if (log_mode)
+        k_adam<true><<<(unsigned)blocks, 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2);
+    else
+        k_adam<false><<<(unsigned)blocks, 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2);
 }
 
 }  // namespace sgad

@@ -133,9 +133,18 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *__r
 cudaError_t launch_sort_tiles(const uint32_t *off, uint64_t *entries, uint64_t *alt, int n_tiles, int cap,
                               const WsHeader *hdr, cudaStream_t st)
 {
-    const size_t smem = (size_t)cap * 2 * sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // Raise the kernel's dynamic shared-memory limit once per device and size (outside
+    // any stream capture, which only replays launches).
+    static int configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)cap * 2 * sizeof(uint64_t);
+    if (dev < 0 || dev >= 64 || configured[dev] < (int)smem) {
+        e = cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) configured[dev] = (int)smem;
+    }
     if (n_tiles > 0) k_sort_tiles<<<n_tiles, kSortThreads, smem, st>>>(off, entries, alt, cap, hdr);
     return cudaSuccess;
 }

@@ -16,10 +16,11 @@ cudaError_t launch_sort_tiles(const uint32_t *, uint64_t *, uint64_t *, int, int
 void launch_composite(bool, const Scene &, const World *, const uint32_t *, const uint64_t *, float *, uint32_t *,
                       float4 *, WsHeader *, cudaStream_t);
 void launch_finalize(const Scene &, const World *, const float4 *, cudaStream_t);
-void launch_l1(const float *, const float *, const float *, const float *, size_t, float, float, uint32_t *, float *,
-               float *, float *, cudaStream_t);
-void launch_adam(int64_t, float *, const float *, float *, float *, float, float, float, float, float, float,
+void launch_l1_batch(int, const float *const *, const float *const *, const float *const *, const float *const *,
+                     float *const *, float *const *, uint32_t *, const uint32_t *, float, float, float *, cudaStream_t);
+void launch_adam(int64_t, float *, const float *, float *, float *, float, float, float, float, float, float, bool,
                  cudaStream_t);
+cudaError_t launch_adam_multi(int, const sgad_adam_tensor *, float, float, float, int32_t *, cudaStream_t);
 }  // namespace sgad
 
 using namespace sgad;
@@ -188,9 +189,9 @@ sgad_status last_launch(const char *what)
 }
 
 // Projection, binning count and scan: the part shared by sgad_count_keys and sgad_forward.
-sgad_status run_binning_count(const Scene &sc, const Ws &ws, int64_t key_cap, cudaStream_t st)
+sgad_status run_binning_count(const Scene &sc, const Ws &ws, int64_t key_cap, bool clear_sticky, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(ws.hdr(), 0, sizeof(WsHeader), st);
+    cudaError_t e = cudaMemsetAsync(ws.hdr(), 0, clear_sticky ? sizeof(WsHeader) : kHeaderPerCall, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.tile_cnt(), 0, ((size_t)sc.n_tiles + 1) * 4, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     launch_project_count(sc, ws.world(), ws.tile_cnt(), st);
@@ -322,7 +323,7 @@ sgad_status sgad_count_keys(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_k
     if (!s) s = get_ws(sc, n_pix, workspace, ws_bytes, 0, ws);
     if (s) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    s = run_binning_count(sc, ws, 0xfffffffell, st);
+    s = run_binning_count(sc, ws, 0xfffffffell, true, st);
     if (s) return s;
     WsHeader h;
     cudaError_t e = cudaMemcpyAsync(&h, ws.hdr(), sizeof(h), cudaMemcpyDeviceToHost, st);
@@ -353,7 +354,7 @@ sgad_status sgad_forward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf, 
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     mark(ctx, 0, st);
-    s = run_binning_count(sc, ws, key_capacity, st);
+    s = run_binning_count(sc, ws, key_capacity, false, st);
     if (s) return s;
     mark(ctx, 1, st);
     launch_emit(sc, ws.world(), ws.tile_off(), ws.tile_cnt(), ws.keys(), ws.hdr(), st);
@@ -415,17 +416,17 @@ sgad_status sgad_check(sgad_ctx *ctx, void *workspace, size_t ws_bytes, int64_t 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "sgad_check");
     if (n_keys) *n_keys = h.n_keys;
-    if (keys_needed) *keys_needed = h.needed;
-    if (h.err != 0 || h.emit_overrun != 0) {
-        const int zero = 0;
-        e = cudaMemcpyAsync(reinterpret_cast<char *>(workspace) + offsetof(WsHeader, err), &zero, sizeof(zero),
-                            cudaMemcpyHostToDevice, st);
+    const uint32_t need = h.sticky_needed > h.needed ? h.sticky_needed : h.needed;
+    if (keys_needed) *keys_needed = need;
+    if (h.sticky_err != 0 || h.sticky_overrun != 0) {
+        e = cudaMemsetAsync(reinterpret_cast<char *>(workspace) + kHeaderPerCall, 0, sizeof(WsHeader) - kHeaderPerCall,
+                            st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "sgad_check");
-        if (h.emit_overrun) return fail(SGAD_ERR_CUDA, "internal: binning count and key emission disagree");
-        if (h.err == SGAD_ERR_KEY_OVERFLOW)
-            return fail(SGAD_ERR_KEY_OVERFLOW, "forward needed %u keys, more than the workspace capacity", h.needed);
-        return fail(h.err, "device reported error %d", h.err);
+        if (h.sticky_overrun) return fail(SGAD_ERR_CUDA, "internal: binning count and key emission disagree");
+        if (h.sticky_err == SGAD_ERR_KEY_OVERFLOW)
+            return fail(SGAD_ERR_KEY_OVERFLOW, "a forward needed %u keys, more than the workspace capacity", need);
+        return fail(h.sticky_err, "device reported error %d", h.sticky_err);
     }
     return SGAD_OK;
 }
@@ -461,34 +462,58 @@ sgad_status sgad_l1_loss_grad(int32_t n_views, const sgad_camera *views, const s
     const bool use_depth = depth_weight != 0.0f;
     if (use_depth && (!target_depth || !d_depth || !valid_count))
         return fail(SGAD_ERR_INVALID_ARG, "depth term needs target_depth, d_depth and valid_count");
+    if (n_views > SGAD_MAX_VIEWS) return fail(SGAD_ERR_INVALID_ARG, "too many views");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (use_depth) {
-        cudaError_t e = cudaMemsetAsync(valid_count, 0, sizeof(uint32_t) * (size_t)n_views, st);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    }
+    const float *rgb[SGAD_MAX_VIEWS], *dep[SGAD_MAX_VIEWS];
+    uint32_t hw[SGAD_MAX_VIEWS];
     for (int i = 0; i < n_views; ++i) {
         if (!valid_camera(views[i])) return fail(SGAD_ERR_INVALID_ARG, "view %d: invalid camera", i);
         if (!rendered[i].rgb || !target_rgb[i] || !d_rgb[i] || (use_depth && (!rendered[i].depth || !target_depth[i])))
             return fail(SGAD_ERR_INVALID_ARG, "view %d: NULL image", i);
-        const size_t hw = (size_t)views[i].width * views[i].height;
-        launch_l1(rendered[i].rgb, rendered[i].depth, target_rgb[i], use_depth ? target_depth[i] : nullptr, hw,
-                  rgb_weight, depth_weight, use_depth ? valid_count + i : nullptr, d_rgb[i],
-                  d_depth ? d_depth[i] : nullptr, loss_accum, st);
+        rgb[i] = rendered[i].rgb;
+        dep[i] = rendered[i].depth;
+        hw[i] = (uint32_t)views[i].width * (uint32_t)views[i].height;
     }
+    if (use_depth) {
+        cudaError_t e = cudaMemsetAsync(valid_count, 0, sizeof(uint32_t) * (size_t)n_views, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
+    launch_l1_batch(n_views, rgb, dep, target_rgb, use_depth ? target_depth : nullptr, d_rgb, d_depth,
+                    use_depth ? valid_count : nullptr, hw, rgb_weight, depth_weight, loss_accum, st);
     return last_launch("sgad_l1_loss_grad");
 }
 
 sgad_status sgad_adam_step(int64_t n, float *param, const float *grad, float *m, float *v, float lr, float beta1,
-                           float beta2, float eps, int32_t step, void *stream)
+                           float beta2, float eps, int32_t step, int32_t mode, void *stream)
 {
     if (n < 0 || (n > 0 && (!param || !grad || !m || !v)) || step < 1)
         return fail(SGAD_ERR_INVALID_ARG, "bad arguments to sgad_adam_step");
+    if (mode != SGAD_ADAM_PLAIN && mode != SGAD_ADAM_LOG) return fail(SGAD_ERR_INVALID_ARG, "unknown Adam mode");
     if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !std::isfinite(lr) || !(eps >= 0.0f))
         return fail(SGAD_ERR_INVALID_ARG, "bad Adam hyper-parameters");
     const float c1 = (float)(1.0 - std::pow((double)beta1, (double)step));
     const float c2 = (float)(1.0 - std::pow((double)beta2, (double)step));
-    launch_adam(n, param, grad, m, v, lr, beta1, beta2, eps, c1, c2, static_cast<cudaStream_t>(stream));
+    launch_adam(n, param, grad, m, v, lr, beta1, beta2, eps, c1, c2, mode == SGAD_ADAM_LOG,
+                static_cast<cudaStream_t>(stream));
     return last_launch("sgad_adam_step");
+}
+
+sgad_status sgad_adam_step_multi(int32_t n_tensors, const sgad_adam_tensor *tensors, float beta1, float beta2,
+                                 float eps, int32_t *step_counter, void *stream)
+{
+    if (n_tensors < 1 || n_tensors > SGAD_ADAM_MAX_TENSORS || !tensors || !step_counter)
+        return fail(SGAD_ERR_INVALID_ARG, "bad arguments to sgad_adam_step_multi");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f))
+        return fail(SGAD_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+    for (int i = 0; i < n_tensors; ++i) {
+        const sgad_adam_tensor &t = tensors[i];
+        if (t.n < 0 || (t.n > 0 && (!t.param || !t.grad || !t.m || !t.v)) || !std::isfinite(t.lr) ||
+            (t.mode != SGAD_ADAM_PLAIN && t.mode != SGAD_ADAM_LOG))
+            return fail(SGAD_ERR_INVALID_ARG, "Adam tensor %d is invalid", i);
+    }
+    const cudaError_t e = launch_adam_multi(n_tensors, tensors, beta1, beta2, eps, step_counter,
+                                            static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SGAD_OK : cuda_fail(e, "sgad_adam_step_multi");
 }
 
 }  // extern "C"

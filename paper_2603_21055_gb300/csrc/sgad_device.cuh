@@ -56,19 +56,26 @@ struct Scene {
     ViewDev view[SGAD_MAX_VIEWS];
 };
 
-// Device-side status block at the start of the workspace.
+// Device-side status block at the start of the workspace. The first 128 bytes describe
+// the last forward and are cleared by every forward; the last 128 bytes accumulate
+// failures until sgad_check() reads and clears them.
 struct WsHeader {
     uint32_t n_keys;             // keys emitted by the last forward
-    uint32_t needed;             // keys the last forward needed (set on overflow)
-    int32_t err;                 // first SGAD_ERR_* recorded on the device, 0 if none
+    uint32_t needed;             // keys the last forward needed
+    int32_t err;                 // first SGAD_ERR_* of the last forward, 0 if none
     uint32_t overflow;           // 1 if the last forward's keys did not fit
     uint32_t emit_overrun;       // binning count and emission disagreed (must stay 0)
     uint32_t pad0;
     unsigned long long n_pairs;  // (pixel, entry) pairs composited by the last forward
     unsigned long long n_evals;  // (pixel, entry) pairs whose alpha the last forward evaluated
-    uint32_t pad[54];
+    uint32_t pad1[22];
+    int32_t sticky_err;          // first error since the last sgad_check()
+    uint32_t sticky_needed;      // largest key count needed since the last sgad_check()
+    uint32_t sticky_overrun;
+    uint32_t pad2[29];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte block");
+constexpr size_t kHeaderPerCall = 128;   // bytes cleared by every forward
 
 // Per-Gaussian record computed once per forward (view independent):
 //   w0 = (mu_x, mu_y, mu_z, s), w1 = (opacity, r, g, b)
@@ -97,6 +104,7 @@ __device__ __forceinline__ int find_view_of_tile(const Scene &sc, int tile)
 __device__ __forceinline__ void record_error(WsHeader *h, int code)
 {
     atomicCAS(reinterpret_cast<int *>(&h->err), 0, code);
+    atomicCAS(reinterpret_cast<int *>(&h->sticky_err), 0, code);
 }
 
 // ------------------------------------------------------- FP32 projection (EWA)

@@ -1,0 +1,122 @@
+"""Mapping iterations (Sec. 3.2, Eq. 1 with the SSIM term left out) on the GPU.
+
+One iteration renders every keyframe of the window into every view (forward splatting),
+takes the L1 colour + depth loss gradient against the observed RGB-D, runs the adjoint
+into offset, colour, opacity logit and scale of the learnable keyframes, and applies one
+Adam step with the learning rates of the supplementary Sec. A (colour 0.0025, radius
+0.005, opacity 0.05, offset 0.01; the radius rate is applied to log s). All of it is
+library launches on one stream; `capture()` records one iteration as a CUDA graph so that
+`step()` replays it with a single launch from the host.
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional
+
+import torch
+
+from . import binding as B
+from . import splat
+
+LR = dict(offset=0.01, rgb=0.0025, logit=0.05, scale=0.005)
+PARAMS = (("offset", "d_offset"), ("rgb", "d_rgb"), ("logit", "d_logit"), ("scale", "d_scale"))
+
+
+class Mapper:
+    """Device state of one keyframe window: parameters, Adam moments, images, gradients,
+    targets and the library workspace."""
+
+    def __init__(self, scene, tile=(16, 16), slack: float = 1.3, lr: Optional[dict] = None,
+                 freeze_offset: bool = False, kfs=None):
+        self.scene = scene
+        self.views = scene.views
+        self.lr = dict(LR, **(lr or {}))
+        self.sp = splat.Splatter(tile=tile, freeze_offset=freeze_offset)
+        self.kfs = kfs if kfs is not None else splat.upload_keyframes(scene)
+        self.trgb, self.tdep = splat.upload_targets(scene)
+        self.images = splat.alloc_images(self.views)
+        self.d_rgb = [torch.empty_like(im["rgb"]) for im in self.images]
+        self.d_dep = [torch.empty_like(im["depth"]) for im in self.images]
+        self.gin = [dict(rgb=r, depth=d) for r, d in zip(self.d_rgb, self.d_dep)]
+        self.loss = torch.zeros(1, device="cuda")
+        self.valid = torch.zeros(len(self.views), dtype=torch.int32, device="cuda")
+        self.grads = [dict(d_offset=torch.empty_like(k.offset), d_rgb=torch.empty_like(k.rgb),
+                           d_logit=torch.empty_like(k.logit), d_scale=torch.empty_like(k.scale))
+                      if k.learnable else None for k in self.kfs]
+        self.moments = [{n: (torch.zeros_like(getattr(k, n)), torch.zeros_like(getattr(k, n))) for n, _ in PARAMS}
+                        if k.learnable else None for k in self.kfs]
+        self.step_counter = torch.zeros(1, dtype=torch.int32, device="cuda")
+        tensors = []
+        for k, g, mo in zip(self.kfs, self.grads, self.moments):
+            if g is None:
+                continue
+            for n, gn in PARAMS:
+                if n == "offset" and freeze_offset:
+                    continue
+                p = getattr(k, n)
+                m, v = mo[n]
+                mode = B.SGAD_ADAM_LOG if n == "scale" else B.SGAD_ADAM_PLAIN
+                tensors.append(B.sgad_adam_tensor(p.data_ptr(), g[gn].data_ptr(), m.data_ptr(), v.data_ptr(),
+                                                  p.numel(), self.lr[n], mode))
+        self.adam = (B.sgad_adam_tensor * max(1, len(tensors)))(*tensors)
+        self.n_adam = len(tensors)
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+        self.n_keys = self.sp.plan(self.kfs, self.views, slack=slack)
+
+    # ------------------------------------------------------------------ one step
+    def forward(self):
+        self.sp.forward(self.kfs, self.views, self.images)
+
+    def step_eager(self):
+        sp = self.sp
+        sp.forward(self.kfs, self.views, self.images)
+        self.loss.zero_()
+        sp.l1_loss_grad(self.views, self.images, self.trgb, self.tdep, self.scene.rgb_weight, self.scene.depth_weight,
+                        self.d_rgb, self.d_dep, self.loss, self.valid)
+        sp.backward(self.kfs, self.views, self.gin, self.grads)
+        if self.n_adam:
+            B.sgad_adam_step_multi(self.adam, 0.9, 0.999, 1e-15, self.step_counter.data_ptr(), sp.stream())
+
+    def capture(self):
+        """Record one iteration as a CUDA graph (after one eager warm-up on a side stream)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step_eager()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step_eager()
+        self.graph = g
+
+    def step(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.step_eager()
+
+    def launches_per_step(self) -> int:
+        """Library kernels per iteration: projection+count, scan, emission, sort, forward
+        compositing; valid-depth count and L1 gradient; backward compositing, finalisation;
+        multi-tensor Adam and its step counter."""
+        n = 5 + (2 if self.scene.depth_weight != 0 else 1) + 2
+        return n + (2 if self.n_adam else 0)
+
+    # ------------------------------------------------------------------ checks
+    def ensure_capacity(self, slack: float = 1.3) -> bool:
+        """False (and a bigger workspace, which invalidates a captured graph) if any
+        forward since the last check ran out of key slots."""
+        s, _, need = self.sp.check()
+        if s != 0:
+            self.sp.reserve(self.kfs, self.views, int(need * slack) + 4096)
+            self.graph = None
+            return False
+        return True
+
+    def psnr(self) -> float:
+        """Mean PSNR over the views of the last forward: 10 log10(1 / MSE), RGB in [0, 1]."""
+        vals = []
+        for im, t in zip(self.images, self.trgb):
+            mse = torch.mean((im["rgb"].clamp(0, 1) - t) ** 2).item()
+            vals.append(10.0 * math.log10(1.0 / max(mse, 1e-12)))
+        return sum(vals) / len(vals)

@@ -80,7 +80,7 @@ class Splatter:
         self.ctx = B.sgad_create(o)
         self.workspace: Optional[torch.Tensor] = None
         self.key_capacity = 0
-        self._views_key = None
+        self._cache = {}
 
     def __del__(self):
         try:
@@ -91,19 +91,34 @@ class Splatter:
 
     # ---------------------------------------------------------------- marshalling
     @staticmethod
-    def kf_structs(kfs: Sequence[DeviceKeyframe]):
-        arr = (B.sgad_keyframe * len(kfs))()
-        for i, k in enumerate(kfs):
-            arr[i] = B.sgad_keyframe(_ptr(k.depth), _ptr(k.offset), _ptr(k.rgb), _ptr(k.logit), _ptr(k.scale),
-                                     _cam(k.cam), int(k.learnable))
-        return arr
+    def _kf_key(kfs):
+        return tuple((k.depth.data_ptr(), k.offset.data_ptr(), k.rgb.data_ptr(), k.logit.data_ptr(),
+                      k.scale.data_ptr(), id(k.cam), bool(k.learnable)) for k in kfs)
 
-    @staticmethod
-    def view_structs(views):
-        arr = (B.sgad_camera * len(views))()
-        for i, v in enumerate(views):
-            arr[i] = _cam(v)
-        return arr
+    def kf_structs(self, kfs: Sequence[DeviceKeyframe]):
+        key = ("kf", self._kf_key(kfs))
+        hit = self._cache.get(key)
+        if hit is None:
+            arr = (B.sgad_keyframe * len(kfs))()
+            for i, k in enumerate(kfs):
+                arr[i] = B.sgad_keyframe(_ptr(k.depth), _ptr(k.offset), _ptr(k.rgb), _ptr(k.logit), _ptr(k.scale),
+                                         _cam(k.cam), int(k.learnable))
+            if len(self._cache) > 64:
+                self._cache.clear()
+            self._cache[key] = (arr, list(kfs))        # keep the keyframes (and cameras) alive
+            return arr
+        return hit[0]
+
+    def view_structs(self, views):
+        key = ("views", tuple(id(v) for v in views))
+        arr = self._cache.get(key)
+        if arr is None:
+            arr = (B.sgad_camera * len(views))()
+            for i, v in enumerate(views):
+                arr[i] = _cam(v)
+            self._cache[key] = (arr, list(views))      # keep the camera objects alive
+            return arr
+        return arr[0]
 
     @staticmethod
     def stream() -> int:
@@ -134,7 +149,11 @@ class Splatter:
         ka, va = self.kf_structs(kfs), self.view_structs(views)
         need = B.sgad_workspace_size(self.ctx, ka, va, key_capacity)
         if self.workspace is None or self.workspace.numel() < need:
+            old = self.workspace
             self.workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+            self.workspace[:256].zero_()          # device status block starts cleared
+            if old is not None:                   # keep the projection state of plan()
+                self.workspace[:old.numel()].copy_(old)
         self.key_capacity = key_capacity
 
     def forward(self, kfs, views, images) -> None:

@@ -85,5 +85,5 @@ def test_host_validation_without_gpu():
     bad[0].fx = -1.0
     assert lib.sgad_workspace_size(ctx, kfs, 1, bad, 1, 0, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
     assert lib.sgad_workspace_size(ctx, kfs, 1, views, 1, -5, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
-    assert lib.sgad_adam_step(10, None, None, None, None, 0.1, 0.9, 0.999, 1e-15, 1, None) == B.SGAD_ERR_INVALID_ARG
+    assert lib.sgad_adam_step(10, None, None, None, None, 0.1, 0.9, 0.999, 1e-15, 1, 0, None) == B.SGAD_ERR_INVALID_ARG
     B.sgad_destroy(ctx)
