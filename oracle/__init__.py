@@ -51,7 +51,7 @@ class Kf(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("bg", C.c_double * 3),
-                ("margin", C.c_double)]
+                ("margin", C.c_double), ("t_margin", C.c_double)]
 
 
 class Proj(C.Structure):
@@ -59,7 +59,8 @@ class Proj(C.Structure):
                 ("ty1", C.c_int32), ("ntiles", C.c_int32), ("near", C.c_int32), ("pad_", C.c_int32),
                 ("mu", C.c_double * 3), ("t", C.c_double * 3), ("p", C.c_double * 2),
                 ("cov", C.c_double * 3), ("conic", C.c_double * 3), ("o", C.c_double),
-                ("rho", C.c_double), ("zf", C.c_double), ("s", C.c_double), ("color", C.c_double * 3)]
+                ("rho", C.c_double), ("zf", C.c_double), ("s", C.c_double), ("color", C.c_double * 3),
+                ("pf", C.c_float * 2), ("conicf", C.c_float * 3), ("of", C.c_float)]
 
 
 class Image(C.Structure):
@@ -81,7 +82,8 @@ PROJ_DTYPE = np.dtype([("visible", np.int32), ("tx0", np.int32), ("tx1", np.int3
                        ("mu", np.float64, 3), ("t", np.float64, 3), ("p", np.float64, 2),
                        ("cov", np.float64, 3), ("conic", np.float64, 3), ("o", np.float64),
                        ("rho", np.float64), ("zf", np.float64), ("s", np.float64),
-                       ("color", np.float64, 3)])
+                       ("color", np.float64, 3), ("pf", np.float32, 2), ("conicf", np.float32, 3),
+                       ("of", np.float32)])
 assert PROJ_DTYPE.itemsize == C.sizeof(Proj)
 
 
@@ -141,8 +143,11 @@ class _Inputs:
         self.views, self.n_views = views, len(scene.views)
 
 
-def opts(tile_w: int = 16, tile_h: int = 16, bg=(0.0, 0.0, 0.0), margin: float = 1e-5) -> Opts:
-    return Opts(tile_w, tile_h, (C.c_double * 3)(*bg), margin)
+def opts(tile_w: int = 16, tile_h: int = 16, bg=(0.0, 0.0, 0.0), margin: float = 4e-6,
+         t_margin: float = 2e-4) -> Opts:
+    """Tile shape, background, and the relative margins under which the single-precision
+    alpha decisions (floor, cap) and the transmittance stop are reported near."""
+    return Opts(tile_w, tile_h, (C.c_double * 3)(*bg), margin, t_margin)
 
 
 def num_gaussians(scene) -> int:

@@ -67,16 +67,6 @@ static int32_t owner(const orc_kf *kfs, int32_t n_kf, int64_t g, int64_t *local)
 
 static double rel_gap(double x, double thr) { return fabs(x - thr) / fabs(thr); }
 
-/* relative distance of x to the nearest value at which a clipped tile index or the
- * empty-rectangle test changes: the multiples of the tile size and the image size */
-static double bound_gap(double x, int32_t tile, int32_t limit)
-{
-    double k = floor(x / tile);
-    double d = fmin(fabs(x - k * tile), fabs(x - (k + 1.0) * tile));
-    d = fmin(d, fabs(x - (double)limit));
-    return d / fmax(1.0, fabs(x));
-}
-
 /* relative distance of z to the nearest midpoint between adjacent f32 values, i.e. how
  * far it is from a change of its f32 rounding */
 static double round_gap(double z)
@@ -89,10 +79,76 @@ static double round_gap(double z)
 
 /* ------------------------------------------------------------------- projection */
 
+/* Decision values of one (Gaussian, view) pair in single precision, the way the kernel
+ * evaluates them: the world centre from the keyframe ray, the view-space centre, the
+ * pixel mean, the dilated 2D covariance, the integer radius and tile rectangle, the
+ * conic and the opacity. Each line is one IEEE single operation (fmaf where the kernel
+ * fuses), so the integers that come out equal the kernel's. */
+static void project_f32(const orc_kf *kf, int64_t j, const orc_cam *view, const orc_opts *opt, orc_proj *P)
+{
+    const orc_cam *c = &kf->cam;
+    const int32_t W = c->width;
+    float M[12], V[12];
+    for (int i = 0; i < 12; ++i) {
+        M[i] = (float)c->pose[i];
+        V[i] = (float)view->pose[i];
+    }
+    const float u = (float)(j % W), v = (float)(j / W);
+    const float d = fabsf((float)kf->depth[j] + (float)kf->offset[j]);
+    const float rx = (u - (float)c->cx) / (float)c->fx;
+    const float ry = (v - (float)c->cy) / (float)c->fy;
+    const float qx = d * rx, qy = d * ry;
+    const float mx = fmaf(M[0], qx, fmaf(M[1], qy, fmaf(M[2], d, M[3])));
+    const float my = fmaf(M[4], qx, fmaf(M[5], qy, fmaf(M[6], d, M[7])));
+    const float mz = fmaf(M[8], qx, fmaf(M[9], qy, fmaf(M[10], d, M[11])));
+    const float s = (float)kf->scale[j];
+    P->of = 1.0f / (1.0f + expf(-(float)kf->logit[j]));
+    const float tx = fmaf(V[0], mx, fmaf(V[1], my, fmaf(V[2], mz, V[3])));
+    const float ty = fmaf(V[4], mx, fmaf(V[5], my, fmaf(V[6], mz, V[7])));
+    const float tz = fmaf(V[8], mx, fmaf(V[9], my, fmaf(V[10], mz, V[11])));
+    const float fx = (float)view->fx, fy = (float)view->fy;
+    const float iz = 1.0f / tz;
+    const float ux = tx * iz, uy = ty * iz;
+    const float px = fmaf(fx, ux, (float)view->cx), py = fmaf(fy, uy, (float)view->cy);
+    const float j00 = fx * iz, j02 = -(j00 * ux);
+    const float j11 = fy * iz, j12 = -(j11 * uy);
+    const float s2 = s * s;
+    const float cxx = fmaf(s2, fmaf(j00, j00, j02 * j02), (float)DILATION);
+    const float cxy = s2 * (j02 * j12);
+    const float cyy = fmaf(s2, fmaf(j11, j11, j12 * j12), (float)DILATION);
+    const float det = cxx * cyy - cxy * cxy;
+    P->pf[0] = px;
+    P->pf[1] = py;
+    P->tx0 = 1; P->tx1 = 0; P->ty0 = 1; P->ty1 = 0;
+    P->visible = 0;
+    P->ntiles = 0;
+    if (!(tz > (float)NEAR_PLANE) || !(det > 0.0f)) return;
+    P->visible = 1;
+    const float id = 1.0f / det;
+    P->conicf[0] = cyy * id;
+    P->conicf[1] = -(cxy * id);
+    P->conicf[2] = cxx * id;
+    const float mid = 0.5f * (cxx + cyy);
+    const float disc = fmaxf(0.1f, mid * mid - det);
+    const float lam = mid + sqrtf(disc);
+    const float rho = ceilf(3.0f * sqrtf(lam));
+    P->rho = rho;
+    /* pixel rectangle [floor(p - rho), floor(p + rho)] clipped to the image */
+    const float x0 = floorf(px - rho), x1 = floorf(px + rho);
+    const float y0 = floorf(py - rho), y1 = floorf(py + rho);
+    if (x1 < 0.0f || y1 < 0.0f || x0 > (float)(view->width - 1) || y0 > (float)(view->height - 1)) return;
+    const int32_t ix0 = x0 < 0.0f ? 0 : (int32_t)x0, iy0 = y0 < 0.0f ? 0 : (int32_t)y0;
+    const int32_t ix1 = x1 > (float)(view->width - 1) ? view->width - 1 : (int32_t)x1;
+    const int32_t iy1 = y1 > (float)(view->height - 1) ? view->height - 1 : (int32_t)y1;
+    P->tx0 = ix0 / opt->tile_w; P->tx1 = ix1 / opt->tile_w;
+    P->ty0 = iy0 / opt->tile_h; P->ty1 = iy1 / opt->tile_h;
+    P->ntiles = (P->tx1 - P->tx0 + 1) * (P->ty1 - P->ty0 + 1);
+}
+
 /* Sec. 3.2: Gaussian at pixel (u, v) of keyframe kf sits at mu = R_i (|D + delta| r) + t_i
  * with r = ((u - cx)/fx, (v - cy)/fy, 1); it is seen by the view at t = R_k mu + t_k.
  * EWA: J = d(pixel)/d(t), Sigma_2D = s^2 J J^T + 0.3 I for the isotropic 3D covariance
- * s^2 I; its inverse is the conic; the square bound is ceil(3 sqrt(lambda_max)). */
+ * s^2 I; its inverse is the conic. FP64 values; the decisions come from project_f32. */
 static void project_one(const orc_kf *kf, int64_t j, const orc_cam *view, const orc_opts *opt,
                         orc_proj *P)
 {
@@ -106,7 +162,6 @@ static void project_one(const orc_kf *kf, int64_t j, const orc_cam *view, const 
     const int64_t hw = (int64_t)c->width * c->height;
 
     memset(P, 0, sizeof(*P));
-    P->tx0 = 1; P->tx1 = 0; P->ty0 = 1; P->ty1 = 0;
     for (int a = 0; a < 3; ++a)
         P->mu[a] = M[4 * a] * dt * r[0] + M[4 * a + 1] * dt * r[1] + M[4 * a + 2] * dt * r[2] + M[4 * a + 3];
     for (int a = 0; a < 3; ++a)
@@ -115,48 +170,28 @@ static void project_one(const orc_kf *kf, int64_t j, const orc_cam *view, const 
     P->s = kf->scale[j];
     for (int ch = 0; ch < 3; ++ch) P->color[ch] = kf->rgb[ch * hw + j];
     P->zf = (double)(float)P->t[2];
+    if (round_gap(P->t[2]) < Z_ROUND_MARGIN) P->near |= ORC_NEAR_Z;
 
     const double tz = P->t[2];
-    if (rel_gap(tz, NEAR_PLANE) < opt->margin) P->near |= ORC_NEAR_PLANE;
-    if (round_gap(tz) < Z_ROUND_MARGIN) P->near |= ORC_NEAR_Z;
-    if (!(tz > 0.0)) return;                      /* behind the camera: nothing to project */
-
-    const double fx = view->fx, fy = view->fy;
-    P->p[0] = fx * P->t[0] / tz + view->cx;
-    P->p[1] = fy * P->t[1] / tz + view->cy;
-    const double J00 = fx / tz, J02 = -fx * P->t[0] / (tz * tz);
-    const double J11 = fy / tz, J12 = -fy * P->t[1] / (tz * tz);
-    const double s2 = P->s * P->s;
-    const double x = s2 * (J00 * J00 + J02 * J02) + DILATION;
-    const double y = s2 * (J02 * J12);
-    const double w = s2 * (J11 * J11 + J12 * J12) + DILATION;
-    const double det = x * w - y * y;
-    P->cov[0] = x; P->cov[1] = y; P->cov[2] = w;
-    if (!(det > 0.0)) return;
-    P->conic[0] = w / det;
-    P->conic[1] = -y / det;
-    P->conic[2] = x / det;
-    const double mid = 0.5 * (x + w);
-    const double lam = mid + sqrt(fmax(0.1, mid * mid - det));
-    const double r3 = 3.0 * sqrt(lam);
-    P->rho = ceil(r3);
-    if (fabs(r3 - nearbyint(r3)) / r3 < opt->margin) P->near |= ORC_NEAR_RHO;
-
-    /* pixel rectangle [floor(p - rho), floor(p + rho)] clipped to the image */
-    const double bx[2] = {P->p[0] - P->rho, P->p[0] + P->rho};
-    const double by[2] = {P->p[1] - P->rho, P->p[1] + P->rho};
-    if (bound_gap(bx[0], opt->tile_w, view->width) < opt->margin) P->near |= ORC_NEAR_X0;
-    if (bound_gap(bx[1], opt->tile_w, view->width) < opt->margin) P->near |= ORC_NEAR_X1;
-    if (bound_gap(by[0], opt->tile_h, view->height) < opt->margin) P->near |= ORC_NEAR_Y0;
-    if (bound_gap(by[1], opt->tile_h, view->height) < opt->margin) P->near |= ORC_NEAR_Y1;
-    double xlo = floor(bx[0]), xhi = floor(bx[1]), ylo = floor(by[0]), yhi = floor(by[1]);
-    xlo = fmax(xlo, 0.0); ylo = fmax(ylo, 0.0);
-    xhi = fmin(xhi, (double)view->width - 1.0); yhi = fmin(yhi, (double)view->height - 1.0);
-    P->visible = tz > NEAR_PLANE;
-    if (xlo > xhi || ylo > yhi) return;
-    P->tx0 = (int32_t)xlo / opt->tile_w; P->tx1 = (int32_t)xhi / opt->tile_w;
-    P->ty0 = (int32_t)ylo / opt->tile_h; P->ty1 = (int32_t)yhi / opt->tile_h;
-    if (P->visible) P->ntiles = (P->tx1 - P->tx0 + 1) * (P->ty1 - P->ty0 + 1);
+    if (tz > 0.0) {
+        const double fx = view->fx, fy = view->fy;
+        P->p[0] = fx * P->t[0] / tz + view->cx;
+        P->p[1] = fy * P->t[1] / tz + view->cy;
+        const double J00 = fx / tz, J02 = -fx * P->t[0] / (tz * tz);
+        const double J11 = fy / tz, J12 = -fy * P->t[1] / (tz * tz);
+        const double s2 = P->s * P->s;
+        const double x = s2 * (J00 * J00 + J02 * J02) + DILATION;
+        const double y = s2 * (J02 * J12);
+        const double w = s2 * (J11 * J11 + J12 * J12) + DILATION;
+        const double det = x * w - y * y;
+        P->cov[0] = x; P->cov[1] = y; P->cov[2] = w;
+        if (det > 0.0) {
+            P->conic[0] = w / det;
+            P->conic[1] = -y / det;
+            P->conic[2] = x / det;
+        }
+    }
+    project_f32(kf, j, view, opt, P);
 }
 
 int32_t orc_project(const orc_kf *kfs, int32_t n_kf, const orc_cam *view, const orc_opts *opt,
@@ -326,33 +361,41 @@ static uint64_t fnv(uint64_t h, uint64_t x)
 /* Front-to-back compositing of one pixel over a depth-sorted list (3DGS convention):
  * power = -(a dx^2 + c dy^2)/2 - b dx dy with d = p - pixel; skip power > 0; alpha =
  * min(0.99, o e^power); skip alpha < 1/255; stop (excluding this entry) once T (1 - alpha)
- * would fall below 1e-4; otherwise add alpha T (colour, depth, 1) and update T. */
+ * would fall below 1e-4; otherwise add alpha T (colour, depth, 1) and update T. The
+ * branches are taken in single precision as the kernel takes them (the transmittance
+ * that decides the stop is the single-precision running product); the accumulated values
+ * are double precision. */
 static void walk_pixel(const orc_proj *proj, const list_entry *list, int64_t n, double qx, double qy,
                        const orc_opts *opt, walk_rec *rec, walk_out *out)
 {
-    const double m = opt->margin;
+    const float floor_f = (float)ALPHA_FLOOR, cap_f = (float)ALPHA_CAP, stop_f = (float)T_STOP;
+    float Tf = 1.0f;
     double T = 1.0, C[3] = {0, 0, 0}, Dp = 0.0, A = 0.0;
     int32_t last = -1, near = 0, nrec = 0;
     int64_t i;
     uint64_t h = 1469598103934665603ull;
     for (i = 0; i < n; ++i) {
         const orc_proj *P = &proj[list[i].g];
+        /* decision, single precision */
+        const float dxf = P->pf[0] - (float)qx, dyf = P->pf[1] - (float)qy;
+        const float quad = fmaf(P->conicf[0], dxf * dxf, P->conicf[2] * (dyf * dyf));
+        const float power = -0.5f * quad - P->conicf[1] * (dxf * dyf);
+        if (power > 0.0f) continue;
+        const float rawf = P->of * expf(power);
+        if (rel_gap(rawf, cap_f) < opt->margin) near = 1;
+        if (rel_gap(rawf, floor_f) < opt->margin) near = 1;
+        const float alphaf = fminf(cap_f, rawf);
+        if (alphaf < floor_f) continue;
+        const float testf = Tf * (1.0f - alphaf);
+        if (rel_gap(testf, stop_f) < opt->t_margin) near = 1;
+        if (testf < stop_f) { h = fnv(h, (uint64_t)i | (1ull << 63)); break; }
+        Tf = testf;
+        /* value, double precision */
         const double dx = P->p[0] - qx, dy = P->p[1] - qy;
-        const double qa = 0.5 * (P->conic[0] * dx * dx + P->conic[2] * dy * dy);
-        const double qb = P->conic[1] * dx * dy;
-        const double power = -qa - qb;
-        const double scale = qa + fabs(qb);
-        if (scale > 0.0 && fabs(power) / scale < m) near = 1;
-        if (power > 0.0) continue;
-        const double ep = exp(power);
-        const double raw = P->o * ep;
-        if (rel_gap(raw, ALPHA_CAP) < m) near = 1;
-        if (rel_gap(raw, ALPHA_FLOOR) < m) near = 1;
-        const double alpha = fmin(ALPHA_CAP, raw);
-        if (alpha < ALPHA_FLOOR) continue;
-        const double test = T * (1.0 - alpha);
-        if (rel_gap(test, T_STOP) < m) near = 1;
-        if (test < T_STOP) { h = fnv(h, (uint64_t)i | (1ull << 63)); break; }
+        const double pw = -0.5 * (P->conic[0] * dx * dx + P->conic[2] * dy * dy) - P->conic[1] * dx * dy;
+        const double ep = exp(pw);
+        const int capped = rawf > cap_f;
+        const double alpha = capped ? ALPHA_CAP : P->o * ep;
         const double w = alpha * T;
         for (int ch = 0; ch < 3; ++ch) C[ch] += w * P->color[ch];
         Dp += w * P->t[2];
@@ -360,10 +403,10 @@ static void walk_pixel(const orc_proj *proj, const list_entry *list, int64_t n, 
         if (rec) {
             walk_rec *r = &rec[nrec];
             r->pos = (int32_t)i; r->g = list[i].g; r->alpha = alpha; r->T = T; r->ep = ep;
-            r->dx = dx; r->dy = dy; r->capped = raw > ALPHA_CAP;
+            r->dx = dx; r->dy = dy; r->capped = capped;
         }
         ++nrec;
-        T = test;
+        T *= 1.0 - alpha;
         last = (int32_t)i;
         h = fnv(h, (uint64_t)i);
     }
@@ -376,55 +419,6 @@ static void walk_pixel(const orc_proj *proj, const list_entry *list, int64_t n, 
     out->n_rec = nrec;
     out->end = (int32_t)i;
     out->hash = h;
-}
-
-/* Tile range [t0, t1] (clipped; t0 > t1 when empty) of the pixel interval
- * [floor(lo), floor(hi)] clipped to [0, size - 1]. */
-static void tile_span(double lo, double hi, int32_t size, int32_t tile, int32_t *t0, int32_t *t1)
-{
-    double a = floor(lo), b = floor(hi);
-    if (b < 0.0 || a > size - 1.0) { *t0 = 1; *t1 = 0; return; }
-    a = fmax(a, 0.0);
-    b = fmin(b, size - 1.0);
-    *t0 = (int32_t)a / tile;
-    *t1 = (int32_t)b / tile;
-}
-
-/* Pixels whose result depends on a binning decision that FP32 may take differently:
- * the tiles that lie in the largest rectangle the near decisions allow (radius + 1 when
- * the ceil is near, near edges moved outwards by half a pixel) but not in the smallest
- * one (radius - 1, near edges moved inwards; nothing when the near-plane cull is near),
- * and there only the pixels at which this Gaussian's alpha passes the floor. */
-static void mark_binning_near(const orc_proj *proj, int64_t nG, const orc_cam *view,
-                              const orc_opts *opt, uint8_t *near)
-{
-    const int32_t W = view->width, H = view->height;
-    const int bin_bits = ORC_NEAR_PLANE | ORC_NEAR_RHO | ORC_NEAR_X0 | ORC_NEAR_X1 | ORC_NEAR_Y0 | ORC_NEAR_Y1;
-    for (int64_t g = 0; g < nG; ++g) {
-        const orc_proj *P = &proj[g];
-        if (!(P->near & bin_bits) || !(P->t[2] > 0.0) || P->rho <= 0.0) continue;
-        const double dr = (P->near & ORC_NEAR_RHO) ? 1.0 : 0.0;
-        const double ex0 = (P->near & ORC_NEAR_X0) ? 0.5 : 0.0, ex1 = (P->near & ORC_NEAR_X1) ? 0.5 : 0.0;
-        const double ey0 = (P->near & ORC_NEAR_Y0) ? 0.5 : 0.0, ey1 = (P->near & ORC_NEAR_Y1) ? 0.5 : 0.0;
-        const double rmax = P->rho + dr, rmin = P->rho - dr;
-        int32_t ax0, ax1, ay0, ay1, ix0, ix1, iy0, iy1;
-        tile_span(P->p[0] - rmax - ex0, P->p[0] + rmax + ex1, W, opt->tile_w, &ax0, &ax1);
-        tile_span(P->p[1] - rmax - ey0, P->p[1] + rmax + ey1, H, opt->tile_h, &ay0, &ay1);
-        tile_span(P->p[0] - rmin + ex0, P->p[0] + rmin - ex1, W, opt->tile_w, &ix0, &ix1);
-        tile_span(P->p[1] - rmin + ey0, P->p[1] + rmin - ey1, H, opt->tile_h, &iy0, &iy1);
-        const int inner_empty = (P->near & ORC_NEAR_PLANE) || ix0 > ix1 || iy0 > iy1;
-        for (int32_t ty = ay0; ty <= ay1; ++ty)
-            for (int32_t tx = ax0; tx <= ax1; ++tx) {
-                if (!inner_empty && tx >= ix0 && tx <= ix1 && ty >= iy0 && ty <= iy1) continue;
-                for (int32_t y = ty * opt->tile_h; y < (ty + 1) * opt->tile_h && y < H; ++y)
-                    for (int32_t x = tx * opt->tile_w; x < (tx + 1) * opt->tile_w && x < W; ++x) {
-                        const double dx = P->p[0] - x, dy = P->p[1] - y;
-                        const double power =
-                            -0.5 * (P->conic[0] * dx * dx + P->conic[2] * dy * dy) - P->conic[1] * dx * dy;
-                        if (P->o * exp(power) >= ALPHA_FLOOR * (1.0 - opt->margin)) near[(int64_t)y * W + x] = 1;
-                    }
-            }
-    }
 }
 
 int32_t orc_render(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int32_t n_views,
@@ -456,7 +450,6 @@ int32_t orc_render(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int32_
                     out[k].near[pix] = (uint8_t)o.near;
                 }
         }
-        mark_binning_near(proj, nG, view, opt, out[k].near);
         free_lists(&L);
     }
     free(proj);
@@ -478,8 +471,6 @@ int32_t orc_render_pixels(const orc_kf *kfs, int32_t n_kf, const orc_cam *views,
         orc_project(kfs, n_kf, view, opt, proj);
         tile_lists L;
         build_lists(proj, nG, view, opt, &L);
-        uint8_t *nearimg = (uint8_t *)calloc((size_t)view->width * view->height, 1);
-        mark_binning_near(proj, nG, view, opt, nearimg);
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t i = 0; i < n_px; ++i) {
             if (px_view[i] != k) continue;
@@ -491,9 +482,8 @@ int32_t orc_render_pixels(const orc_kf *kfs, int32_t n_kf, const orc_cam *views,
             alpha[i] = o.alpha;
             t_final[i] = o.T;
             n_contrib[i] = o.n_contrib;
-            near[i] = (uint8_t)(o.near | nearimg[(int64_t)px_y[i] * view->width + px_x[i]]);
+            near[i] = (uint8_t)o.near;
         }
-        free(nearimg);
         free_lists(&L);
     }
     free(proj);
@@ -685,11 +675,8 @@ int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int3
         const int32_t nt = L.ntx * L.nty;
         int32_t *tiles = (int32_t *)malloc(sizeof(int32_t) * (size_t)nt);
         for (int32_t t = 0; t < nt; ++t) tiles[t] = t;
-        uint8_t *near_img = (uint8_t *)calloc((size_t)views[k].width * views[k].height, 1);
-        mark_binning_near(proj, nG, &views[k], opt, near_img);
         memset(g2d, 0, sizeof(*g2d) * (size_t)nG);
-        view_adjoint_tiles(proj, &L, &views[k], opt, &grad_in[k], tiles, nt, NULL, g2d, near_img, near_gauss);
-        free(near_img);
+        view_adjoint_tiles(proj, &L, &views[k], opt, &grad_in[k], tiles, nt, NULL, g2d, NULL, near_gauss);
         for (int64_t g = 0; g < nG; ++g) {
             if (!(proj[g].ntiles > 0)) continue;
             int64_t j;
@@ -753,10 +740,7 @@ int32_t orc_backward_gaussians(const orc_kf *kfs, int32_t n_kf, const orc_cam *v
         for (int32_t t = 0; t < nt; ++t)
             if (want[t]) tiles[nw++] = t;
         memset(g2d, 0, sizeof(*g2d) * (size_t)(n_sel + 1));
-        uint8_t *near_img = (uint8_t *)calloc((size_t)views[k].width * views[k].height, 1);
-        mark_binning_near(proj, nG, &views[k], opt, near_img);
-        view_adjoint_tiles(proj, &L, &views[k], opt, &grad_in[k], tiles, nw, slot, g2d, near_img, near_sel);
-        free(near_img);
+        view_adjoint_tiles(proj, &L, &views[k], opt, &grad_in[k], tiles, nw, slot, g2d, NULL, near_sel);
         for (int64_t s = 0; s < n_sel; ++s) {
             const int64_t g = sel[s];
             if (!(proj[g].ntiles > 0)) continue;

@@ -22,11 +22,17 @@
  * Inputs are FP64 arrays; the tests pass exact upcasts of the float32 arrays the CUDA
  * library receives (and perturb them in FP64 for finite differences).
  *
- * Every discrete decision (near-plane cull, the integer radius, the tile bounds, the
- * f32 rounding of the depth key, power > 0, the alpha floor and cap, the transmittance
- * stop) is taken in FP64 and its relative margin to the threshold is reported, so a
- * comparison against an FP32 implementation can set aside the few items whose outcome
- * FP32 rounding may legitimately flip.
+ * Values (positions, conics, alphas, transmittance, images, gradients) are computed in
+ * FP64. Every discrete decision (near-plane cull, the integer radius, the tile bounds,
+ * power > 0, the alpha floor and cap, the transmittance stop) is an integer decided by
+ * floating point, and is taken in the precision the kernel uses, FP32, evaluating the
+ * same formulas in the same order with IEEE single-precision operations (fmaf where the
+ * kernel fuses). Binning therefore matches the kernel bit for bit. The alpha decisions
+ * involve exp, whose single-precision implementations differ in the last bits, so they
+ * are reported "near" when within 1e-6 relative of their threshold (the transmittance
+ * stop, which accumulates those differences, within 5e-5). The depth key is t_z
+ * evaluated in FP64 and rounded once to f32; it is near when within 1e-12 relative of an
+ * f32 rounding midpoint.
  */
 #ifndef SGAD_ORACLE_H
 #define SGAD_ORACLE_H
@@ -56,27 +62,21 @@ typedef struct {
 typedef struct {
     int32_t tile_w, tile_h;
     double bg[3];               /* background colour */
-    double margin;              /* relative margin below which a decision is "near" */
+    double margin;              /* relative margin of the alpha floor/cap decisions (1e-6) */
+    double t_margin;            /* relative margin of the transmittance stop (5e-5) */
 } orc_opts;
 
-/* Decisions of the binning of one (Gaussian, view) pair that lie within the margin of
- * their threshold: the near-plane cull, the ceil of the radius, each of the four edges of
- * the tile rectangle (lower/upper x, lower/upper y), and the f32 rounding of the depth
- * key (which changes the key bits but, short of an exact depth tie, not the order). */
-#define ORC_NEAR_PLANE 1
-#define ORC_NEAR_RHO 2
-#define ORC_NEAR_X0 4
-#define ORC_NEAR_X1 8
-#define ORC_NEAR_Y0 16
-#define ORC_NEAR_Y1 32
+/* The f32 rounding of the depth key lies within 1e-12 of a rounding midpoint (the key
+ * bits may differ; the order does not, short of an exact depth tie). */
 #define ORC_NEAR_Z 64
 
-/* Projection of one Gaussian into one view. */
+/* Projection of one Gaussian into one view. The FP32 fields are the decision values
+ * (the kernel's arithmetic); the others are FP64 values. */
 typedef struct {
-    int32_t visible;            /* passed the near plane (t_z > 0.2) */
+    int32_t visible;            /* passed the near plane (FP32 t_z > 0.2) */
     int32_t tx0, tx1, ty0, ty1; /* inclusive tile rectangle; empty when tx0 > tx1 */
     int32_t ntiles;
-    int32_t near;               /* bit mask of decisions within the margin (ORC_NEAR_*) */
+    int32_t near;               /* ORC_NEAR_Z or 0 */
     int32_t pad_;
     double mu[3];               /* world-space centre */
     double t[3];                /* view-space centre */
@@ -84,10 +84,13 @@ typedef struct {
     double cov[3];              /* 2D covariance (xx, xy, yy) */
     double conic[3];            /* its inverse (a, b, c) */
     double o;                   /* sigmoid(logit) */
-    double rho;                 /* integer pixel radius */
+    double rho;                 /* integer pixel radius (FP32 decision) */
     double zf;                  /* t_z rounded once to f32 */
     double s;                   /* scale */
     double color[3];
+    float pf[2];                /* FP32 pixel-space mean */
+    float conicf[3];            /* FP32 conic */
+    float of;                   /* FP32 opacity */
 } orc_proj;
 
 /* Per view, per pixel forward outputs. */

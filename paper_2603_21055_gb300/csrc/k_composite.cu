@@ -247,7 +247,8 @@ __global__ void __launch_bounds__(kBlock) k_composite_bwd(const __grid_constant_
                         if (gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) {
                             contrib = true;
                             const float om = __fsub_rn(1.0f, alpha);
-                            const float Ti = __fdiv_rn(T, om);
+                            const float rom = __fdividef(1.0f, om);     // om >= 0.01: fast reciprocal
+                            const float Ti = T * rom;
                             const float w = alpha * Ti;
                             val[0] = w * gr;
                             val[1] = w * gg;
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(kBlock) k_composite_bwd(const __grid_constant_
                             val[3] = w * gD;
                             const float dal = Ti * ((st.c.x - SCr) * gr + (st.c.y - SCg) * gg + (st.c.z - SCb) * gb +
                                                     (st.c.w - SD) * gD + (1.0f - SA) * gA) -
-                                              (Tf / om) * bgdot;
+                                              (Tf * rom) * bgdot;
                             SCr = alpha * st.c.x + om * SCr;
                             SCg = alpha * st.c.y + om * SCg;
                             SCb = alpha * st.c.z + om * SCb;
@@ -273,10 +274,19 @@ __global__ void __launch_bounds__(kBlock) k_composite_bwd(const __grid_constant_
                             T = Ti;
                         }
                     }
-                    if (__any_sync(kFull, contrib)) {
-                        const float total = warp_reduce_scatter16(val, lane);
-                        const int slot = lane >> 1;
-                        if ((lane & 1) == 0 && slot < 10) atomicAdd(&acc[jj][slot], total);
+                    const uint32_t cm = __ballot_sync(kFull, contrib);
+                    if (cm != 0) {
+                        if (__popc(cm) <= 3) {
+                            // few contributors: add each lane's moments directly (<= 3-way conflicts)
+                            if (contrib) {
+#pragma unroll
+                                for (int q = 0; q < 10; ++q) atomicAdd(&acc[jj][q], val[q]);
+                            }
+                        } else {
+                            const float total = warp_reduce_scatter16(val, lane);
+                            const int slot = lane >> 1;
+                            if ((lane & 1) == 0 && slot < 10) atomicAdd(&acc[jj][slot], total);
+                        }
                     }
                 }
             }

@@ -19,6 +19,9 @@ constexpr float kDilation = 0.3f;         // px^2 added to the 2D covariance dia
 constexpr float kAlphaCap = 0.99f;
 constexpr float kAlphaFloor = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;
+// Below this exponent alpha = o e^power < e^power < (1/255) e^-0.0012 for any opacity
+// o <= 1, so the entry is skipped whatever the rounding of exp: ln(1/255) = -5.54126.
+constexpr float kPowerSkip = -5.5425f;
 constexpr uint32_t kInvalidTile = 0xffffffffu;
 
 // ------------------------------------------------------------ launch parameters
@@ -295,7 +298,7 @@ __device__ __forceinline__ bool gauss_alpha(const Staged &s, float qx, float qy,
     dy = __fsub_rn(s.a.y, qy);
     const float quad = __fmaf_rn(s.b.x, __fmul_rn(dx, dx), __fmul_rn(s.b.z, __fmul_rn(dy, dy)));
     const float power = __fsub_rn(__fmul_rn(-0.5f, quad), __fmul_rn(s.b.y, __fmul_rn(dx, dy)));
-    if (power > 0.0f) return false;
+    if (power > 0.0f || power < kPowerSkip) return false;
     ep = __expf(power);
     const float raw = __fmul_rn(s.b.w, ep);
     alpha = fminf(kAlphaCap, raw);

@@ -195,13 +195,15 @@ def test_two_gaussians_ordering_closed_form(swap):
 
 def test_transmittance_stop_excludes_entry():
     """Stop rule: an entry whose acceptance would take T below 1e-4 is excluded and ends
-    the walk. Four Gaussians with alpha = 0.99 at the centre pixel: after two, T = 1e-4;
-    the third would give 1e-6 < 1e-4, so exactly two contribute there."""
-    kfs = [one_gaussian_kf(z, 9.0, (1, 1, 1), z / 64.0) for z in (2.0, 2.5, 3.0, 3.5)]
+    the walk. At the centre pixel alphas are 0.99 (capped), 0.9, 0.99, 0.99 front to
+    back: after two, T = 1e-3; the third would give 1e-5 < 1e-4, so exactly two
+    contribute (all products well away from the threshold)."""
+    l9 = math.log(0.9 / 0.1)
+    kfs = [one_gaussian_kf(z, l, (1, 1, 1), z / 64.0) for z, l in ((2.0, 9.0), (2.5, l9), (3.0, 9.0), (3.5, 9.0))]
     out = oracle.render(scene_of(kfs, [identity_view()]))[0]
     assert out["n_contrib"][16, 16] == 2
-    np.testing.assert_allclose(out["t_final"][16, 16], 0.01 * 0.01, rtol=1e-12)
-    np.testing.assert_allclose(out["depth"][16, 16], 0.99 * 2.0 + 0.01 * 0.99 * 2.5, rtol=1e-12)
+    np.testing.assert_allclose(out["t_final"][16, 16], 0.01 * 0.1, rtol=1e-6)
+    np.testing.assert_allclose(out["depth"][16, 16], 0.99 * 2.0 + 0.01 * 0.9 * 2.5, rtol=1e-6)
 
 
 def test_invariants_and_zero_opacity(scene1):
@@ -224,21 +226,36 @@ def test_invariants_and_zero_opacity(scene1):
 
 # ------------------------------------------------------------- brute-force pins
 
+def _fmaf(a, b, c):
+    # the float32 product is exact in float64; one float64 rounding, then one to float32
+    return np.float32(float(a) * float(b) + float(c))
+
+
 def _composite_python(P, order, qx, qy):
-    T, C, D = 1.0, np.zeros(3), 0.0
+    """Per-pixel compositing written out directly: branches in float32 from the oracle's
+    single-precision decision values, accumulation in float64."""
+    f32 = np.float32
+    T, Tf, C, D = 1.0, f32(1.0), np.zeros(3), 0.0
     last = -1
     for pos, g in enumerate(order):
         r = P[g]
-        dx, dy = r["p"][0] - qx, r["p"][1] - qy
-        a_, b_, c_ = r["conic"]
-        power = -0.5 * (a_ * dx * dx + c_ * dy * dy) - b_ * dx * dy
+        dxf, dyf = f32(r["pf"][0] - f32(qx)), f32(r["pf"][1] - f32(qy))
+        a_, b_, c_ = r["conicf"]
+        quad = _fmaf(a_, f32(dxf * dxf), f32(c_ * f32(dyf * dyf)))
+        power = f32(f32(f32(-0.5) * quad) - f32(b_ * f32(dxf * dyf)))
         if power > 0:
             continue
-        alpha = min(0.99, r["o"] * math.exp(power))
-        if alpha < ALPHA_FLOOR:
+        raw = f32(r["of"] * f32(math.exp(float(power))))
+        alphaf = min(f32(0.99), raw)
+        if alphaf < f32(1.0 / 255.0):
             continue
-        if T * (1 - alpha) < 1e-4:
+        test = f32(Tf * f32(f32(1.0) - alphaf))
+        if test < f32(1e-4):
             break
+        Tf = test
+        dx, dy = r["p"][0] - qx, r["p"][1] - qy
+        a64, b64, c64 = r["conic"]
+        alpha = 0.99 if raw > f32(0.99) else r["o"] * math.exp(-0.5 * (a64 * dx * dx + c64 * dy * dy) - b64 * dx * dy)
         C += alpha * T * r["color"]
         D += alpha * T * r["t"][2]
         T *= 1 - alpha
