@@ -103,8 +103,8 @@ def lib():
             l.orc_render.argtypes = [P, C.c_int32, P, C.c_int32, P, P]
             l.orc_render_pixels.argtypes = [P, C.c_int32, P, C.c_int32, P, C.c_int64, P, P, P, P, P, P,
                                             P, P, P]
-            l.orc_backward.argtypes = [P, C.c_int32, P, C.c_int32, P, P, P, P]
-            l.orc_backward_gaussians.argtypes = [P, C.c_int32, P, C.c_int32, P, P, C.c_int64, P, P, P]
+            l.orc_backward.argtypes = [P, C.c_int32, P, C.c_int32, P, P, P, P, P]
+            l.orc_backward_gaussians.argtypes = [P, C.c_int32, P, C.c_int32, P, P, C.c_int64, P, P, P, P]
             l.orc_decision_hash.restype = C.c_uint64
             l.orc_decision_hash.argtypes = [P, C.c_int32, P, C.c_int32, P]
             l.orc_l1_loss.restype = C.c_double
@@ -222,8 +222,9 @@ def _image_grads(scene, grads_in):
 def backward(scene, grads_in, o: Opts = None):
     """Adjoint of the render. grads_in: per view dict with 'rgb' (3,H,W), 'depth',
     'alpha' (missing entries are zero). Returns per keyframe dict d_offset, d_rgb,
-    d_logit, d_scale (zeros for fixed keyframes) and 'near' (H, W): Gaussians reached by a
-    pixel with a near decision, whose gradient FP32 may legitimately change."""
+    d_logit, d_scale (zeros for fixed keyframes), 'near' (H, W): Gaussians reached by a
+    pixel with a near decision, whose gradient FP32 may legitimately change, and 'abs':
+    per attribute the sum over views and pixels of |each pixel's contribution|."""
     o = o or opts()
     inp = _Inputs(scene)
     gi, keep = _image_grads(scene, grads_in)
@@ -235,11 +236,16 @@ def backward(scene, grads_in, o: Opts = None):
         outs.append(d)
         gk[i] = KfGrads(*[_ptr(d[q]) for q in ("d_offset", "d_rgb", "d_logit", "d_scale")])
     near = np.zeros(num_gaussians(scene), np.uint8)
-    lib().orc_backward(inp.kfs, inp.n_kf, inp.views, inp.n_views, C.byref(o), gi, gk, _ptr(near))
+    absum = np.zeros((num_gaussians(scene), 6))
+    lib().orc_backward(inp.kfs, inp.n_kf, inp.views, inp.n_views, C.byref(o), gi, gk, _ptr(near), _ptr(absum))
     base = 0
     for d, k in zip(outs, scene.keyframes):
         n = k.cam.width * k.cam.height
-        d["near"] = near[base:base + n].reshape(k.cam.height, k.cam.width).astype(bool)
+        h, w = k.cam.height, k.cam.width
+        d["near"] = near[base:base + n].reshape(h, w).astype(bool)
+        a = absum[base:base + n]
+        d["abs"] = dict(d_offset=a[:, 0].reshape(h, w), d_rgb=a[:, 1:4].T.reshape(3, h, w),
+                        d_logit=a[:, 4].reshape(h, w), d_scale=a[:, 5].reshape(h, w))
         base += n
     del keep
     return outs
@@ -247,17 +253,19 @@ def backward(scene, grads_in, o: Opts = None):
 
 def backward_gaussians(scene, grads_in, sel, o: Opts = None):
     """Adjoint for selected global Gaussian indices: ((n, 6) array of (d_offset, d_r, d_g,
-    d_b, d_logit, d_scale), (n,) bool near flags as in backward())."""
+    d_b, d_logit, d_scale), (n,) bool near flags and (n, 6) contribution magnitudes as in
+    backward())."""
     o = o or opts()
     inp = _Inputs(scene)
     gi, keep = _image_grads(scene, grads_in)
     s = np.ascontiguousarray(sel, np.int64)
     out = np.zeros((s.shape[0], 6))
     near = np.zeros(s.shape[0], np.uint8)
+    absum = np.zeros((s.shape[0], 6))
     lib().orc_backward_gaussians(inp.kfs, inp.n_kf, inp.views, inp.n_views, C.byref(o), gi, s.shape[0],
-                                 _ptr(s), _ptr(out), _ptr(near))
+                                 _ptr(s), _ptr(out), _ptr(near), _ptr(absum))
     del keep
-    return out, near.astype(bool)
+    return out, near.astype(bool), absum
 
 
 def decision_hash(scene, o: Opts = None) -> int:

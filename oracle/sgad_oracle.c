@@ -592,10 +592,10 @@ static void chain_params(const orc_kf *kf, int64_t j, const orc_cam *view, const
 /* Walk the given tiles of one view and accumulate per-entry 2D gradients into g2d
  * (indexed by global Gaussian). Tiles are processed in parallel in chunks; each chunk's
  * per-entry contributions are merged in tile order, so the sum is deterministic. */
-static void view_adjoint_tiles(const orc_proj *proj, const tile_lists *L, const orc_cam *view,
-                               const orc_opts *opt, const orc_image_grads *gi, const int32_t *tiles,
-                               int32_t n_tiles, const int64_t *slot, double (*g2d)[G_N],
-                               const uint8_t *near_img, uint8_t *near_out)
+static void view_adjoint_tiles(const orc_kf *kfs, int32_t n_kf, const orc_proj *proj, const tile_lists *L,
+                               const orc_cam *view, const orc_opts *opt, const orc_image_grads *gi,
+                               const int32_t *tiles, int32_t n_tiles, const int64_t *slot, double (*g2d)[G_N],
+                               double (*gabs)[6], uint8_t *near_out)
 {
     const int32_t W = view->width, H = view->height;
     const int64_t hw = (int64_t)W * H;
@@ -603,6 +603,7 @@ static void view_adjoint_tiles(const orc_proj *proj, const tile_lists *L, const 
     for (int32_t c0 = 0; c0 < n_tiles; c0 += chunk) {
         const int32_t c1 = c0 + chunk < n_tiles ? c0 + chunk : n_tiles;
         double (**acc)[G_N] = (double (**)[G_N])calloc((size_t)(c1 - c0), sizeof(*acc));
+        double (**aacc)[6] = (double (**)[6])calloc((size_t)(c1 - c0), sizeof(*aacc));
         uint8_t **nacc = (uint8_t **)calloc((size_t)(c1 - c0), sizeof(*nacc));
 #pragma omp parallel for schedule(dynamic, 1)
         for (int32_t ci = c0; ci < c1; ++ci) {
@@ -610,6 +611,7 @@ static void view_adjoint_tiles(const orc_proj *proj, const tile_lists *L, const 
             const int64_t n = L->off[t + 1] - L->off[t];
             const list_entry *list = L->e + L->off[t];
             double (*a)[G_N] = (double (*)[G_N])calloc((size_t)(n + 1), sizeof(*a));
+            double (*ab)[6] = gabs ? (double (*)[6])calloc((size_t)(n + 1), sizeof(*ab)) : NULL;
             uint8_t *nf = (uint8_t *)calloc((size_t)(n + 1), 1);
             double (*pa)[G_N] = (double (*)[G_N])calloc((size_t)(n + 1), sizeof(*pa));
             walk_rec *rec = (walk_rec *)malloc(sizeof(walk_rec) * (size_t)(n + 1));
@@ -624,7 +626,17 @@ static void view_adjoint_tiles(const orc_proj *proj, const tile_lists *L, const 
                     pixel_adjoint(proj, rec, o.n_rec, o.T, gC, gi->d_depth[pix], gi->d_alpha[pix], opt, pa);
                     for (int32_t r = 0; r < o.n_rec; ++r)
                         for (int q = 0; q < G_N; ++q) a[rec[r].pos][q] += pa[r][q];
-                    if (o.near || (near_img && near_img[pix])) {
+                    if (ab) {
+                        /* magnitude of this pixel's contribution to each parameter gradient */
+                        for (int32_t r = 0; r < o.n_rec; ++r) {
+                            int64_t j;
+                            const int32_t ki = owner(kfs, n_kf, rec[r].g, &j);
+                            double o6[6];
+                            chain_params(&kfs[ki], j, view, &proj[rec[r].g], pa[r], o6);
+                            for (int q = 0; q < 6; ++q) ab[rec[r].pos][q] += fabs(o6[q]);
+                        }
+                    }
+                    if (o.near) {
                         /* entries up to the stop whose alpha is at or near the floor here */
                         const int64_t end = o.end < n ? o.end + 1 : n;
                         for (int64_t i = 0; i < end; ++i) {
@@ -639,6 +651,7 @@ static void view_adjoint_tiles(const orc_proj *proj, const tile_lists *L, const 
             free(rec);
             free(pa);
             acc[ci - c0] = a;
+            aacc[ci - c0] = ab;
             nacc[ci - c0] = nf;
         }
         for (int32_t ci = c0; ci < c1; ++ci) {
@@ -649,20 +662,26 @@ static void view_adjoint_tiles(const orc_proj *proj, const tile_lists *L, const 
                 const int64_t s = slot ? slot[list[i].g] : (int64_t)list[i].g;
                 if (s < 0) continue;
                 for (int q = 0; q < G_N; ++q) g2d[s][q] += acc[ci - c0][i][q];
+                if (gabs)
+                    for (int q = 0; q < 6; ++q) gabs[s][q] += aacc[ci - c0][i][q];
                 if (near_out && nacc[ci - c0][i]) near_out[s] = 1;
             }
             free(acc[ci - c0]);
+            free(aacc[ci - c0]);
             free(nacc[ci - c0]);
         }
         free(acc);
+        free(aacc);
         free(nacc);
     }
 }
 
 int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int32_t n_views,
                      const orc_opts *opt, const orc_image_grads *grad_in, orc_kf_grads *grads,
-                     uint8_t *near_gauss)
+                     uint8_t *near_gauss, double *abs_out)
 {
+    double (*gabs)[6] = (double (*)[6])abs_out;
+    if (gabs) memset(gabs, 0, sizeof(*gabs) * (size_t)orc_num_gaussians(kfs, n_kf));
     const int64_t nG = orc_num_gaussians(kfs, n_kf);
     orc_proj *proj = (orc_proj *)malloc(sizeof(orc_proj) * (size_t)nG);
     double (*g2d)[G_N] = (double (*)[G_N])malloc(sizeof(*g2d) * (size_t)nG);
@@ -676,7 +695,7 @@ int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int3
         int32_t *tiles = (int32_t *)malloc(sizeof(int32_t) * (size_t)nt);
         for (int32_t t = 0; t < nt; ++t) tiles[t] = t;
         memset(g2d, 0, sizeof(*g2d) * (size_t)nG);
-        view_adjoint_tiles(proj, &L, &views[k], opt, &grad_in[k], tiles, nt, NULL, g2d, NULL, near_gauss);
+        view_adjoint_tiles(kfs, n_kf, proj, &L, &views[k], opt, &grad_in[k], tiles, nt, NULL, g2d, gabs, near_gauss);
         for (int64_t g = 0; g < nG; ++g) {
             if (!(proj[g].ntiles > 0)) continue;
             int64_t j;
@@ -713,8 +732,9 @@ int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int3
 int32_t orc_backward_gaussians(const orc_kf *kfs, int32_t n_kf, const orc_cam *views,
                                int32_t n_views, const orc_opts *opt,
                                const orc_image_grads *grad_in, int64_t n_sel,
-                               const int64_t *sel, double *out, uint8_t *near_sel)
+                               const int64_t *sel, double *out, uint8_t *near_sel, double *abs_sel)
 {
+    if (abs_sel) memset(abs_sel, 0, sizeof(double) * 6 * (size_t)n_sel);
     if (near_sel) memset(near_sel, 0, (size_t)n_sel);
     const int64_t nG = orc_num_gaussians(kfs, n_kf);
     orc_proj *proj = (orc_proj *)malloc(sizeof(orc_proj) * (size_t)nG);
@@ -740,7 +760,8 @@ int32_t orc_backward_gaussians(const orc_kf *kfs, int32_t n_kf, const orc_cam *v
         for (int32_t t = 0; t < nt; ++t)
             if (want[t]) tiles[nw++] = t;
         memset(g2d, 0, sizeof(*g2d) * (size_t)(n_sel + 1));
-        view_adjoint_tiles(proj, &L, &views[k], opt, &grad_in[k], tiles, nw, slot, g2d, NULL, near_sel);
+        view_adjoint_tiles(kfs, n_kf, proj, &L, &views[k], opt, &grad_in[k], tiles, nw, slot, g2d,
+                           (double (*)[6])abs_sel, near_sel);
         for (int64_t s = 0; s < n_sel; ++s) {
             const int64_t g = sel[s];
             if (!(proj[g].ntiles > 0)) continue;

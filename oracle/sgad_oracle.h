@@ -29,8 +29,9 @@
  * same formulas in the same order with IEEE single-precision operations (fmaf where the
  * kernel fuses). Binning therefore matches the kernel bit for bit. The alpha decisions
  * involve exp, whose single-precision implementations differ in the last bits, so they
- * are reported "near" when within 1e-6 relative of their threshold (the transmittance
- * stop, which accumulates those differences, within 5e-5). The depth key is t_z
+ * are reported "near" when within opts.margin (4e-6) relative of their threshold (the
+ * transmittance stop, which accumulates those differences, within opts.t_margin, 2e-4).
+ * The depth key is t_z
  * evaluated in FP64 and rounded once to f32; it is near when within 1e-12 relative of an
  * f32 rounding midpoint.
  */
@@ -62,8 +63,8 @@ typedef struct {
 typedef struct {
     int32_t tile_w, tile_h;
     double bg[3];               /* background colour */
-    double margin;              /* relative margin of the alpha floor/cap decisions (1e-6) */
-    double t_margin;            /* relative margin of the transmittance stop (5e-5) */
+    double margin;              /* relative margin of the alpha floor/cap decisions (4e-6) */
+    double t_margin;            /* relative margin of the transmittance stop (2e-4) */
 } orc_opts;
 
 /* The f32 rounding of the depth key lies within 1e-12 of a rounding midpoint (the key
@@ -149,19 +150,23 @@ int32_t orc_render_pixels(const orc_kf *kfs, int32_t n_kf, const orc_cam *views,
  * gradient arrays of learnable keyframes; fixed keyframes are not touched.
  * near_gauss (optional, one byte per Gaussian, global index) is set to 1 for every
  * Gaussian whose alpha passes (or nearly passes) the floor at a pixel with a near
- * decision: its gradient includes a term FP32 may legitimately drop or add. */
+ * decision: its gradient includes a term FP32 may legitimately drop or add.
+ * abs_out (optional, [n_gaussians][6] in the order d_offset, d_r, d_g, d_b, d_logit,
+ * d_scale) receives, per Gaussian, the sum over views and pixels of the absolute value
+ * of each pixel's contribution: the scale against which the rounding error of a sum
+ * with cancellation is measured. */
 int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int32_t n_views,
                      const orc_opts *opt, const orc_image_grads *grad_in, orc_kf_grads *grads,
-                     uint8_t *near_gauss);
+                     uint8_t *near_gauss, double *abs_out);
 
 /* Adjoint restricted to a list of Gaussians (global indices): out[n][6] =
  * (d_offset, d_r, d_g, d_b, d_logit, d_scale). Only the tiles these Gaussians touch are
- * walked, so it runs on full-size scenes. near_sel (optional, n bytes) as near_gauss
- * above for the selected Gaussians. */
+ * walked, so it runs on full-size scenes. near_sel (optional, n bytes) and abs_sel
+ * (optional, [n][6]) as near_gauss and abs_out above for the selected Gaussians. */
 int32_t orc_backward_gaussians(const orc_kf *kfs, int32_t n_kf, const orc_cam *views,
                                int32_t n_views, const orc_opts *opt,
                                const orc_image_grads *grad_in, int64_t n_sel,
-                               const int64_t *sel, double *out, uint8_t *near_sel);
+                               const int64_t *sel, double *out, uint8_t *near_sel, double *abs_sel);
 
 /* Fingerprint of every discrete decision of a forward pass (binning and, per pixel, the
  * accepted entries and the stopping point). Two parameter sets with equal fingerprints

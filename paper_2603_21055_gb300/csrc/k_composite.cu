@@ -274,19 +274,10 @@ __global__ void __launch_bounds__(kBlock) k_composite_bwd(const __grid_constant_
                             T = Ti;
                         }
                     }
-                    const uint32_t cm = __ballot_sync(kFull, contrib);
-                    if (cm != 0) {
-                        if (__popc(cm) <= 3) {
-                            // few contributors: add each lane's moments directly (<= 3-way conflicts)
-                            if (contrib) {
-#pragma unroll
-                                for (int q = 0; q < 10; ++q) atomicAdd(&acc[jj][q], val[q]);
-                            }
-                        } else {
-                            const float total = warp_reduce_scatter16(val, lane);
-                            const int slot = lane >> 1;
-                            if ((lane & 1) == 0 && slot < 10) atomicAdd(&acc[jj][slot], total);
-                        }
+                    if (__any_sync(kFull, contrib)) {
+                        const float total = warp_reduce_scatter16(val, lane);
+                        const int slot = lane >> 1;
+                        if ((lane & 1) == 0 && slot < 10) atomicAdd(&acc[jj][slot], total);
                     }
                 }
             }

@@ -105,18 +105,16 @@ def compare_images(res, ref, atol=IMAGE_ATOL):
     return worst, n_near
 
 
-def grad_error(g_gpu, g_ref, rtol=GRAD_RTOL, floor=1e-6):
-    """Max over entries of |gpu - ref| / (rtol |ref| + floor * max|ref|) (<= 1 passes)."""
-    scale = np.abs(g_ref).max()
-    den = rtol * np.abs(g_ref) + floor * max(scale, 1e-30)
-    return float((np.abs(g_gpu.astype(np.float64) - g_ref) / den).max())
+GRAD_ABS_RTOL = 1e-4       # FP32 error per summed term, relative to the term's magnitude
 
 
-def compare_grads(res, ref_grads, rtol=GRAD_RTOL, floor=1e-6, near_ratio=50.0, max_near_frac=0.1):
-    """Gradients within rtol |ref| + floor max|ref| on every Gaussian the oracle does not
-    flag as reached by a near decision; flagged ones (at most max_near_frac of them) only
-    within near_ratio times that. Returns the worst ratio on clean Gaussians (<= 1
-    passes) and asserts the rest."""
+def compare_grads(res, ref_grads, rtol=GRAD_RTOL, abs_rtol=GRAD_ABS_RTOL, near_ratio=50.0, max_near_frac=0.1):
+    """Gradients within rtol |ref| + abs_rtol A, where A is the sum of the magnitudes of
+    the per-pixel contributions the oracle reports (a gradient is a sum over pixels and
+    views whose terms can cancel; FP32 carries an error proportional to the terms, not
+    to their sum). Gaussians the oracle flags as reached by a near decision are held only
+    to near_ratio times that, and must be at most max_near_frac of all. Returns the worst
+    ratio on the others (<= 1 passes)."""
     worst, n_flag, n_all = 0.0, 0, 0
     for g, r in zip(res["grads"], ref_grads):
         if g is None:
@@ -125,10 +123,9 @@ def compare_grads(res, ref_grads, rtol=GRAD_RTOL, floor=1e-6, near_ratio=50.0, m
         n_flag += int(nr.sum())
         n_all += nr.size
         for q in ("d_offset", "d_rgb", "d_logit", "d_scale"):
-            gq, rq = g[q].astype(np.float64), r[q]
+            gq, rq, aq = g[q].astype(np.float64), r[q], r["abs"][q]
             assert np.all(np.isfinite(gq)), q
-            scale = np.abs(rq).max()
-            ratio = np.abs(gq - rq) / (rtol * np.abs(rq) + floor * max(scale, 1e-30))
+            ratio = np.abs(gq - rq) / (rtol * np.abs(rq) + abs_rtol * aq + 1e-30)
             clean = np.broadcast_to(~nr, ratio.shape)
             if clean.any():
                 worst = max(worst, float(ratio[clean].max()))

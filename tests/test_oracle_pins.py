@@ -418,6 +418,18 @@ def test_adjoint_sign_at_zero_and_mirror():
     assert z["d_scale"][0, 0] != 0.0
 
 
+def test_contribution_magnitudes_bound_the_gradient(scene1):
+    """The reported magnitude A (sum of |per-pixel contributions|) is >= |gradient| by the
+    triangle inequality, and equals it when every contribution has one sign: with an
+    all-positive colour gradient image, d_rgb = sum alpha T g > 0 term by term."""
+    g = [dict(rgb=np.ones((3, 48, 64)), depth=np.linspace(-1, 1, 48 * 64).reshape(48, 64))]
+    out = oracle.backward(scene1, g)[0]
+    for q in ("d_offset", "d_rgb", "d_logit", "d_scale"):
+        assert np.all(out["abs"][q] >= np.abs(out[q]) * (1 - 1e-12) - 1e-300)
+    np.testing.assert_allclose(out["abs"]["d_rgb"], out["d_rgb"], rtol=1e-12)
+    assert np.any(out["abs"]["d_offset"] > 1.5 * np.abs(out["d_offset"]))   # cancellation exists
+
+
 def test_fixed_keyframes_get_no_gradient(scene1):
     """Eq. 1 learns only the current frame's Gaussians; neighbours are fixed (Sec. 3.2)."""
     k = scene1.keyframes[0]
