@@ -108,13 +108,15 @@ def compare_images(res, ref, atol=IMAGE_ATOL):
 GRAD_ABS_RTOL = 1e-4       # FP32 error per summed term, relative to the term's magnitude
 
 
-def compare_grads(res, ref_grads, rtol=GRAD_RTOL, abs_rtol=GRAD_ABS_RTOL, near_ratio=50.0, max_near_frac=0.1):
-    """Gradients within rtol |ref| + abs_rtol A, where A is the sum of the magnitudes of
-    the per-pixel contributions the oracle reports (a gradient is a sum over pixels and
-    views whose terms can cancel; FP32 carries an error proportional to the terms, not
-    to their sum). Gaussians the oracle flags as reached by a near decision are held only
-    to near_ratio times that, and must be at most max_near_frac of all. Returns the worst
-    ratio on the others (<= 1 passes)."""
+def compare_grads(res, ref_grads, rtol=GRAD_RTOL, abs_rtol=GRAD_ABS_RTOL, floor=1e-6, near_ratio=50.0,
+                  max_near_frac=0.1):
+    """Gradients within rtol |ref| + abs_rtol A + floor max|ref|, where A is the sum of
+    the magnitudes of the per-pixel contributions the oracle reports (a gradient is a sum
+    over pixels and views whose terms can cancel; FP32 carries an error proportional to
+    the terms, not to their sum) and the floor covers near-zero entries whose single
+    contributions cancel inside the chain rule. Gaussians the oracle flags as reached by
+    a near decision are held only to near_ratio times that, and must be at most
+    max_near_frac of all. Returns the worst ratio on the others (<= 1 passes)."""
     worst, n_flag, n_all = 0.0, 0, 0
     for g, r in zip(res["grads"], ref_grads):
         if g is None:
@@ -125,7 +127,7 @@ def compare_grads(res, ref_grads, rtol=GRAD_RTOL, abs_rtol=GRAD_ABS_RTOL, near_r
         for q in ("d_offset", "d_rgb", "d_logit", "d_scale"):
             gq, rq, aq = g[q].astype(np.float64), r[q], r["abs"][q]
             assert np.all(np.isfinite(gq)), q
-            ratio = np.abs(gq - rq) / (rtol * np.abs(rq) + abs_rtol * aq + 1e-30)
+            ratio = np.abs(gq - rq) / (rtol * np.abs(rq) + abs_rtol * aq + floor * np.abs(rq).max() + 1e-30)
             clean = np.broadcast_to(~nr, ratio.shape)
             if clean.any():
                 worst = max(worst, float(ratio[clean].max()))

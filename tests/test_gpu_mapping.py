@@ -99,7 +99,10 @@ def test_autograd_function_matches_direct_backward(scene1):
 
 def test_graph_replay_equals_eager_iterations(room2):
     """Three mapping iterations replayed from one captured CUDA graph give the same
-    parameters as three eager iterations (up to the order of float atomics)."""
+    parameters as three eager iterations. The gradients differ only by the order of float
+    atomics; Adam normalises each gradient by its running RMS, so a near-zero gradient's
+    update may change by up to its full step (lr) per iteration: all but a few elements
+    agree to 1e-3, and none differs by more than 2 lr per iteration."""
     import torch
     from paper_2603_21055_gb300.mapping import Mapper
     from paper_2603_21055_gb300.synth import crop_scene
@@ -116,7 +119,11 @@ def test_graph_replay_equals_eager_iterations(room2):
     for ka, kb in zip(a.kfs, b.kfs):
         for n in ("offset", "rgb", "logit", "scale"):
             x, y = getattr(ka, n).cpu().numpy(), getattr(kb, n).cpu().numpy()
-            np.testing.assert_allclose(x, y, rtol=1e-3, atol=1e-5 * np.abs(x).max())
+            if n == "scale":                      # Adam runs on log s
+                x, y = np.log(x), np.log(y)
+            close = np.isclose(x, y, rtol=1e-3, atol=1e-5 * np.abs(x).max())
+            assert close.mean() > 0.999, (n, close.mean())
+            assert np.abs(x - y).max() <= 2 * 3 * a.lr[n] + 1e-6, (n, np.abs(x - y).max())
 
 
 def test_mapping_reduces_loss_and_raises_psnr(room2):
