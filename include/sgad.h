@@ -272,6 +272,29 @@ typedef struct {
 sgad_status sgad_adam_step_multi(int32_t n_tensors, const sgad_adam_tensor *tensors, float beta1,
                                  float beta2, float eps, int32_t *step_counter, void *stream);
 
+/* Forward splatting that allocates nothing, for callers that cannot allocate device
+ * memory (code running in a host callback or a real-time loop where cudaMalloc would
+ * stall the device, or an application whose memory manager owns every allocation and
+ * hands this library only its input and output buffers). The paper has no counterpart:
+ * this is an interface convenience around sgad_forward().
+ *
+ * Same arguments and results as sgad_forward(), without the workspace: the scratch is a
+ * static device array of SGAD_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
+ * that loads the library holds until the process exits. Problems whose workspace does
+ * not fit (64 B per Gaussian, 8 B per view pixel, 16 B per key, plus per-tile offsets)
+ * are rejected with SGAD_ERR_WORKSPACE_TOO_SMALL before anything is launched; a forward
+ * whose keys exceed the room left returns SGAD_ERR_KEY_OVERFLOW. The call synchronises
+ * `stream` to report that status. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture on that
+ * device. All calls share the one array and it keeps the last call's contents: calls
+ * that may run concurrently on the GPU (different streams or threads) race and must be
+ * serialised by the caller. No backward pass is offered this way (its state would live
+ * in the shared array). */
+#define SGAD_NOALLOC_SCRATCH_BYTES (64u << 20)
+sgad_status sgad_forward_noalloc(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
+                                 const sgad_camera *views, int32_t n_views, sgad_images *out,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ SGAD_MAX_VIEWS = 64
 EXPORTS = ["sgad_default_options", "sgad_create", "sgad_destroy", "sgad_last_error", "sgad_workspace_size",
            "sgad_count_keys", "sgad_forward", "sgad_backward", "sgad_check", "sgad_state", "sgad_read_stats",
            "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_adam_step",
-           "sgad_adam_step_multi"]
+           "sgad_adam_step_multi", "sgad_forward_noalloc"]
 SGAD_NUM_STAGES = 6
 STAGE_NAMES = ["binning", "emit", "sort", "composite_fwd", "composite_bwd", "finalize"]
 
@@ -116,6 +116,7 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         "sgad_l1_loss_grad": (st, [I32, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P]),
         "sgad_adam_step": (st, [I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I32, I32, P]),
         "sgad_adam_step_multi": (st, [I32, P, C.c_float, C.c_float, C.c_float, P, P]),
+        "sgad_forward_noalloc": (st, [P, P, I32, P, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(l, name)
@@ -236,3 +237,9 @@ def sgad_adam_step_multi(tensors, beta1: float, beta2: float, eps: float, step_c
     """tensors: a ctypes array of sgad_adam_tensor; step_counter: device int32 address."""
     _call("sgad_adam_step_multi", len(tensors), tensors, float(beta1), float(beta2), float(eps), step_counter,
           stream)
+
+
+def sgad_forward_noalloc(ctx, kfs, views, out, stream: int) -> None:
+    """Forward splatting into `out` with the library's static scratch (no workspace, no
+    allocation); synchronises `stream`."""
+    _call("sgad_forward_noalloc", ctx, kfs, len(kfs), views, len(views), out, stream)

@@ -59,6 +59,18 @@ sgad_status cuda_fail(cudaError_t e, const char *what)
     return fail(SGAD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+}  // namespace
+
+namespace sgad {
+// Records the message returned by sgad_last_error() for entry points in other files.
+sgad_status report_error(sgad_status code, const char *msg)
+{
+    return fail(code, "%s", msg);
+}
+}  // namespace sgad
+
+namespace {
+
 int ilog2_exact(int x)
 {
     int l = 0;
