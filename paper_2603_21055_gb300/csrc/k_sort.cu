@@ -14,49 +14,75 @@
 
 namespace sgad {
 
-constexpr int kSortThreads = 512;
+#ifndef SGAD_SORT_THREADS
+#define SGAD_SORT_THREADS 512
+#endif
+constexpr int kSortThreads = SGAD_SORT_THREADS;
 
-__device__ __forceinline__ void insertion_sort(uint64_t *a, int n)
+// Shared-memory index with one padding slot per 16 entries: each thread works on its own
+// run of consecutive entries, and without padding the 64-bit accesses of lanes whose runs
+// start 128 bytes apart would all hit the same two banks.
+template <bool kPad>
+__device__ __forceinline__ int pidx(int i)
+{
+    return kPad ? i + (i >> 4) : i;
+}
+
+template <bool kPad>
+__device__ __forceinline__ void insertion_sort(uint64_t *a, int lo, int n)
 {
     for (int i = 1; i < n; ++i) {
-        const uint64_t x = a[i];
+        const uint64_t x = a[pidx<kPad>(lo + i)];
         int j = i - 1;
-        while (j >= 0 && a[j] > x) {
-            a[j + 1] = a[j];
+        while (j >= 0 && a[pidx<kPad>(lo + j)] > x) {
+            a[pidx<kPad>(lo + j + 1)] = a[pidx<kPad>(lo + j)];
             --j;
         }
-        a[j + 1] = x;
+        a[pidx<kPad>(lo + j + 1)] = x;
     }
 }
 
-// Merged positions [k0, k1) of sorted runs A[0..la) and B[0..lb), written to out[k0..k1).
-__device__ __forceinline__ void merge_segment(const uint64_t *A, int la, const uint64_t *B, int lb, int k0, int k1,
-                                              uint64_t *out)
+// Merged positions [k0, k1) of the sorted runs src[a0 .. a0+la) and src[b0 .. b0+lb),
+// written to dst[d0 + k0 .. d0 + k1) (indices before padding).
+template <bool kPad>
+__device__ __forceinline__ void merge_segment(const uint64_t *src, int a0, int la, int b0, int lb, int k0, int k1,
+                                              uint64_t *dst, int d0)
 {
     int lo = k0 - lb > 0 ? k0 - lb : 0;
     int hi = k0 < la ? k0 : la;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (A[mid] <= B[k0 - 1 - mid])
+        if (src[pidx<kPad>(a0 + mid)] <= src[pidx<kPad>(b0 + k0 - 1 - mid)])
             lo = mid + 1;
         else
             hi = mid;
     }
     int i = lo, j = k0 - lo;
+    uint64_t va = i < la ? src[pidx<kPad>(a0 + i)] : ~0ull;
+    uint64_t vb = j < lb ? src[pidx<kPad>(b0 + j)] : ~0ull;
     for (int k = k0; k < k1; ++k) {
-        const bool take_a = j >= lb || (i < la && A[i] <= B[j]);
-        out[k] = take_a ? A[i++] : B[j++];
+        const bool take_a = j >= lb || (i < la && va <= vb);
+        if (take_a) {
+            dst[pidx<kPad>(d0 + k)] = va;
+            ++i;
+            va = i < la ? src[pidx<kPad>(a0 + i)] : ~0ull;
+        } else {
+            dst[pidx<kPad>(d0 + k)] = vb;
+            ++j;
+            vb = j < lb ? src[pidx<kPad>(b0 + j)] : ~0ull;
+        }
     }
 }
 
-// Sorts a[0..n) (n <= blockDim * C for the C computed here) using b as scratch; returns
-// the buffer holding the result. Works on shared or global pointers.
+// Sorts a[0..n) using b as scratch (both padded shared-memory buffers when kPad); returns
+// the buffer holding the result.
+template <bool kPad>
 __device__ uint64_t *block_merge_sort(uint64_t *a, uint64_t *b, int n)
 {
     const int T = blockDim.x;
     const int C = n > T ? (n + T - 1) / T : 1;
     const int lo = threadIdx.x * C;
-    if (lo < n) insertion_sort(a + lo, n - lo < C ? n - lo : C);
+    if (lo < n) insertion_sort<kPad>(a, lo, n - lo < C ? n - lo : C);
     __syncthreads();
     for (int w = C; w < n; w <<= 1) {
         const int k0 = threadIdx.x * C;
@@ -67,7 +93,7 @@ __device__ uint64_t *block_merge_sort(uint64_t *a, uint64_t *b, int n)
             const int lb = rest < w ? rest : w;
             int k1 = k0 + C;
             if (k1 > base + la + lb) k1 = base + la + lb;
-            merge_segment(a + base, la, a + base + la, lb, k0 - base, k1 - base, b + base);
+            merge_segment<kPad>(a, base, la, base + la, lb, k0 - base, k1 - base, b, base);
         }
         __syncthreads();
         uint64_t *t = a;
@@ -76,6 +102,8 @@ __device__ uint64_t *block_merge_sort(uint64_t *a, uint64_t *b, int n)
     }
     return a;
 }
+
+__host__ __device__ constexpr int padded(int n) { return n + (n >> 4) + 16; }
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *__restrict__ off,
                                                              uint64_t *__restrict__ entries,
@@ -88,22 +116,22 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *__r
     const uint32_t s = off[t];
     const int n = (int)(off[t + 1] - s);
     if (n <= 1) return;
-    uint64_t *a = smem, *b = smem + cap;
+    uint64_t *a = smem, *b = smem + padded(cap);
     uint64_t *gk = entries + s;
     if (n <= cap) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = gk[i];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) a[pidx<true>(i)] = gk[i];
         __syncthreads();
-        const uint64_t *r = block_merge_sort(a, b, n);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) gk[i] = r[i];
+        const uint64_t *r = block_merge_sort<true>(a, b, n);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) gk[i] = r[pidx<true>(i)];
         return;
     }
     // large bucket: sort cap-sized chunks in shared memory ...
     for (int c0 = 0; c0 < n; c0 += cap) {
         const int m = n - c0 < cap ? n - c0 : cap;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) a[i] = gk[c0 + i];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) a[pidx<true>(i)] = gk[c0 + i];
         __syncthreads();
-        const uint64_t *r = block_merge_sort(a, b, m);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) gk[c0 + i] = r[i];
+        const uint64_t *r = block_merge_sort<true>(a, b, m);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) gk[c0 + i] = r[pidx<true>(i)];
         __syncthreads();
     }
     // ... then merge the sorted chunks through global memory
@@ -118,7 +146,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *__r
             const int rest = n - base - la;
             const int lb = rest < w ? rest : w;
             const int seg_end = kend < base + la + lb ? kend : base + la + lb;
-            merge_segment(src + base, la, src + base + la, lb, k - base, seg_end - base, dst + base);
+            merge_segment<false>(src, base, la, base + la, lb, k - base, seg_end - base, dst, base);
             k = seg_end;
         }
         __syncthreads();
@@ -139,7 +167,7 @@ cudaError_t launch_sort_tiles(const uint32_t *off, uint64_t *entries, uint64_t *
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)cap * 2 * sizeof(uint64_t);
+    const size_t smem = (size_t)padded(cap) * 2 * sizeof(uint64_t);
     if (dev < 0 || dev >= 64 || configured[dev] < (int)smem) {
         e = cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
