@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--json-out", default="")
+    p.add_argument("--workload", choices=["room8", "batching", "mapping"], default="room8",
+                   help="room8: the headline line (default); batching: 32 uneven views, batched vs per-view "
+                        "launches and the autotuner; mapping: 10 x 1200x680 keyframes, 100 Adam iterations")
     return p.parse_args()
 
 
@@ -323,7 +326,7 @@ def roofline(stages, stats, scene, peaks, src):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     ng, nk = scene.n_gaussians, stats["n_keys"]
-    kernel_of = {"composite_bwd": "k_composite_bwd2", "composite_fwd": "k_composite_fwd", "sort": "k_sort_tiles",
+    kernel_of = {"composite_bwd": "k_composite_bwd", "composite_fwd": "k_composite_fwd", "sort": "k_sort_tiles",
                  "emit": "k_emit", "binning": "k_project_count", "finalize": "k_finalize"}
     if name in ("composite_fwd", "composite_bwd"):
         per = FLOPS_FWD_PAIR if name == "composite_fwd" else FLOPS_BWD_PAIR
@@ -403,10 +406,220 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- secondary workloads (1 GPU)
+
+def _emit(line, args):
+    out = json.dumps(line)
+    print(out, flush=True)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            f.write(out + "\n")
+
+
+def _time_graph(fn, steps, flush, stream):
+    """Capture fn() once as a CUDA graph and time `steps` replays (L2 flushed before each,
+    outside the events); returns ms per replay."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    for _ in range(3):
+        g.replay()
+    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        s_ev[i].record(stream)
+        g.replay()
+        e_ev[i].record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(s.elapsed_time(e) for s, e in zip(s_ev, e_ev)), g
+
+
+def run_batching(args):
+    """32 views of uneven size (8 x 320x240, 16 x 640x480, 8 x 1200x680) of 16 keyframes
+    at 640x480 (4,915,200 Gaussians). The autotuner picks tile shape, batch sizes and
+    schedules; then forward + backward splatting of all views in one CUDA graph (one launch
+    per stage) is timed against the same calls made once per view (n_views = 1, 32 times,
+    also one graph). Images must be bit-identical; gradients (summed over the per-view
+    calls outside the timing) equal up to FP32 addition order."""
+    import torch
+    from paper_2603_21055_gb300 import splat, synth
+    from paper_2603_21055_gb300 import binding as B
+    from paper_2603_21055_gb300.mapping import Mapper
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    scene = synth.config3_batching(seed=3)
+    gen_s = time.perf_counter() - t0
+    mp = Mapper(scene)                      # buffers + one L1 gradient as the image gradients
+    mp.step_eager()
+    torch.cuda.synchronize()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    kfs, views, images, gin, grads = mp.kfs, mp.views, mp.images, mp.gin, mp.grads
+
+    def batched(sp):
+        def fn():
+            sp.forward(kfs, views, images)
+            sp.backward(kfs, views, gin, grads)
+        return fn
+
+    def ensure(sp):
+        s, _, need = sp.check()
+        if s != 0:
+            sp.reserve(kfs, views, int(need * 1.2) + 4096)
+            return False
+        return True
+
+    # default work split, all views in one launch per stage
+    sp0 = splat.Splatter()
+    sp0.plan(kfs, views)
+    ms_default, _ = _time_graph(batched(sp0), args.steps, flush, stream)
+    assert ensure(sp0)
+    # autotuned
+    sp = splat.Splatter()
+    sp.plan(kfs, views)
+    t0 = time.perf_counter()
+    rows = sp.autotune(kfs, views, images, gin, grads, reps=3)
+    tune_s = time.perf_counter() - t0
+    o = sp.options
+    chosen = {"tile": "%dx%d" % (o.tile_w, o.tile_h), "fwd_batch": o.fwd_batch, "bwd_batch": o.bwd_batch,
+              "fwd_schedule": B.SCHEDULE_NAMES[o.fwd_schedule], "bwd_schedule": B.SCHEDULE_NAMES[o.bwd_schedule]}
+    ms_batched, _ = _time_graph(batched(sp), args.steps, flush, stream)
+    assert ensure(sp)
+    sp.forward(kfs, views, images)
+    sp.backward(kfs, views, gin, grads)
+    ref_img = [{k: v.clone() for k, v in im.items()} for im in images]
+    ref_grad = [{k: v.clone() for k, v in g.items()} for g in grads]
+    # per view: the same library calls with one view each, same options
+    spv = splat.Splatter(tile=(o.tile_w, o.tile_h), fwd_batch=o.fwd_batch, bwd_batch=o.bwd_batch,
+                         fwd_schedule=o.fwd_schedule, bwd_schedule=o.bwd_schedule)
+    cap = max(spv.plan(kfs, [v]) for v in views)
+    spv.reserve(kfs, views[:1], int(cap * 1.15) + 4096)
+    big = max(range(len(views)), key=lambda i: views[i].width * views[i].height)
+    need = B.sgad_workspace_size(spv.ctx, spv.kf_structs(kfs), spv.view_structs([views[big]]), spv.key_capacity)
+    spv._grow(need)
+
+    def per_view():
+        for i, v in enumerate(views):
+            spv.forward(kfs, [v], [images[i]])
+            spv.backward(kfs, [v], [gin[i]], grads)
+    ms_per_view, _ = _time_graph(per_view, args.steps, flush, stream)
+    assert spv.check()[0] == 0
+    # identity of the outputs (outside the timing)
+    acc = [{k: torch.zeros_like(t) for k, t in g.items()} for g in grads]
+    for i, v in enumerate(views):
+        spv.forward(kfs, [v], [images[i]])
+        spv.backward(kfs, [v], [gin[i]], grads)
+        for a, g in zip(acc, grads):
+            for k in a:
+                a[k] += g[k]
+    torch.cuda.synchronize()
+    images_identical = all(torch.equal(a[q], b[q]) for a, b in zip(images, ref_img) for q in a)
+    rel = 0.0
+    for a, b in zip(acc, ref_grad):
+        for k in a:
+            rel = max(rel, float((a[k] - b[k]).norm() / b[k].norm().clamp_min(1e-30)))
+    n_pix = scene.n_pixels
+    mpx = lambda ms: round(n_pix / (ms / 1e3) / 1e6, 2)
+    best_rows = sorted((r for r in rows if r["ms"] > 0), key=lambda r: (r["stage"], r["ms"]))
+    line = {
+        "metric": "fwd+bwd splat Mpix/s, 32 views of uneven size batched in one launch per stage",
+        "value": mpx(ms_batched), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 3,
+        "ms_per_step": round(ms_batched, 4), "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "room16kf_32views_uneven: 16 keyframes x 640x480 (4,915,200 Gaussians) -> "
+                               "8 x 320x240 (fx 300) + 16 x 640x480 (fx 600) + 8 x 1200x680 (fx 600)",
+                   "pixels_per_step": n_pix, "step": "sgad_forward + sgad_backward over all views, one CUDA graph",
+                   "l2": "flushed (256 MB write) before every replay, outside the timed events",
+                   "generation_s": round(gen_s, 1)},
+        "autotuned": chosen, "autotune_s": round(tune_s, 2),
+        "default_split": {"value": mpx(ms_default), "ms_per_step": round(ms_default, 4),
+                          "tile": "16x16", "fwd_batch": 512, "bwd_batch": 256, "schedule": "tiles"},
+        "per_view_launches": {"value": mpx(ms_per_view), "ms_per_step": round(ms_per_view, 4),
+                              "calls": "32 x (sgad_forward + sgad_backward) with n_views = 1, one CUDA graph, "
+                                       "autotuned split"},
+        "speedup_vs_per_view": round(ms_per_view / ms_batched, 3),
+        "images_identical": images_identical, "grad_rel_l2_diff": rel,
+        "autotune_rows": [[r["tile"][0], r["tile"][1], r["stage"], r["batch"], r["schedule"], round(r["ms"], 4)]
+                          for r in best_rows],
+    }
+    _emit(line, args)
+
+
+def run_mapping(args):
+    """Full mapping optimisation of 10 keyframes at 1200x680 (8,160,000 Gaussians) against
+    10 views at the keyframe poses: 100 Adam iterations on offset, colour, opacity and
+    scale, each one CUDA graph replay (forward, L1 loss gradient, backward, Adam). Reports
+    iterations/s, peak device memory and the PSNR before and after."""
+    import torch
+    from paper_2603_21055_gb300 import synth
+    from paper_2603_21055_gb300.mapping import Mapper
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    scene = synth.config4_mapping(seed=4)
+    gen_s = time.perf_counter() - t0
+    torch.cuda.reset_peak_memory_stats()
+    mp = Mapper(scene)
+    mp.forward()
+    psnr0 = mp.psnr()
+    iters = 100
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        mp.step_eager()
+    torch.cuda.synchronize()
+    if not mp.ensure_capacity():
+        mp.step_eager()
+        assert mp.ensure_capacity()
+    mp.capture()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(iters):
+        mp.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    assert mp.ensure_capacity(), "key capacity overflowed during the timed iterations"
+    ms = ev0.elapsed_time(ev1)
+    mp.forward()
+    psnr1 = mp.psnr()
+    peak = torch.cuda.max_memory_allocated()
+    free, total = torch.cuda.mem_get_info()
+    line = {
+        "metric": "mapping iterations/s (forward + L1 grad + backward + Adam), 10 x 1200x680 keyframes",
+        "value": round(iters / (ms / 1e3), 2), "unit": "iter/s", "n_gpus": 1, "steps": iters, "warmup": 3,
+        "ms_per_step": round(ms / iters, 4), "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "room10x1200x680: 10 keyframes x 1200x680 (8,160,000 Gaussians) -> 10 views at "
+                               "the keyframe poses, fx 600", "pixels_per_step": scene.n_pixels,
+                   "iterations": iters, "step": "one CUDA graph replay per iteration, back to back (no flush)",
+                   "generation_s": round(gen_s, 1)},
+        "wall_s_100_iterations": round(wall, 3),
+        "mpix_per_s": round(scene.n_pixels * iters / (ms / 1e3) / 1e6, 2),
+        "peak_device_bytes_torch": int(peak), "device_bytes_in_use": int(total - free),
+        "keys": mp.n_keys, "psnr_db_before": round(psnr0, 3), "psnr_db_after": round(psnr1, 3),
+        "clocks": clk,
+    }
+    _emit(line, args)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batching":
+        run_batching(args)
+    elif args.workload == "mapping":
+        run_mapping(args)
     else:
         run_ours(args)
 

@@ -110,7 +110,16 @@ typedef struct {
     float *d_scale;
 } sgad_keyframe_grads;
 
-/* Options fixed at sgad_create(). */
+/* Work split of a compositing pass (forward or backward) over the tiles of all views.
+ * Every schedule computes the same images bit for bit and the same gradients up to the
+ * order of floating-point additions. */
+#define SGAD_SCHEDULE_TILES 0       /* one launch; one thread block per tile, in view order */
+#define SGAD_SCHEDULE_PERSISTENT 1  /* one launch of as many blocks as are resident on the
+                                       GPU; each block takes tiles from a queue ordered by
+                                       list length, longest first */
+#define SGAD_SCHEDULE_PER_VIEW 2    /* one launch per view (one block per tile) */
+
+/* Options fixed at sgad_create() (sgad_autotune() may change the last five). */
 typedef struct {
     int32_t tile_w, tile_h;      /* 16x16 (default), 8x32 or 32x8 */
     float bg[3];                 /* background colour (default black) */
@@ -118,6 +127,11 @@ typedef struct {
                                     global memory; 0 = default (6144); >= 64 */
     int32_t freeze_offset;       /* 1: delta is held fixed (Table 9 "Mode3"): d_offset is
                                     written as zeros */
+    int32_t fwd_batch;           /* list entries staged per thread-block barrier in forward
+                                    compositing: 128, 192, 256, 384 or 512; 0 = default (512) */
+    int32_t bwd_batch;           /* the same for backward compositing; 0 = default (256) */
+    int32_t fwd_schedule;        /* SGAD_SCHEDULE_* of forward compositing (default TILES) */
+    int32_t bwd_schedule;        /* SGAD_SCHEDULE_* of backward compositing (default TILES) */
     int32_t reserved[4];         /* must be zero */
 } sgad_options;
 
@@ -135,9 +149,9 @@ const char *sgad_last_error(void);
 
 /* Bytes of workspace needed for a problem of this shape holding up to key_capacity
  * (tile, Gaussian) keys. Host arithmetic only. The workspace holds the per-Gaussian
- * world records and gradient accumulators (64 B per Gaussian), per-tile offsets, the
- * per-pixel state kept for the backward pass (8 B per view pixel), and two key arrays
- * (16 B per key). */
+ * world records and gradient accumulators (64 B per Gaussian), per-tile offsets,
+ * counters and heavy-first order (12 B per tile), the per-pixel state kept for the
+ * backward pass (8 B per view pixel), and two key arrays (16 B per key). */
 sgad_status sgad_workspace_size(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                                 const sgad_camera *views, int32_t n_views, int64_t key_capacity,
                                 size_t *bytes);
@@ -169,6 +183,40 @@ sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                           const sgad_camera *views, int32_t n_views,
                           const sgad_image_grads *grad_in, sgad_keyframe_grads *grads_out,
                           void *workspace, size_t ws_bytes, int64_t key_capacity, void *stream);
+
+/* Project-written autotuner for one problem shape (synchronous; not capturable).
+ * Sweeps the tile shapes {16x16, 8x32, 32x8}, the batch sizes {128, 192, 256, 384, 512}
+ * and the schedules {TILES, PERSISTENT} of both compositing passes, timing each candidate
+ * with CUDA events on `stream` (median of `reps` runs after one warm-up), and stores the
+ * fastest combination in ctx's options: per tile shape, binning + emission + sort is
+ * timed once, then each (batch, schedule) of forward compositing, then of backward
+ * compositing (including the clearing of the gradient accumulators) on the gradients
+ * grad_in; the shape with the smallest sum of the three best times wins.
+ *
+ * kfs, views, out, grad_in and grads_out are as for sgad_forward() / sgad_backward();
+ * the workspace must hold the keys of every tile shape tried (a shape whose keys do not
+ * fit is skipped and reported with ms = -1). The contents of out, grads_out and the
+ * workspace are unspecified afterwards, and the key count depends on the tile shape:
+ * size the workspace again (sgad_count_keys) before the next sgad_forward().
+ * entries (host memory, up to max_entries) receives one row per timed candidate;
+ * *n_entries the number of rows written (both may be NULL / 0). */
+#define SGAD_TUNE_PREP 0         /* binning + emission + sort; batch and schedule are 0 */
+#define SGAD_TUNE_FWD 1          /* forward compositing */
+#define SGAD_TUNE_BWD 2          /* backward compositing */
+typedef struct {
+    int32_t tile_w, tile_h, stage, batch, schedule;
+    float ms;
+} sgad_tune_entry;
+
+sgad_status sgad_autotune(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
+                          const sgad_camera *views, int32_t n_views, sgad_images *out,
+                          const sgad_image_grads *grad_in, sgad_keyframe_grads *grads_out,
+                          void *workspace, size_t ws_bytes, int32_t reps,
+                          sgad_tune_entry *entries, int32_t max_entries, int32_t *n_entries,
+                          void *stream);
+
+/* The options ctx currently uses (after sgad_autotune(), its choice). */
+sgad_status sgad_get_options(const sgad_ctx *ctx, sgad_options *opt);
 
 /* Synchronise `stream`, then read the device-side status of the workspace: the first
  * error recorded by any forward since the previous sgad_check() (SGAD_OK,

@@ -25,7 +25,7 @@ SGAD_MAX_VIEWS = 64
 EXPORTS = ["sgad_default_options", "sgad_create", "sgad_destroy", "sgad_last_error", "sgad_workspace_size",
            "sgad_count_keys", "sgad_forward", "sgad_backward", "sgad_check", "sgad_state", "sgad_read_stats",
            "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_adam_step",
-           "sgad_adam_step_multi", "sgad_forward_noalloc"]
+           "sgad_adam_step_multi", "sgad_forward_noalloc", "sgad_autotune", "sgad_get_options"]
 SGAD_NUM_STAGES = 6
 STAGE_NAMES = ["binning", "emit", "sort", "composite_fwd", "composite_bwd", "finalize"]
 
@@ -60,9 +60,29 @@ class sgad_keyframe_grads(C.Structure):
                 ("d_scale", C.c_void_p)]
 
 
+SGAD_SCHEDULE_TILES = 0
+SGAD_SCHEDULE_PERSISTENT = 1
+SGAD_SCHEDULE_PER_VIEW = 2
+SCHEDULE_NAMES = {0: "tiles", 1: "persistent", 2: "per_view"}
+BATCH_SIZES = (128, 192, 256, 384, 512)
+TILE_SHAPES = ((16, 16), (8, 32), (32, 8))
+
+
 class sgad_options(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("bg", C.c_float * 3),
-                ("sort_smem_cap", C.c_int32), ("freeze_offset", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("sort_smem_cap", C.c_int32), ("freeze_offset", C.c_int32), ("fwd_batch", C.c_int32),
+                ("bwd_batch", C.c_int32), ("fwd_schedule", C.c_int32), ("bwd_schedule", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
+
+
+SGAD_TUNE_PREP = 0
+SGAD_TUNE_FWD = 1
+SGAD_TUNE_BWD = 2
+
+
+class sgad_tune_entry(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("stage", C.c_int32), ("batch", C.c_int32),
+                ("schedule", C.c_int32), ("ms", C.c_float)]
 
 
 class sgad_state_view(C.Structure):
@@ -117,6 +137,8 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         "sgad_adam_step": (st, [I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I32, I32, P]),
         "sgad_adam_step_multi": (st, [I32, P, C.c_float, C.c_float, C.c_float, P, P]),
         "sgad_forward_noalloc": (st, [P, P, I32, P, I32, P, P]),
+        "sgad_autotune": (st, [P, P, I32, P, I32, P, P, P, P, C.c_size_t, I32, P, I32, P, P]),
+        "sgad_get_options": (st, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(l, name)
@@ -243,3 +265,20 @@ def sgad_forward_noalloc(ctx, kfs, views, out, stream: int) -> None:
     """Forward splatting into `out` with the library's static scratch (no workspace, no
     allocation); synchronises `stream`."""
     _call("sgad_forward_noalloc", ctx, kfs, len(kfs), views, len(views), out, stream)
+
+
+def sgad_get_options(ctx) -> sgad_options:
+    o = sgad_options()
+    _call("sgad_get_options", ctx, C.byref(o))
+    return o
+
+
+def sgad_autotune(ctx, kfs, views, out, grad_in, grads_out, workspace: int, ws_bytes: int, reps: int,
+                  stream: int, max_entries: int = 256):
+    """Runs the library's autotuner (synchronous); returns its timing rows as dicts."""
+    rows = (sgad_tune_entry * max_entries)()
+    n = C.c_int32()
+    _call("sgad_autotune", ctx, kfs, len(kfs), views, len(views), out, grad_in, grads_out, workspace, ws_bytes,
+          int(reps), rows, max_entries, C.byref(n), stream)
+    return [dict(tile=(r.tile_w, r.tile_h), stage=("prep", "fwd", "bwd")[r.stage], batch=r.batch,
+                 schedule=SCHEDULE_NAMES.get(r.schedule, r.schedule), ms=r.ms) for r in rows[:n.value]]

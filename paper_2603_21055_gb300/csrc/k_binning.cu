@@ -14,6 +14,8 @@
 
 namespace sgad {
 
+constexpr int kOrderClasses = 128;
+
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
     uint32_t m;
@@ -67,13 +69,26 @@ __global__ void __launch_bounds__(256) k_project_count(const __grid_constant__ S
     }
 }
 
+// Position of a tile with `len` list entries in the heavy-first order: 128 classes, four
+// per power of two of the length, longest first (lengths 0 and 1 share the last class).
+__device__ __forceinline__ int order_class(uint32_t len)
+{
+    if (len <= 1) return kOrderClasses - 1;
+    const int e = 31 - __clz(len);
+    const int sub = e >= 2 ? (int)((len >> (e - 2)) & 3u) : (int)((len << (2 - e)) & 3u);
+    return kOrderClasses - 1 - (4 * e + sub);
+}
+
 // Single-CTA exclusive scan of the per-tile counts (1024 threads, 4 tiles per thread per
-// round). Also resets the counts to serve as emission cursors.
+// round). Also resets the counts to serve as emission cursors and, when `order` is
+// given, writes the tiles in heavy-first order (by list-length class; the order within a
+// class is unspecified) for the persistent compositing schedule.
 __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t *__restrict__ cnt, uint32_t *__restrict__ off, int n_tiles,
-                                                     uint64_t key_cap, WsHeader *hdr)
+                                                     uint64_t key_cap, WsHeader *hdr, uint32_t *__restrict__ order)
 {
     __shared__ uint32_t warp_sums[32];
     __shared__ uint64_t carry_s;
+    __shared__ uint32_t cls_cnt[kOrderClasses];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
@@ -130,6 +145,36 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t *__restrict__ cnt,
             atomicMax(&hdr->sticky_needed, (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull));
         }
     }
+    if (!order) return;
+    // heavy-first order: class histogram, exclusive scan of the classes, scatter
+    for (int i = threadIdx.x; i < kOrderClasses; i += blockDim.x) cls_cnt[i] = 0u;
+    __syncthreads();     // also makes this block's writes of off[] visible to all its threads
+    for (int i = threadIdx.x; i < n_tiles; i += blockDim.x) atomicAdd(&cls_cnt[order_class(off[i + 1] - off[i])], 1u);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        constexpr int kPer = kOrderClasses / 32;
+        uint32_t c[kPer], sum = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            c[q] = cls_cnt[threadIdx.x * kPer + q];
+            sum += c[q];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            cls_cnt[threadIdx.x * kPer + q] = run;
+            run += c[q];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_tiles; i += blockDim.x)
+        order[atomicAdd(&cls_cnt[order_class(off[i + 1] - off[i])], 1u)] = (uint32_t)i;
 }
 
 __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Scene sc, const World *__restrict__ world,
@@ -188,9 +233,10 @@ void launch_project_count(const Scene &sc, World *world, uint32_t *tile_cnt, cud
     if (blocks) k_project_count<<<blocks, 256, 0, st>>>(sc, world, tile_cnt);
 }
 
-void launch_scan_tiles(uint32_t *cnt, uint32_t *off, int n_tiles, uint64_t key_cap, WsHeader *hdr, cudaStream_t st)
+void launch_scan_tiles(uint32_t *cnt, uint32_t *off, int n_tiles, uint64_t key_cap, WsHeader *hdr, uint32_t *order,
+                       cudaStream_t st)
 {
-    k_scan_tiles<<<1, 1024, 0, st>>>(cnt, off, n_tiles, key_cap, hdr);
+    k_scan_tiles<<<1, 1024, 0, st>>>(cnt, off, n_tiles, key_cap, hdr, order);
 }
 
 void launch_emit(const Scene &sc, const World *world, const uint32_t *off, uint32_t *cursor, uint64_t *entries,

@@ -1,0 +1,477 @@
+// Front-to-back compositing (forward step a7) and its reverse-order adjoint (a9, with
+// the per-Gaussian chain rule of a10 down to the world centre, scale, opacity and
+// colour), templated on the tile shape (TW x TH = 256 pixels) and on the number of list
+// entries staged per block-wide barrier (B).
+//
+// Forward: 256 threads per tile, one pixel per thread; each warp owns an 8x4 block of
+// pixels. The tile's sorted list is consumed in batches of B entries: the threads stage
+// them (gathering each Gaussian's 32-byte world record and projecting it into the view)
+// into shared memory, then every warp tests 32 staged Gaussians at a time against its
+// pixel block (one lane per Gaussian, a ballot) and walks only the ones whose
+// alpha >= 1/255 box reaches it. A warp stops when all its pixels are done; the block
+// stops when all warps are.
+//
+// Backward: 128 threads per tile, each warp an 8x8 pixel block and each lane the pixels
+// (x, y) and (x, y + 4). The same lists are walked from the tile's largest contributor
+// count down to 0. Each pixel starts from its saved final transmittance and recovers the
+// transmittance in front of entry i by division, T_i = T_{i+1} / (1 - alpha_i), which is
+// stable because alpha <= 0.99. Per (pixel, entry) it forms the gradient of the colour,
+// depth and alpha terms; the moments of the lane's two pixels are summed in registers,
+// reduced over the warp with a reduce-scatter and accumulated per staged Gaussian in
+// shared memory. At the end of the batch each staging thread turns them into d mu, d s,
+// d opacity and d colour and adds them to the per-Gaussian accumulator with two 16-byte
+// vector atomics.
+//
+// Work split (CompositeArgs): either one block per tile (blockIdx.x + tile0), or a
+// persistent grid of resident blocks that take tiles from an atomic queue in the
+// heavy-first order written by the tile scan.
+#pragma once
+
+#include "sgad_device.cuh"
+
+namespace sgad {
+
+constexpr int kFwdThreads = 256;
+constexpr int kBwdThreads = 128;
+constexpr unsigned kFull = 0xffffffffu;
+// Resident-block targets (they bound the registers per thread).
+#ifndef SGAD_FWD_MINBLOCKS
+#define SGAD_FWD_MINBLOCKS 6
+#endif
+#ifndef SGAD_BWD_MINBLOCKS
+#define SGAD_BWD_MINBLOCKS 8
+#endif
+
+// Launch arguments common to both directions.
+struct CompositeArgs {
+    const World *world;
+    const uint32_t *off;          // [n_tiles + 1] list offsets
+    const uint64_t *entries;      // sorted (depth bits << 32 | Gaussian) per tile
+    float *pix_t;                 // per-pixel final transmittance
+    uint32_t *pix_n;              // per-pixel contributor count
+    float4 *gacc;                 // per-Gaussian accumulators (backward)
+    WsHeader *hdr;
+    const uint32_t *order;        // persistent: heavy-first tile order; nullptr: one block per tile
+    uint32_t *queue;              // persistent: next position in `order` (starts at 0)
+    int32_t tile0;                // one block per tile: tile of block 0
+};
+
+// Next tile of this block, or -1 when there is none. s_tile is a shared-memory slot.
+__device__ __forceinline__ int next_tile(const Scene &sc, const CompositeArgs &a, bool &first, int *s_tile)
+{
+    if (!a.order) {
+        const bool f = first;
+        first = false;
+        return f ? a.tile0 + (int)blockIdx.x : -1;
+    }
+    __syncthreads();     // every thread has read the previous slot value
+    if (threadIdx.x == 0) {
+        const uint32_t q = atomicAdd(a.queue, 1u);
+        *s_tile = q < (uint32_t)sc.n_tiles ? (int)a.order[q] : -1;
+    }
+    __syncthreads();
+    return *s_tile;
+}
+
+__device__ __forceinline__ void stage_entry(const Scene &sc, const CompositeArgs &a, const ViewDev &v, uint64_t ent,
+                                            Staged &st)
+{
+    const uint32_t g = (uint32_t)ent;
+    if (g < sc.n_gauss) {
+        const World w = a.world[g];
+        stage(project(w.w0, v), w.w1, __uint_as_float((uint32_t)(ent >> 32)), st);
+    } else {
+        st.a = make_float4(0.f, 0.f, -1.f, -1.f);     // never reaches a pixel
+    }
+}
+
+// ------------------------------------------------------------------ forward
+
+template <int TW, int TH, int B>
+__device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a, int tile, Staged *sm,
+                                         uint32_t &n_pairs, uint32_t &n_evals)
+{
+    static_assert(TW * TH == kFwdThreads, "tile must hold 256 pixels");
+    const ViewDev &v = sc.view[find_view_of_tile(sc, tile)];
+    const int local = tile - v.tile_base;
+    const int tx = local % v.tiles_x, ty = local / v.tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * 4;
+    const int px = bx + (lane & 7), py = by + (lane >> 3);
+    const bool inside = px < v.W && py < v.H;
+    const WarpRect wr = {(float)bx, (float)by, (float)(bx + 7), (float)(by + 3)};
+    const float qx = (float)px, qy = (float)py;
+
+    float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f, aa = 0.f;
+    int last = -1;
+    bool done = !inside;
+    bool warp_done = __all_sync(kFull, done);
+    const uint32_t s = a.off[tile], e = a.off[tile + 1];
+    for (uint32_t b0 = s; b0 < e; b0 += B) {
+        if (__syncthreads_and(done)) break;
+#pragma unroll
+        for (int r = 0; r < (B + kFwdThreads - 1) / kFwdThreads; ++r) {
+            const int k = r * kFwdThreads + threadIdx.x;
+            if (k < B && b0 + k < e) stage_entry(sc, a, v, a.entries[b0 + k], sm[k]);
+        }
+        __syncthreads();
+        const int nb = (int)min((uint32_t)B, e - b0);
+        if (warp_done) continue;
+        for (int c0 = 0; c0 < nb; c0 += 32) {
+            const int j = c0 + lane;
+            const uint32_t hits = __ballot_sync(kFull, j < nb && overlaps(sm[j], wr));
+            uint32_t mask = hits;
+            while (mask) {
+                const int jj = c0 + __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (done) continue;
+                const Staged st = sm[jj];
+                float dx, dy, ep, alpha;
+                ++n_evals;
+                if (!gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) continue;
+                const float test = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+                if (test < kTStop) {
+                    done = true;
+                    continue;
+                }
+                ++n_pairs;
+                const float w = __fmul_rn(alpha, T);
+                cr = __fmaf_rn(w, st.c.x, cr);
+                cg = __fmaf_rn(w, st.c.y, cg);
+                cb = __fmaf_rn(w, st.c.z, cb);
+                dd = __fmaf_rn(w, st.c.w, dd);
+                aa = __fadd_rn(aa, w);
+                T = test;
+                last = (int)(b0 + jj - s);
+            }
+            if (__all_sync(kFull, done)) {
+                warp_done = true;
+                break;
+            }
+        }
+    }
+    if (inside) {
+        const size_t hw = (size_t)v.W * v.H, p = (size_t)py * v.W + px;
+        v.rgb[p] = cr + T * sc.bg[0];
+        v.rgb[hw + p] = cg + T * sc.bg[1];
+        v.rgb[2 * hw + p] = cb + T * sc.bg[2];
+        v.depth[p] = dd;
+        v.alpha[p] = aa;
+        a.pix_t[v.pix_base + p] = T;
+        a.pix_n[v.pix_base + p] = (uint32_t)(last + 1);
+    }
+}
+
+template <int TW, int TH, int B>
+__global__ void __launch_bounds__(kFwdThreads, SGAD_FWD_MINBLOCKS)
+    k_composite_fwd(const __grid_constant__ Scene sc, const CompositeArgs a)
+{
+    __shared__ Staged sm[B];
+    __shared__ int s_tile;
+    if (a.hdr->overflow) return;
+    uint32_t n_pairs = 0, n_evals = 0;
+    bool first = true;
+    for (;;) {
+        const int tile = next_tile(sc, a, first, &s_tile);
+        if (tile < 0) break;
+        fwd_tile<TW, TH, B>(sc, a, tile, sm, n_pairs, n_evals);
+    }
+    const uint32_t wp = __reduce_add_sync(kFull, n_pairs), we = __reduce_add_sync(kFull, n_evals);
+    if ((threadIdx.x & 31) == 0 && we) {
+        atomicAdd(&a.hdr->n_pairs, (unsigned long long)wp);
+        atomicAdd(&a.hdr->n_evals, (unsigned long long)we);
+    }
+}
+
+// ------------------------------------------------------------------ backward
+
+// Reduce-scatter of 16 per-lane values over the warp in 16 shuffles (instead of 80 for
+// 16 butterfly all-reductions): at each level a lane sends the half of its slots its
+// partner keeps and adds the partner's copy of the half it keeps. Afterwards every lane
+// returns the warp total of slot (lane >> 1).
+__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
+{
+#pragma unroll
+    for (int lvl = 0; lvl < 4; ++lvl) {
+        const int half = 8 >> lvl, mask = 16 >> lvl;
+        const bool upper = (lane & mask) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = upper ? v[i] : v[i + half];
+            const float keep = upper ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, mask);
+        }
+    }
+    return v[0] + __shfl_xor_sync(kFull, v[0], 1);
+}
+
+// Chain rule of one staged Gaussian from its ten accumulated pair moments (colour (3),
+// depth, G, G dx, G dy, G dx^2, G dx dy, G dy^2 with G = dL/dpower) down to d mu, d s,
+// d opacity and d colour, added to its accumulator.
+__device__ __forceinline__ void chain_and_accumulate(const float *A, const Staged &st, const Proj &pr, float s_,
+                                                     const ViewDev &v, float4 *gacc, uint32_t g)
+{
+    const float ca = st.b.x, cbb = st.b.y, cc = st.b.z, o = st.b.w;
+    const float G = A[4], Gx = A[5], Gy = A[6], Gxx = A[7], Gxy = A[8], Gyy = A[9];
+    const float d_o = G / o;
+    const float da = -0.5f * Gxx, db = -Gxy, dc = -0.5f * Gyy;
+    const float dpx = -(ca * Gx + cbb * Gy), dpy = -(cbb * Gx + cc * Gy);
+    // conic (a, b, c) = (w, -y, x) / det of Sigma_2D = [[x, y], [y, w]]
+    const float x = pr.cxx, y = pr.cxy, wv = pr.cyy;
+    const float det = x * wv - y * y, id2 = 1.0f / (det * det);
+    const float gx = (-wv * wv * da + y * wv * db - y * y * dc) * id2;
+    const float gy = (2.0f * y * wv * da - (det + 2.0f * y * y) * db + 2.0f * x * y * dc) * id2;
+    const float gw = (-y * y * da + y * x * db - x * x * dc) * id2;
+    // Sigma_2D = s^2 J J^T + 0.3 I
+    const float tz = pr.tz, iz = 1.0f / tz, iz2 = iz * iz;
+    const float j00 = v.fx * iz, j02 = -v.fx * pr.tx * iz2;
+    const float j11 = v.fy * iz, j12 = -v.fy * pr.ty * iz2;
+    const float s2 = s_ * s_;
+    const float ds = 2.0f * s_ * ((j00 * j00 + j02 * j02) * gx + j02 * j12 * gy + (j11 * j11 + j12 * j12) * gw);
+    const float gj00 = 2.0f * s2 * j00 * gx;
+    const float gj02 = s2 * (2.0f * j02 * gx + j12 * gy);
+    const float gj11 = 2.0f * s2 * j11 * gw;
+    const float gj12 = s2 * (j02 * gy + 2.0f * j12 * gw);
+    // p = (fx tx/tz + cx, fy ty/tz + cy); composited depth z = tz
+    const float gtx = gj02 * (-v.fx * iz2) + dpx * v.fx * iz;
+    const float gty = gj12 * (-v.fy * iz2) + dpy * v.fy * iz;
+    const float gtz = gj00 * (-v.fx * iz2) + gj02 * (2.0f * v.fx * pr.tx * iz2 * iz) + gj11 * (-v.fy * iz2) +
+                      gj12 * (2.0f * v.fy * pr.ty * iz2 * iz) + dpx * (-v.fx * pr.tx * iz2) +
+                      dpy * (-v.fy * pr.ty * iz2) + A[3];
+    // t = R mu + t_k  ->  d mu = R^T d t
+    const float4 ga = make_float4(v.R[0] * gtx + v.R[3] * gty + v.R[6] * gtz, v.R[1] * gtx + v.R[4] * gty + v.R[7] * gtz,
+                                  v.R[2] * gtx + v.R[5] * gty + v.R[8] * gtz, ds);
+    atomicAdd(&gacc[2 * (size_t)g], ga);
+    atomicAdd(&gacc[2 * (size_t)g + 1], make_float4(d_o, A[0], A[1], A[2]));
+}
+
+// Shared memory of the backward pass for a batch of B entries: the staged records, their
+// Gaussian indices and eleven-float moment rows (odd stride: the per-thread row reads of
+// the chain phase hit distinct banks).
+template <int B>
+constexpr size_t bwd_smem_bytes()
+{
+    return (size_t)B * (sizeof(Staged) + sizeof(uint32_t) + 11 * sizeof(float));
+}
+
+template <int TW, int TH, int B>
+__device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a, int tile, Staged *sm, uint32_t *sg,
+                                         float (*acc)[11], int *s_nmax)
+{
+    static_assert(TW * TH == 2 * kBwdThreads, "tile must hold 256 pixels");
+    const ViewDev &v = sc.view[find_view_of_tile(sc, tile)];
+    const int local = tile - v.tile_base;
+    const int tx = local % v.tiles_x, ty = local / v.tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * 8;
+    const int px = bx + (lane & 7);
+    const int py[2] = {by + (lane >> 3), by + (lane >> 3) + 4};
+    const WarpRect wr = {(float)bx, (float)by, (float)(bx + 7), (float)(by + 7)};
+    const float qx = (float)px;
+    const float qy[2] = {(float)py[0], (float)py[1]};
+    const uint32_t s = a.off[tile];
+    const int len = (int)(a.off[tile + 1] - s);
+    const size_t hw = (size_t)v.W * v.H;
+
+    float Tf[2], gr[2], gg[2], gb[2], gD[2], gA[2], T[2], SCr[2], SCg[2], SCb[2], SD[2], SA[2];
+    int nc[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        Tf[p] = 1.0f;
+        gr[p] = gg[p] = gb[p] = gD[p] = gA[p] = 0.f;
+        nc[p] = 0;
+        if (px < v.W && py[p] < v.H) {
+            const size_t q = (size_t)py[p] * v.W + px;
+            Tf[p] = a.pix_t[v.pix_base + q];
+            nc[p] = min((int)a.pix_n[v.pix_base + q], len);
+            if (v.g_rgb) {
+                gr[p] = v.g_rgb[q];
+                gg[p] = v.g_rgb[hw + q];
+                gb[p] = v.g_rgb[2 * hw + q];
+            }
+            if (v.g_depth) gD[p] = v.g_depth[q];
+            if (v.g_alpha) gA[p] = v.g_alpha[q];
+        }
+        T[p] = Tf[p];
+        SCr[p] = SCg[p] = SCb[p] = SD[p] = SA[p] = 0.f;
+    }
+    const int warp_nc = __reduce_max_sync(kFull, (unsigned)max(nc[0], nc[1]));
+    __syncthreads();     // the previous tile's readers of *s_nmax are done
+    if (threadIdx.x == 0) *s_nmax = 0;
+    __syncthreads();
+    if (lane == 0) atomicMax(s_nmax, warp_nc);
+    __syncthreads();
+    const int nmax = *s_nmax;
+    float bgdot[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) bgdot[p] = sc.bg[0] * gr[p] + sc.bg[1] * gg[p] + sc.bg[2] * gb[p];
+
+    for (int b1 = nmax; b1 > 0; b1 -= B) {
+        const int b0 = b1 > B ? b1 - B : 0;
+        const int nb = b1 - b0;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < (B + kBwdThreads - 1) / kBwdThreads; ++r) {
+            const int k = r * kBwdThreads + threadIdx.x;
+            if (k >= B) continue;
+            if (k < nb) {
+                const uint64_t ent = a.entries[s + b0 + k];
+                stage_entry(sc, a, v, ent, sm[k]);
+                sg[k] = (uint32_t)ent;
+            }
+#pragma unroll
+            for (int q = 0; q < 10; ++q) acc[k][q] = 0.f;
+        }
+        __syncthreads();
+        if (b0 < warp_nc) {
+            for (int c0 = ((nb - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+                const int j = c0 + lane;
+                const uint32_t hits = __ballot_sync(kFull, j < nb && b0 + j < warp_nc && overlaps(sm[j], wr));
+                uint32_t mask = hits;
+                while (mask) {
+                    const int bit = 31 - __clz(mask);
+                    mask &= ~(1u << bit);
+                    const int jj = c0 + bit;
+                    float val[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) val[q] = 0.f;
+                    bool contrib = false;
+                    const Staged st = sm[jj];
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        if (b0 + jj >= nc[p]) continue;
+                        float dx, dy, ep, alpha;
+                        if (!gauss_alpha(st, qx, qy[p], dx, dy, ep, alpha)) continue;
+                        contrib = true;
+                        const float om = __fsub_rn(1.0f, alpha);
+                        const float rom = __fdividef(1.0f, om);     // om >= 0.01: fast reciprocal
+                        const float Ti = T[p] * rom;
+                        const float w = alpha * Ti;
+                        val[0] += w * gr[p];
+                        val[1] += w * gg[p];
+                        val[2] += w * gb[p];
+                        val[3] += w * gD[p];
+                        const float dal = Ti * ((st.c.x - SCr[p]) * gr[p] + (st.c.y - SCg[p]) * gg[p] +
+                                                (st.c.z - SCb[p]) * gb[p] + (st.c.w - SD[p]) * gD[p] +
+                                                (1.0f - SA[p]) * gA[p]) -
+                                          (Tf[p] * rom) * bgdot[p];
+                        SCr[p] = alpha * st.c.x + om * SCr[p];
+                        SCg[p] = alpha * st.c.y + om * SCg[p];
+                        SCb[p] = alpha * st.c.z + om * SCb[p];
+                        SD[p] = alpha * st.c.w + om * SD[p];
+                        SA[p] = alpha + om * SA[p];
+                        if (!(st.b.w * ep > kAlphaCap)) {
+                            const float G = dal * alpha;
+                            val[4] += G;
+                            val[5] += G * dx;
+                            val[6] += G * dy;
+                            val[7] += G * dx * dx;
+                            val[8] += G * dx * dy;
+                            val[9] += G * dy * dy;
+                        }
+                        T[p] = Ti;
+                    }
+                    if (__any_sync(kFull, contrib)) {
+                        const float total = warp_reduce_scatter16(val, lane);
+                        const int slot = lane >> 1;
+                        if ((lane & 1) == 0 && slot < 10) atomicAdd(&acc[jj][slot], total);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < (B + kBwdThreads - 1) / kBwdThreads; ++r) {
+            const int k = r * kBwdThreads + threadIdx.x;
+            if (k >= nb || sg[k] >= sc.n_gauss) continue;
+            const float *A = acc[k];
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < 10; ++q) any |= A[q] != 0.f;
+            if (!any) continue;
+            const float4 w0 = a.world[sg[k]].w0;
+            chain_and_accumulate(A, sm[k], project(w0, v), w0.w, v, a.gacc, sg[k]);
+        }
+    }
+}
+
+template <int TW, int TH, int B>
+__global__ void __launch_bounds__(kBwdThreads, SGAD_BWD_MINBLOCKS)
+    k_composite_bwd(const __grid_constant__ Scene sc, const CompositeArgs a)
+{
+    extern __shared__ float4 dyn_smem[];
+    Staged *sm = reinterpret_cast<Staged *>(dyn_smem);
+    uint32_t *sg = reinterpret_cast<uint32_t *>(sm + B);
+    float(*acc)[11] = reinterpret_cast<float(*)[11]>(sg + B);
+    __shared__ int s_tile, s_nmax;
+    if (a.hdr->overflow) return;
+    bool first = true;
+    for (;;) {
+        const int tile = next_tile(sc, a, first, &s_tile);
+        if (tile < 0) break;
+        bwd_tile<TW, TH, B>(sc, a, tile, sm, sg, acc, &s_nmax);
+    }
+}
+
+// ------------------------------------------------------------------ launch
+
+// Batch sizes the kernels are built for (entries staged per block-wide barrier).
+constexpr int kBatchSizes[] = {128, 192, 256, 384, 512};
+
+// Launches one direction for tile shape TW x TH with batch B. grid_blocks > 0: that many
+// blocks (one per tile from tile0, or the persistent grid); returns the launch error.
+template <int TW, int TH, int B>
+cudaError_t launch_composite_tb(bool fwd, const Scene &sc, const CompositeArgs &a, int grid_blocks, cudaStream_t st)
+{
+    if (grid_blocks <= 0) return cudaSuccess;
+    if (fwd) {
+        k_composite_fwd<TW, TH, B><<<grid_blocks, kFwdThreads, 0, st>>>(sc, a);
+    } else {
+        constexpr size_t smem = bwd_smem_bytes<B>();
+        static int configured[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64 || !configured[dev]) {
+            e = cudaFuncSetAttribute(k_composite_bwd<TW, TH, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) configured[dev] = 1;
+        }
+        k_composite_bwd<TW, TH, B><<<grid_blocks, kBwdThreads, smem, st>>>(sc, a);
+    }
+    return cudaGetLastError();
+}
+
+// Resident blocks per SM of one direction for tile shape TW x TH with batch B.
+template <int TW, int TH, int B>
+cudaError_t occupancy_tb(bool fwd, int *blocks_per_sm)
+{
+    if (fwd)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_composite_fwd<TW, TH, B>, kFwdThreads, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_composite_bwd<TW, TH, B>, kBwdThreads,
+                                                         bwd_smem_bytes<B>());
+}
+
+// Dispatch on the batch size for one tile shape (instantiated in one translation unit per
+// shape). occupancy != nullptr: only report the resident blocks per SM.
+template <int TW, int TH>
+cudaError_t launch_composite_shape(bool fwd, int batch, const Scene &sc, const CompositeArgs &a, int grid_blocks,
+                                   int *occupancy, cudaStream_t st)
+{
+#define SGAD_BATCH_CASE(Bv)                                                                     \
+    case Bv:                                                                                    \
+        return occupancy ? occupancy_tb<TW, TH, Bv>(fwd, occupancy)                            \
+                         : launch_composite_tb<TW, TH, Bv>(fwd, sc, a, grid_blocks, st);
+    switch (batch) {
+        SGAD_BATCH_CASE(128)
+        SGAD_BATCH_CASE(192)
+        SGAD_BATCH_CASE(256)
+        SGAD_BATCH_CASE(384)
+        SGAD_BATCH_CASE(512)
+    default:
+        return cudaErrorInvalidValue;
+    }
+#undef SGAD_BATCH_CASE
+}
+
+}  // namespace sgad

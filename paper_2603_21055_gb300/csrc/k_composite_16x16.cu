@@ -1,0 +1,7 @@
+// Compositing kernels for 16x16-pixel tiles, every batch size.
+#include "k_composite.cuh"
+
+namespace sgad {
+template cudaError_t launch_composite_shape<16, 16>(bool, int, const Scene &, const CompositeArgs &, int, int *,
+                                                   cudaStream_t);
+}  // namespace sgad

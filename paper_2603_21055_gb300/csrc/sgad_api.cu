@@ -10,11 +10,12 @@
 
 namespace sgad {
 void launch_project_count(const Scene &, World *, uint32_t *, cudaStream_t);
-void launch_scan_tiles(uint32_t *, uint32_t *, int, uint64_t, WsHeader *, cudaStream_t);
+void launch_scan_tiles(uint32_t *, uint32_t *, int, uint64_t, WsHeader *, uint32_t *, cudaStream_t);
 void launch_emit(const Scene &, const World *, const uint32_t *, uint32_t *, uint64_t *, WsHeader *, cudaStream_t);
 cudaError_t launch_sort_tiles(const uint32_t *, uint64_t *, uint64_t *, int, int, const WsHeader *, cudaStream_t);
-void launch_composite(bool, const Scene &, const World *, const uint32_t *, const uint64_t *, float *, uint32_t *,
-                      float4 *, WsHeader *, cudaStream_t);
+cudaError_t launch_composite(bool, int, int, const Scene &, const World *, const uint32_t *, const uint64_t *, float *,
+                             uint32_t *, float4 *, WsHeader *, const uint32_t *, cudaStream_t);
+bool valid_batch(int);
 void launch_finalize(const Scene &, const World *, const float4 *, cudaStream_t);
 void launch_l1_batch(int, const float *const *, const float *const *, const float *const *, const float *const *,
                      float *const *, float *const *, uint32_t *, const uint32_t *, float, float, float *, cudaStream_t);
@@ -167,6 +168,7 @@ struct Ws {
     float4 *gacc() const { return reinterpret_cast<float4 *>(base + L.gacc); }
     uint32_t *tile_off() const { return reinterpret_cast<uint32_t *>(base + L.tile_off); }
     uint32_t *tile_cnt() const { return reinterpret_cast<uint32_t *>(base + L.tile_cnt); }
+    uint32_t *tile_order() const { return reinterpret_cast<uint32_t *>(base + L.tile_order); }
     float *pix_t() const { return reinterpret_cast<float *>(base + L.pix_t); }
     uint32_t *pix_n() const { return reinterpret_cast<uint32_t *>(base + L.pix_n); }
     uint64_t *keys() const { return reinterpret_cast<uint64_t *>(base + L.keys); }
@@ -200,16 +202,133 @@ sgad_status last_launch(const char *what)
     return e == cudaSuccess ? SGAD_OK : cuda_fail(e, what);
 }
 
+bool uses_order(const sgad_options &o)
+{
+    return o.fwd_schedule == SGAD_SCHEDULE_PERSISTENT || o.bwd_schedule == SGAD_SCHEDULE_PERSISTENT;
+}
+
 // Projection, binning count and scan: the part shared by sgad_count_keys and sgad_forward.
-sgad_status run_binning_count(const Scene &sc, const Ws &ws, int64_t key_cap, bool clear_sticky, cudaStream_t st)
+sgad_status run_binning_count(const sgad_options &o, const Scene &sc, const Ws &ws, int64_t key_cap,
+                              bool clear_sticky, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(ws.hdr(), 0, clear_sticky ? sizeof(WsHeader) : kHeaderPerCall, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.tile_cnt(), 0, ((size_t)sc.n_tiles + 1) * 4, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     launch_project_count(sc, ws.world(), ws.tile_cnt(), st);
-    launch_scan_tiles(ws.tile_cnt(), ws.tile_off(), sc.n_tiles, (uint64_t)key_cap, ws.hdr(), st);
+    launch_scan_tiles(ws.tile_cnt(), ws.tile_off(), sc.n_tiles, (uint64_t)key_cap, ws.hdr(),
+                      uses_order(o) ? ws.tile_order() : nullptr, st);
     return last_launch("binning");
 }
+
+// Forward steps before compositing: binning count and scan, key emission, per-tile sort.
+sgad_status run_forward_prep(sgad_ctx *ctx, const Scene &sc, const Ws &ws, int64_t key_cap, cudaStream_t st)
+{
+    mark(ctx, 0, st);
+    sgad_status s = run_binning_count(ctx->opt, sc, ws, key_cap, false, st);
+    if (s) return s;
+    mark(ctx, 1, st);
+    launch_emit(sc, ws.world(), ws.tile_off(), ws.tile_cnt(), ws.keys(), ws.hdr(), st);
+    mark(ctx, 2, st);
+    cudaError_t e = launch_sort_tiles(ws.tile_off(), ws.keys(), ws.keys_alt(), sc.n_tiles, ctx->sort_cap, ws.hdr(), st);
+    if (e != cudaSuccess) return cuda_fail(e, "sort launch");
+    mark(ctx, 3, st);
+    return last_launch("binning / emission / sort");
+}
+
+sgad_status run_composite(const sgad_ctx *ctx, bool fwd, int batch, int schedule, const Scene &sc, const Ws &ws,
+                          cudaStream_t st)
+{
+    const cudaError_t e = launch_composite(fwd, batch, schedule, sc, ws.world(), ws.tile_off(), ws.keys(), ws.pix_t(),
+                                           ws.pix_n(), fwd ? nullptr : ws.gacc(), ws.hdr(), ws.tile_order(), st);
+    (void)ctx;
+    return e == cudaSuccess ? SGAD_OK : cuda_fail(e, fwd ? "forward compositing launch" : "backward compositing launch");
+}
+
+// Output images of sgad_forward into the launch parameters.
+sgad_status bind_images(Scene &sc, const sgad_images *out, int n_views)
+{
+    if (!out) return fail(SGAD_ERR_INVALID_ARG, "out is NULL");
+    for (int i = 0; i < n_views; ++i) {
+        if (!out[i].rgb || !out[i].depth || !out[i].alpha)
+            return fail(SGAD_ERR_INVALID_ARG, "view %d: an output image is NULL", i);
+        sc.view[i].rgb = out[i].rgb;
+        sc.view[i].depth = out[i].depth;
+        sc.view[i].alpha = out[i].alpha;
+    }
+    return SGAD_OK;
+}
+
+// Image gradients in and keyframe gradients out of sgad_backward into the launch parameters.
+sgad_status bind_grads(Scene &sc, const sgad_image_grads *grad_in, sgad_keyframe_grads *grads_out, int n_kf,
+                       int n_views)
+{
+    if (!grad_in || !grads_out) return fail(SGAD_ERR_INVALID_ARG, "grad_in / grads_out is NULL");
+    for (int i = 0; i < n_views; ++i) {
+        sc.view[i].g_rgb = grad_in[i].d_rgb;
+        sc.view[i].g_depth = grad_in[i].d_depth;
+        sc.view[i].g_alpha = grad_in[i].d_alpha;
+    }
+    for (int i = 0; i < n_kf; ++i) {
+        KfDev &d = sc.kf[i];
+        d.d_offset = grads_out[i].d_offset;
+        d.d_rgb = grads_out[i].d_rgb;
+        d.d_logit = grads_out[i].d_opacity_logit;
+        d.d_scale = grads_out[i].d_scale;
+        if (d.learnable && (!d.d_offset || !d.d_rgb || !d.d_logit || !d.d_scale))
+            return fail(SGAD_ERR_INVALID_ARG, "keyframe %d is learnable but a gradient plane is NULL", i);
+    }
+    return SGAD_OK;
+}
+
+
+// Event pair for the autotuner: times `reps` runs of a launch sequence after one warm-up
+// and returns the median in milliseconds.
+struct TuneTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~TuneTimer()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    cudaError_t init()
+    {
+        cudaError_t e = cudaEventCreate(&a);
+        return e == cudaSuccess ? cudaEventCreate(&b) : e;
+    }
+    template <class F>
+    sgad_status median(int reps, cudaStream_t st, F &&run, float *ms)
+    {
+        float t[101];
+        for (int r = 0; r <= reps; ++r) {
+            cudaError_t e = cudaEventRecord(a, st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+            const sgad_status s = run();
+            if (s) return s;
+            e = cudaEventRecord(b, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            if (e == cudaSuccess && r > 0) e = cudaEventElapsedTime(&t[r - 1], a, b);
+            if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+        }
+        for (int i = 1; i < reps; ++i)      // insertion sort of at most 100 values
+            for (int j = i; j > 0 && t[j] < t[j - 1]; --j) {
+                const float x = t[j];
+                t[j] = t[j - 1];
+                t[j - 1] = x;
+            }
+        *ms = t[reps / 2];
+        return SGAD_OK;
+    }
+};
+
+struct TuneLog {
+    sgad_tune_entry *rows;
+    int max_rows, n = 0;
+    void add(int tw, int th, int stage, int batch, int sched, float ms)
+    {
+        if (rows && n < max_rows) rows[n] = sgad_tune_entry{tw, th, stage, batch, sched, ms};
+        if (rows && n < max_rows) ++n;
+    }
+};
 
 }  // namespace
 
@@ -223,6 +342,17 @@ sgad_status sgad_default_options(sgad_options *opt)
     opt->tile_h = 16;
     opt->sort_smem_cap = 0;
     opt->freeze_offset = 0;
+    opt->fwd_batch = 512;
+    opt->bwd_batch = 256;
+    opt->fwd_schedule = SGAD_SCHEDULE_TILES;
+    opt->bwd_schedule = SGAD_SCHEDULE_TILES;
+    return SGAD_OK;
+}
+
+sgad_status sgad_get_options(const sgad_ctx *ctx, sgad_options *opt)
+{
+    if (!ctx || !opt) return fail(SGAD_ERR_INVALID_ARG, "ctx / opt is NULL");
+    *opt = ctx->opt;
     return SGAD_OK;
 }
 
@@ -242,6 +372,13 @@ sgad_status sgad_create(sgad_ctx **out, const sgad_options *opt)
         if (o.reserved[i] != 0) return fail(SGAD_ERR_INVALID_ARG, "reserved options must be zero");
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(o.bg[c])) return fail(SGAD_ERR_INVALID_ARG, "background must be finite");
+    if (o.fwd_batch == 0) o.fwd_batch = 512;
+    if (o.bwd_batch == 0) o.bwd_batch = 256;
+    if (!valid_batch(o.fwd_batch) || !valid_batch(o.bwd_batch))
+        return fail(SGAD_ERR_UNSUPPORTED, "batch sizes must be 128, 192, 256, 384 or 512");
+    for (int sch : {o.fwd_schedule, o.bwd_schedule})
+        if (sch != SGAD_SCHEDULE_TILES && sch != SGAD_SCHEDULE_PERSISTENT && sch != SGAD_SCHEDULE_PER_VIEW)
+            return fail(SGAD_ERR_INVALID_ARG, "unknown schedule %d", sch);
     const int cap = o.sort_smem_cap == 0 ? 6144 : o.sort_smem_cap;
     if (cap < 64 || cap > 12288) return fail(SGAD_ERR_INVALID_ARG, "sort_smem_cap must be in [64, 12288]");
     sgad_ctx *c = new (std::nothrow) sgad_ctx;
@@ -335,7 +472,7 @@ sgad_status sgad_count_keys(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_k
     if (!s) s = get_ws(sc, n_pix, workspace, ws_bytes, 0, ws);
     if (s) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    s = run_binning_count(sc, ws, 0xfffffffell, true, st);
+    s = run_binning_count(ctx->opt, sc, ws, 0xfffffffell, true, st);
     if (s) return s;
     WsHeader h;
     cudaError_t e = cudaMemcpyAsync(&h, ws.hdr(), sizeof(h), cudaMemcpyDeviceToHost, st);
@@ -355,26 +492,12 @@ sgad_status sgad_forward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf, 
     sgad_status s = build_scene(ctx, kfs, n_kf, views, n_views, sc, n_pix);
     if (!s) s = check_kf_inputs(kfs, n_kf);
     if (!s) s = get_ws(sc, n_pix, workspace, ws_bytes, key_capacity, ws);
+    if (!s) s = bind_images(sc, out, n_views);
     if (s) return s;
-    if (!out) return fail(SGAD_ERR_INVALID_ARG, "out is NULL");
-    for (int i = 0; i < n_views; ++i) {
-        if (!out[i].rgb || !out[i].depth || !out[i].alpha)
-            return fail(SGAD_ERR_INVALID_ARG, "view %d: an output image is NULL", i);
-        sc.view[i].rgb = out[i].rgb;
-        sc.view[i].depth = out[i].depth;
-        sc.view[i].alpha = out[i].alpha;
-    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    mark(ctx, 0, st);
-    s = run_binning_count(sc, ws, key_capacity, false, st);
+    s = run_forward_prep(ctx, sc, ws, key_capacity, st);
+    if (!s) s = run_composite(ctx, true, ctx->opt.fwd_batch, ctx->opt.fwd_schedule, sc, ws, st);
     if (s) return s;
-    mark(ctx, 1, st);
-    launch_emit(sc, ws.world(), ws.tile_off(), ws.tile_cnt(), ws.keys(), ws.hdr(), st);
-    mark(ctx, 2, st);
-    cudaError_t e = launch_sort_tiles(ws.tile_off(), ws.keys(), ws.keys_alt(), sc.n_tiles, ctx->sort_cap, ws.hdr(), st);
-    if (e != cudaSuccess) return cuda_fail(e, "sort launch");
-    mark(ctx, 3, st);
-    launch_composite(true, sc, ws.world(), ws.tile_off(), ws.keys(), ws.pix_t(), ws.pix_n(), nullptr, ws.hdr(), st);
     mark(ctx, 4, st);
     ctx->fwd_recorded = ctx->profile;
     return last_launch("sgad_forward");
@@ -390,27 +513,14 @@ sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
     sgad_status s = build_scene(ctx, kfs, n_kf, views, n_views, sc, n_pix);
     if (!s) s = check_kf_inputs(kfs, n_kf);
     if (!s) s = get_ws(sc, n_pix, workspace, ws_bytes, key_capacity, ws);
+    if (!s) s = bind_grads(sc, grad_in, grads_out, n_kf, n_views);
     if (s) return s;
-    if (!grad_in || !grads_out) return fail(SGAD_ERR_INVALID_ARG, "grad_in / grads_out is NULL");
-    for (int i = 0; i < n_views; ++i) {
-        sc.view[i].g_rgb = grad_in[i].d_rgb;
-        sc.view[i].g_depth = grad_in[i].d_depth;
-        sc.view[i].g_alpha = grad_in[i].d_alpha;
-    }
-    for (int i = 0; i < n_kf; ++i) {
-        KfDev &d = sc.kf[i];
-        d.d_offset = grads_out[i].d_offset;
-        d.d_rgb = grads_out[i].d_rgb;
-        d.d_logit = grads_out[i].d_opacity_logit;
-        d.d_scale = grads_out[i].d_scale;
-        if (d.learnable && (!d.d_offset || !d.d_rgb || !d.d_logit || !d.d_scale))
-            return fail(SGAD_ERR_INVALID_ARG, "keyframe %d is learnable but a gradient plane is NULL", i);
-    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     mark(ctx, 5, st);
     cudaError_t e = cudaMemsetAsync(ws.gacc(), 0, (size_t)sc.n_gauss * 32, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    launch_composite(false, sc, ws.world(), ws.tile_off(), ws.keys(), ws.pix_t(), ws.pix_n(), ws.gacc(), ws.hdr(), st);
+    s = run_composite(ctx, false, ctx->opt.bwd_batch, ctx->opt.bwd_schedule, sc, ws, st);
+    if (s) return s;
     mark(ctx, 6, st);
     launch_finalize(sc, ws.world(), ws.gacc(), st);
     mark(ctx, 7, st);
@@ -526,6 +636,111 @@ sgad_status sgad_adam_step_multi(int32_t n_tensors, const sgad_adam_tensor *tens
     const cudaError_t e = launch_adam_multi(n_tensors, tensors, beta1, beta2, eps, step_counter,
                                             static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? SGAD_OK : cuda_fail(e, "sgad_adam_step_multi");
+}
+
+sgad_status sgad_autotune(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf, const sgad_camera *views,
+                          int32_t n_views, sgad_images *out, const sgad_image_grads *grad_in,
+                          sgad_keyframe_grads *grads_out, void *workspace, size_t ws_bytes, int32_t reps,
+                          sgad_tune_entry *entries, int32_t max_entries, int32_t *n_entries, void *stream)
+{
+    if (n_entries) *n_entries = 0;
+    if (!ctx) return fail(SGAD_ERR_INVALID_ARG, "ctx is NULL");
+    if (reps < 1 || reps > 100) return fail(SGAD_ERR_INVALID_ARG, "reps must be in [1, 100]");
+    if (max_entries < 0 || (max_entries > 0 && !entries)) return fail(SGAD_ERR_INVALID_ARG, "bad entries buffer");
+    static const int kShapes[3][2] = {{16, 16}, {8, 32}, {32, 8}};
+    static const int kBatches[5] = {128, 192, 256, 384, 512};
+    static const int kScheds[2] = {SGAD_SCHEDULE_TILES, SGAD_SCHEDULE_PERSISTENT};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TuneTimer timer;
+    cudaError_t ce = timer.init();
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
+    TuneLog log{entries, max_entries};
+    // Candidates run on a copy of the context: persistent order always computed, no
+    // profiling events.
+    sgad_ctx trial;
+    trial.opt = ctx->opt;
+    trial.sort_cap = ctx->sort_cap;
+    trial.opt.fwd_schedule = SGAD_SCHEDULE_PERSISTENT;
+    float best_total = -1.0f;
+    sgad_options best = ctx->opt;
+    for (const auto &shape : kShapes) {
+        trial.opt.tile_w = shape[0];
+        trial.opt.tile_h = shape[1];
+        Scene sc;
+        uint64_t n_pix;
+        Ws ws;
+        sgad_status s = build_scene(&trial, kfs, n_kf, views, n_views, sc, n_pix);
+        if (!s) s = check_kf_inputs(kfs, n_kf);
+        if (!s) s = bind_images(sc, out, n_views);
+        if (!s) s = bind_grads(sc, grad_in, grads_out, n_kf, n_views);
+        if (s) return s;
+        // keys of this shape (synchronises)
+        if (get_ws(sc, n_pix, workspace, ws_bytes, 0, ws) != SGAD_OK) {
+            log.add(shape[0], shape[1], SGAD_TUNE_PREP, 0, 0, -1.0f);
+            continue;
+        }
+        s = run_binning_count(trial.opt, sc, ws, 0xfffffffell, true, st);
+        if (s) return s;
+        WsHeader h;
+        ce = cudaMemcpyAsync(&h, ws.hdr(), sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "sgad_autotune");
+        const int64_t keys = (int64_t)h.needed;
+        if (get_ws(sc, n_pix, workspace, ws_bytes, keys, ws) != SGAD_OK) {
+            log.add(shape[0], shape[1], SGAD_TUNE_PREP, 0, 0, -1.0f);
+            continue;
+        }
+        float prep = 0.f;
+        s = timer.median(reps, st, [&] { return run_forward_prep(&trial, sc, ws, keys, st); }, &prep);
+        if (s) return s;
+        log.add(shape[0], shape[1], SGAD_TUNE_PREP, 0, 0, prep);
+        float best_f = -1.f, best_b = -1.f;
+        int fb = 0, fs = 0, bb = 0, bs = 0;
+        for (int sched : kScheds)
+            for (int batch : kBatches) {
+                float ms = 0.f;
+                s = timer.median(reps, st, [&] { return run_composite(&trial, true, batch, sched, sc, ws, st); }, &ms);
+                if (s) return s;
+                log.add(shape[0], shape[1], SGAD_TUNE_FWD, batch, sched, ms);
+                if (best_f < 0.f || ms < best_f) {
+                    best_f = ms;
+                    fb = batch;
+                    fs = sched;
+                }
+            }
+        for (int sched : kScheds)
+            for (int batch : kBatches) {
+                float ms = 0.f;
+                auto run = [&] {
+                    const cudaError_t e = cudaMemsetAsync(ws.gacc(), 0, (size_t)sc.n_gauss * 32, st);
+                    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+                    return run_composite(&trial, false, batch, sched, sc, ws, st);
+                };
+                s = timer.median(reps, st, run, &ms);
+                if (s) return s;
+                log.add(shape[0], shape[1], SGAD_TUNE_BWD, batch, sched, ms);
+                if (best_b < 0.f || ms < best_b) {
+                    best_b = ms;
+                    bb = batch;
+                    bs = sched;
+                }
+            }
+        const float total = prep + best_f + best_b;
+        if (best_total < 0.f || total < best_total) {
+            best_total = total;
+            best.tile_w = shape[0];
+            best.tile_h = shape[1];
+            best.fwd_batch = fb;
+            best.fwd_schedule = fs;
+            best.bwd_batch = bb;
+            best.bwd_schedule = bs;
+        }
+    }
+    if (n_entries) *n_entries = log.n;
+    if (best_total < 0.f)
+        return fail(SGAD_ERR_WORKSPACE_TOO_SMALL, "sgad_autotune: the workspace holds the keys of no tile shape");
+    ctx->opt = best;
+    return SGAD_OK;
 }
 
 }  // extern "C"

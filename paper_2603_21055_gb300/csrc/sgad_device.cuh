@@ -68,10 +68,11 @@ struct WsHeader {
     int32_t err;                 // first SGAD_ERR_* of the last forward, 0 if none
     uint32_t overflow;           // 1 if the last forward's keys did not fit
     uint32_t emit_overrun;       // binning count and emission disagreed (must stay 0)
-    uint32_t pad0;
+    uint32_t queue_fwd;          // persistent forward compositing: next tile-order position
     unsigned long long n_pairs;  // (pixel, entry) pairs composited by the last forward
     unsigned long long n_evals;  // (pixel, entry) pairs whose alpha the last forward evaluated
-    uint32_t pad1[22];
+    uint32_t queue_bwd;          // persistent backward compositing: next tile-order position
+    uint32_t pad1[21];
     int32_t sticky_err;          // first error since the last sgad_check()
     uint32_t sticky_needed;      // largest key count needed since the last sgad_check()
     uint32_t sticky_overrun;
@@ -319,7 +320,7 @@ __device__ __forceinline__ bool overlaps(const Staged &s, const WarpRect &r)
 // Workspace layout (byte offsets, 256-aligned sections). Shared by the host API and the
 // kernels' launch code.
 struct Layout {
-    size_t header, world, gacc, tile_off, tile_cnt, pix_t, pix_n, keys, keys_alt, total;
+    size_t header, world, gacc, tile_off, tile_cnt, tile_order, pix_t, pix_n, keys, keys_alt, total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -333,6 +334,7 @@ inline Layout make_layout(uint64_t n_gauss, uint64_t n_tiles, uint64_t n_pix, ui
     L.gacc = o; o = align256(o + n_gauss * 32);
     L.tile_off = o; o = align256(o + (n_tiles + 1) * 4);
     L.tile_cnt = o; o = align256(o + (n_tiles + 1) * 4);
+    L.tile_order = o; o = align256(o + n_tiles * 4);
     L.pix_t = o; o = align256(o + n_pix * 4);
     L.pix_n = o; o = align256(o + n_pix * 4);
     L.keys = o; o = align256(o + key_cap * 8);

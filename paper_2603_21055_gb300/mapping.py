@@ -27,11 +27,11 @@ class Mapper:
     targets and the library workspace."""
 
     def __init__(self, scene, tile=(16, 16), slack: float = 1.3, lr: Optional[dict] = None,
-                 freeze_offset: bool = False, kfs=None):
+                 freeze_offset: bool = False, kfs=None, work_split: Optional[dict] = None):
         self.scene = scene
         self.views = scene.views
         self.lr = dict(LR, **(lr or {}))
-        self.sp = splat.Splatter(tile=tile, freeze_offset=freeze_offset)
+        self.sp = splat.Splatter(tile=tile, freeze_offset=freeze_offset, **(work_split or {}))
         self.kfs = kfs if kfs is not None else splat.upload_keyframes(scene)
         self.trgb, self.tdep = splat.upload_targets(scene)
         self.images = splat.alloc_images(self.views)
@@ -97,10 +97,21 @@ class Mapper:
 
     def launches_per_step(self) -> int:
         """Library kernels per iteration: projection+count, scan, emission, sort, forward
-        compositing; valid-depth count and L1 gradient; backward compositing, finalisation;
-        multi-tensor Adam and its step counter."""
-        n = 5 + (2 if self.scene.depth_weight != 0 else 1) + 2
+        compositing (one launch per view with the per-view schedule); valid-depth count and
+        L1 gradient; backward compositing, finalisation; multi-tensor Adam and its step
+        counter."""
+        o = self.sp.options
+        per = lambda sched: len(self.views) if sched == B.SGAD_SCHEDULE_PER_VIEW else 1
+        n = 4 + per(o.fwd_schedule) + (2 if self.scene.depth_weight != 0 else 1) + per(o.bwd_schedule) + 1
         return n + (2 if self.n_adam else 0)
+
+    def autotune(self, reps: int = 5):
+        """Let the library's autotuner pick tile shape, batch sizes and schedules for this
+        window (on the current gradients of one eager iteration); drops a captured graph."""
+        self.step_eager()
+        rows = self.sp.autotune(self.kfs, self.views, self.images, self.gin, self.grads, reps=reps)
+        self.graph = None
+        return rows
 
     # ------------------------------------------------------------------ checks
     def ensure_capacity(self, slack: float = 1.3) -> bool:

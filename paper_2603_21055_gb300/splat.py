@@ -60,6 +60,15 @@ def upload_targets(scene, device="cuda"):
     return [f(r) for r in scene.target_rgb], [f(d) for d in scene.target_depth]
 
 
+def _schedule(x) -> int:
+    if isinstance(x, str):
+        names = {v: k for k, v in B.SCHEDULE_NAMES.items()}
+        if x not in names:
+            raise ValueError("schedule must be one of %s" % sorted(names))
+        return names[x]
+    return int(x)
+
+
 def alloc_images(views, device="cuda"):
     return [dict(rgb=torch.empty(3, v.height, v.width, device=device),
                  depth=torch.empty(v.height, v.width, device=device),
@@ -69,13 +78,20 @@ def alloc_images(views, device="cuda"):
 class Splatter:
     """A library context plus a workspace sized for one problem shape."""
 
-    def __init__(self, tile=(16, 16), bg=(0.0, 0.0, 0.0), sort_smem_cap: int = 0, freeze_offset: bool = False):
+    def __init__(self, tile=(16, 16), bg=(0.0, 0.0, 0.0), sort_smem_cap: int = 0, freeze_offset: bool = False,
+                 fwd_batch: int = 0, bwd_batch: int = 0, fwd_schedule="tiles", bwd_schedule="tiles"):
         o = B.sgad_default_options()
         o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
         for i in range(3):
             o.bg[i] = float(bg[i])
         o.sort_smem_cap = int(sort_smem_cap)
         o.freeze_offset = int(bool(freeze_offset))
+        if fwd_batch:
+            o.fwd_batch = int(fwd_batch)
+        if bwd_batch:
+            o.bwd_batch = int(bwd_batch)
+        o.fwd_schedule = _schedule(fwd_schedule)
+        o.bwd_schedule = _schedule(bwd_schedule)
         self.options = o
         self.ctx = B.sgad_create(o)
         self.workspace: Optional[torch.Tensor] = None
@@ -145,6 +161,11 @@ class Splatter:
         self.reserve(kfs, views, cap)
         return n
 
+    def _grow(self, nbytes: int) -> None:
+        if self.workspace is None or self.workspace.numel() < nbytes:
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            self.workspace[:256].zero_()          # device status block starts cleared
+
     def reserve(self, kfs, views, key_capacity: int) -> None:
         ka, va = self.kf_structs(kfs), self.view_structs(views)
         need = B.sgad_workspace_size(self.ctx, ka, va, key_capacity)
@@ -156,27 +177,63 @@ class Splatter:
                 self.workspace[:old.numel()].copy_(old)
         self.key_capacity = key_capacity
 
-    def forward(self, kfs, views, images) -> None:
-        ka, va = self.kf_structs(kfs), self.view_structs(views)
-        out = (B.sgad_images * len(views))()
+    @staticmethod
+    def _images(images):
+        out = (B.sgad_images * len(images))()
         for i, im in enumerate(images):
             out[i] = B.sgad_images(_ptr(im["rgb"]), _ptr(im["depth"]), _ptr(im["alpha"]))
-        B.sgad_forward(self.ctx, ka, va, out, self.ws_ptr, self.ws_bytes, self.key_capacity, self.stream())
+        return out
+
+    @staticmethod
+    def _grads(grads_in, grads_out):
+        gi = (B.sgad_image_grads * len(grads_in))()
+        for i, g in enumerate(grads_in):
+            gi[i] = B.sgad_image_grads(_ptr(g.get("rgb")), _ptr(g.get("depth")), _ptr(g.get("alpha")))
+        go = (B.sgad_keyframe_grads * len(grads_out))()
+        for i, g in enumerate(grads_out):
+            if g is not None:
+                go[i] = B.sgad_keyframe_grads(_ptr(g["d_offset"]), _ptr(g["d_rgb"]), _ptr(g["d_logit"]),
+                                              _ptr(g["d_scale"]))
+        return gi, go
+
+    def forward(self, kfs, views, images) -> None:
+        ka, va = self.kf_structs(kfs), self.view_structs(views)
+        B.sgad_forward(self.ctx, ka, va, self._images(images), self.ws_ptr, self.ws_bytes, self.key_capacity,
+                       self.stream())
 
     def backward(self, kfs, views, grads_in, grads_out) -> None:
         """grads_in: per view dict of d_rgb / d_depth / d_alpha tensors (missing = 0);
         grads_out: per keyframe dict of d_offset / d_rgb / d_logit / d_scale tensors
         (None for fixed keyframes)."""
         ka, va = self.kf_structs(kfs), self.view_structs(views)
-        gi = (B.sgad_image_grads * len(views))()
-        for i, g in enumerate(grads_in):
-            gi[i] = B.sgad_image_grads(_ptr(g.get("rgb")), _ptr(g.get("depth")), _ptr(g.get("alpha")))
-        go = (B.sgad_keyframe_grads * len(kfs))()
-        for i, g in enumerate(grads_out):
-            if g is not None:
-                go[i] = B.sgad_keyframe_grads(_ptr(g["d_offset"]), _ptr(g["d_rgb"]), _ptr(g["d_logit"]),
-                                              _ptr(g["d_scale"]))
+        gi, go = self._grads(grads_in, grads_out)
         B.sgad_backward(self.ctx, ka, va, gi, go, self.ws_ptr, self.ws_bytes, self.key_capacity, self.stream())
+
+    def autotune(self, kfs, views, images, grads_in, grads_out, reps: int = 5, slack: float = 1.15):
+        """Runs the library's autotuner on these inputs (synchronous), adopts its choice of
+        tile shape, batch sizes and schedules, and re-plans the workspace for that tile
+        shape. The workspace is first grown to hold the keys of the largest tile shape.
+        Returns the timing rows."""
+        ka, va = self.kf_structs(kfs), self.view_structs(views)
+        need_bytes = 0
+        for shape in B.TILE_SHAPES:            # workspace for the keys of every shape tried
+            o = B.sgad_options.from_buffer_copy(self.options)
+            o.tile_w, o.tile_h = shape
+            c = B.sgad_create(o)
+            try:
+                base = B.sgad_workspace_size(c, ka, va, 0)
+                self._grow(base)
+                n = B.sgad_count_keys(c, ka, va, self.ws_ptr, self.ws_bytes, self.stream())
+                need_bytes = max(need_bytes, B.sgad_workspace_size(c, ka, va, n))
+            finally:
+                B.sgad_destroy(c)
+        self._grow(need_bytes)
+        gi, go = self._grads(grads_in, grads_out)
+        rows = B.sgad_autotune(self.ctx, ka, va, self._images(images), gi, go, self.ws_ptr, self.ws_bytes, reps,
+                               self.stream())
+        self.options = B.sgad_get_options(self.ctx)
+        self.plan(kfs, views, slack=slack)
+        return rows
 
     def check(self):
         """(status, n_keys, keys_needed) of the last forward; synchronises."""

@@ -366,6 +366,17 @@ def config3_batching(seed: int = 3) -> Scene:
                       name="room16kf_32views_uneven")
 
 
+def batching_small(seed: int = 6) -> Scene:
+    """A small version of the batching workload for parity tests: 2 keyframes of 160x120
+    (fx 150) into 5 views of uneven size and ragged tile edges: 2 at 72x54 (fx 67.5),
+    2 at 160x120 (fx 150) and 1 at 300x170 (fx 150, cx 150, cy 85)."""
+    small = (72, 54, 67.5, 36.0, 27.0)
+    mid = (160, 120, 150.0, 80.0, 60.0)
+    wide = (300, 170, 150.0, 150.0, 85.0)
+    return room_scene(seed, 2, mid, [small, small, mid, mid, wide], view_of_keyframe=[0, 1, 0, 1, 0],
+                      name="room2kf_5views_uneven")
+
+
 def config4_mapping(seed: int = 4) -> Scene:
     """Mapping workload: 10 keyframes at 1200x680 (8,160,000 Gaussians) and 10 views at
     the keyframe poses themselves (no perturbation)."""

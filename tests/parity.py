@@ -10,12 +10,14 @@ IMAGE_ATOL = 1e-4          # spec tolerance for rendered images
 GRAD_RTOL = 1e-3           # spec tolerance for gradients (relative)
 
 
-def gpu_run(scene, grads_in=None, tile=(16, 16), sort_smem_cap=0, freeze_offset=False, bg=(0.0, 0.0, 0.0)):
+def gpu_run(scene, grads_in=None, tile=(16, 16), sort_smem_cap=0, freeze_offset=False, bg=(0.0, 0.0, 0.0),
+            **work_split):
     """Forward (and backward when grads_in is given) through libsgad. Returns a dict of
-    numpy results plus the raw forward state."""
+    numpy results plus the raw forward state. work_split: fwd_batch, bwd_batch,
+    fwd_schedule, bwd_schedule of the Splatter."""
     import torch
     from paper_2603_21055_gb300 import splat
-    sp = splat.Splatter(tile=tile, sort_smem_cap=sort_smem_cap, freeze_offset=freeze_offset, bg=bg)
+    sp = splat.Splatter(tile=tile, sort_smem_cap=sort_smem_cap, freeze_offset=freeze_offset, bg=bg, **work_split)
     kfs = splat.upload_keyframes(scene)
     n_keys = sp.plan(kfs, scene.views)
     images = splat.alloc_images(scene.views)

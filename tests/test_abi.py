@@ -30,6 +30,8 @@ def test_library_exports_every_declared_function():
 def test_default_options_and_create():
     o = B.sgad_default_options()
     assert (o.tile_w, o.tile_h) == (16, 16) and o.freeze_offset == 0
+    assert (o.fwd_batch, o.bwd_batch) == (512, 256)
+    assert o.fwd_schedule == o.bwd_schedule == B.SGAD_SCHEDULE_TILES
     ctx = B.sgad_create(o)
     B.sgad_destroy(ctx)
     for w, h in ((8, 32), (32, 8)):
@@ -37,9 +39,44 @@ def test_default_options_and_create():
         B.sgad_destroy(B.sgad_create(o))
 
 
+def test_work_split_options_round_trip():
+    """Every batch size and schedule is accepted and read back unchanged; 0 batches take
+    the defaults."""
+    for fb in B.BATCH_SIZES:
+        for sched in (B.SGAD_SCHEDULE_TILES, B.SGAD_SCHEDULE_PERSISTENT, B.SGAD_SCHEDULE_PER_VIEW):
+            o = B.sgad_default_options()
+            o.fwd_batch, o.bwd_batch, o.fwd_schedule, o.bwd_schedule = fb, B.BATCH_SIZES[-1], sched, sched
+            ctx = B.sgad_create(o)
+            r = B.sgad_get_options(ctx)
+            assert (r.fwd_batch, r.bwd_batch, r.fwd_schedule, r.bwd_schedule) == (fb, 512, sched, sched)
+            B.sgad_destroy(ctx)
+    o = B.sgad_default_options()
+    o.fwd_batch = o.bwd_batch = 0
+    ctx = B.sgad_create(o)
+    r = B.sgad_get_options(ctx)
+    assert (r.fwd_batch, r.bwd_batch) == (512, 256)
+    B.sgad_destroy(ctx)
+
+
+def test_autotune_validates_on_the_host():
+    ctx = B.sgad_create()
+    lib = B.load()
+    n = C.c_int32(-1)
+    assert lib.sgad_autotune(ctx, None, 1, None, 1, None, None, None, None, 0, 0, None, 0, C.byref(n),
+                             None) == B.SGAD_ERR_INVALID_ARG
+    assert n.value == 0 and "reps" in B.last_error()
+    assert lib.sgad_autotune(None, None, 1, None, 1, None, None, None, None, 0, 3, None, 0, None,
+                             None) == B.SGAD_ERR_INVALID_ARG
+    B.sgad_destroy(ctx)
+
+
 @pytest.mark.parametrize("field,value,status", [
     ("tile_w", 12, B.SGAD_ERR_UNSUPPORTED),
     ("sort_smem_cap", 8, B.SGAD_ERR_INVALID_ARG),
+    ("fwd_batch", 100, B.SGAD_ERR_UNSUPPORTED),
+    ("bwd_batch", 1024, B.SGAD_ERR_UNSUPPORTED),
+    ("fwd_schedule", 3, B.SGAD_ERR_INVALID_ARG),
+    ("bwd_schedule", -1, B.SGAD_ERR_INVALID_ARG),
 ])
 def test_create_rejects_bad_options(field, value, status):
     o = B.sgad_default_options()
