@@ -25,7 +25,10 @@ SGAD_MAX_VIEWS = 64
 EXPORTS = ["sgad_default_options", "sgad_create", "sgad_destroy", "sgad_last_error", "sgad_workspace_size",
            "sgad_count_keys", "sgad_forward", "sgad_backward", "sgad_check", "sgad_state", "sgad_read_stats",
            "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_adam_step",
-           "sgad_adam_step_multi", "sgad_forward_noalloc", "sgad_autotune", "sgad_get_options"]
+           "sgad_adam_step_multi", "sgad_forward_noalloc", "sgad_autotune", "sgad_get_options",
+           # include/sgad_net.h
+           "sgad_net_layer_shape", "sgad_net_workspace_size", "sgad_net_forward", "sgad_net_loss_grad",
+           "sgad_net_backward", "sgad_net_check", "sgad_net_buffers_view"]
 SGAD_NUM_STAGES = 6
 STAGE_NAMES = ["binning", "emit", "sort", "composite_fwd", "composite_bwd", "finalize"]
 
@@ -100,6 +103,21 @@ class sgad_stats(C.Structure):
                 ("n_evals", C.c_int64)]
 
 
+SGAD_NET_LAYERS = 4
+
+
+class sgad_net_params(C.Structure):
+    _fields_ = [("w", C.c_void_p * SGAD_NET_LAYERS), ("b", C.c_void_p * SGAD_NET_LAYERS)]
+
+
+class sgad_net_grads(C.Structure):
+    _fields_ = [("dw", C.c_void_p * SGAD_NET_LAYERS), ("db", C.c_void_p * SGAD_NET_LAYERS)]
+
+
+class sgad_net_buffers(C.Structure):
+    _fields_ = [("x", C.c_void_p * 4), ("y4", C.c_void_p), ("dy4", C.c_void_p), ("dpre", C.c_void_p * 3)]
+
+
 _lib = None
 
 
@@ -139,6 +157,13 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         "sgad_forward_noalloc": (st, [P, P, I32, P, I32, P, P]),
         "sgad_autotune": (st, [P, P, I32, P, I32, P, P, P, P, C.c_size_t, I32, P, I32, P, P]),
         "sgad_get_options": (st, [P, P]),
+        "sgad_net_layer_shape": (st, [I32, P, P, P, P]),
+        "sgad_net_workspace_size": (st, [I32, I32, I32, P]),
+        "sgad_net_forward": (st, [P, I32, I32, I32, P, P, P, P, P, C.c_size_t, P]),
+        "sgad_net_loss_grad": (st, [I32, I32, I32, P, P, C.c_float, P, P, C.c_size_t, P]),
+        "sgad_net_backward": (st, [P, P, I32, I32, I32, P, C.c_size_t, P]),
+        "sgad_net_check": (st, [P, C.c_size_t, P]),
+        "sgad_net_buffers_view": (st, [I32, I32, I32, P, C.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(l, name)
@@ -282,3 +307,45 @@ def sgad_autotune(ctx, kfs, views, out, grad_in, grads_out, workspace: int, ws_b
           int(reps), rows, max_entries, C.byref(n), stream)
     return [dict(tile=(r.tile_w, r.tile_h), stage=("prep", "fwd", "bwd")[r.stage], batch=r.batch,
                  schedule=SCHEDULE_NAMES.get(r.schedule, r.schedule), ms=r.ms) for r in rows[:n.value]]
+
+
+# ------------------------------------------------------------------ proposal net
+
+def sgad_net_layer_shape(layer: int):
+    """(cin, cout, cin_padded, cout_padded) of layer 0..3."""
+    v = [C.c_int32() for _ in range(4)]
+    _call("sgad_net_layer_shape", int(layer), *[C.byref(x) for x in v])
+    return tuple(x.value for x in v)
+
+
+def sgad_net_workspace_size(n: int, h: int, w: int) -> int:
+    b = C.c_size_t()
+    _call("sgad_net_workspace_size", int(n), int(h), int(w), C.byref(b))
+    return b.value
+
+
+def sgad_net_forward(params, n, h, w, rgb, depth, delta, logit, workspace, ws_bytes, stream) -> None:
+    _call("sgad_net_forward", C.byref(params), int(n), int(h), int(w), rgb, depth, delta or None, logit or None,
+          workspace, ws_bytes, stream)
+
+
+def sgad_net_loss_grad(n, h, w, target_delta, target_logit, logit_weight, loss_accum, workspace, ws_bytes,
+                       stream) -> None:
+    _call("sgad_net_loss_grad", int(n), int(h), int(w), target_delta, target_logit, float(logit_weight),
+          loss_accum or None, workspace, ws_bytes, stream)
+
+
+def sgad_net_backward(params, grads, n, h, w, workspace, ws_bytes, stream) -> None:
+    _call("sgad_net_backward", C.byref(params), C.byref(grads), int(n), int(h), int(w), workspace, ws_bytes,
+          stream)
+
+
+def sgad_net_check(workspace, ws_bytes, stream) -> int:
+    """Device status of the net workspace (0 = ok); synchronises; does not raise."""
+    return load().sgad_net_check(workspace, ws_bytes, stream)
+
+
+def sgad_net_buffers_view(n, h, w, workspace, ws_bytes) -> sgad_net_buffers:
+    out = sgad_net_buffers()
+    _call("sgad_net_buffers_view", int(n), int(h), int(w), workspace, ws_bytes, C.byref(out))
+    return out

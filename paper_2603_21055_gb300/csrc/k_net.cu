@@ -1,0 +1,486 @@
+// Learned proposal net (workload extension; the paper initialises offsets at zero):
+// 3x3 convolutions as implicit GEMMs on the tcgen05 tensor cores, bf16 operands, f32
+// accumulation in tensor memory.
+//
+// Activations are NHWC bf16 with 16 or 32 channels (the 4-channel input and 2-channel
+// output are zero-padded). A conv tile is 128 consecutive output pixels of one image row
+// (the MMA's M), all output channels (N = 16 or 32) and K = 9 taps x C_in. The three
+// input rows the tile reads are staged once in shared memory as K-major 16-byte units
+// [row][channel chunk][pixel]; the tap (dy, dx) is then just a descriptor start offset of
+// dx units into row dy, so no im2col copy is made. Weights are staged once per block in
+// the B layout [tap][channel chunk][c_out]. One thread issues the 9 x C_in/16 MMAs, a
+// tcgen05.commit arrives on an mbarrier, and the four warps read their 32 accumulator
+// rows back with tcgen05.ld for the epilogue (bias + ReLU + bf16; or the ReLU-masked
+// input gradient; or the two f32 outputs).
+//
+// The weight gradient dW[t][i][o] = sum_p x[p + d_t][i] dy[p][o] is a GEMM with the
+// pixels as K: its A rows are (tap, input channel) pairs, 4 or 8 taps per 128-row MMA,
+// plus one row of ones whose product gives the bias gradient. A 64-pixel K block of the
+// three input rows is staged pixel-major and transposed into the K-major layout with
+// ldmatrix.trans / stmatrix (one copy per dx shift); the accumulators stay in tensor
+// memory across all K blocks of the persistent block and are added to the output with
+// one atomic per (row, column) at the end.
+#include <cuda_bf16.h>
+
+#include "sgad_net_device.cuh"
+#include "tc5.cuh"
+
+namespace sgad {
+namespace net {
+
+constexpr uint32_t kSpinLimit = 1u << 22;   // bounded mbarrier waits (each try_wait may suspend)
+constexpr int kTileM = 128;                  // output pixels per conv tile
+constexpr int kRowUnits = kTileM + 2;        // staged pixels per input row (1-pixel halo)
+constexpr int kKBlock = 64;                  // pixels per weight-gradient K block
+
+__device__ __forceinline__ void set_status(uint32_t *status, uint32_t code)
+{
+    atomicCAS(status, 0u, code);
+}
+
+// ------------------------------------------------------------------ small kernels
+
+// (N,3,H,W) colour + (N,H,W) depth (f32) -> NHWC bf16, 16 channels (R, G, B, D, 0 ...).
+__global__ void k_pack_input(const float *__restrict__ rgb, const float *__restrict__ depth, uint4 *__restrict__ x0,
+                             int n, int h, int w)
+{
+    const size_t hw = (size_t)h * w, total = (size_t)n * hw;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const size_t f = p / hw, q = p - f * hw;
+        const float *c = rgb + f * 3 * hw + q;
+        __nv_bfloat162 rg = __floats2bfloat162_rn(c[0], c[hw]);
+        __nv_bfloat162 bd = __floats2bfloat162_rn(c[2 * hw], depth[p]);
+        uint4 v0;
+        v0.x = *reinterpret_cast<uint32_t *>(&rg);
+        v0.y = *reinterpret_cast<uint32_t *>(&bd);
+        v0.z = 0u;
+        v0.w = 0u;
+        x0[2 * p] = v0;
+        x0[2 * p + 1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// f32 master weights W[9][ci_p][co_p] -> forward B units [9][ci_p/8][co_p] (unit = 8
+// consecutive input channels of one output channel) and, when bwd != nullptr, the
+// input-gradient B units [9][co_p/8][ci_p] of the flipped taps (unit = 8 consecutive
+// output channels of one input channel).
+__global__ void k_prep_weights(const float *__restrict__ w, uint4 *__restrict__ fwd, uint4 *__restrict__ bwd, int ci_p,
+                               int co_p)
+{
+    const int nf = 9 * (ci_p / 8) * co_p, nb = 9 * (co_p / 8) * ci_p;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nf) {
+        const int co = i % co_p, kc = (i / co_p) % (ci_p / 8), t = i / (co_p * (ci_p / 8));
+        uint32_t u[4];
+        for (int j = 0; j < 4; ++j) {
+            __nv_bfloat162 v = __floats2bfloat162_rn(w[((size_t)t * ci_p + 8 * kc + 2 * j) * co_p + co],
+                                                     w[((size_t)t * ci_p + 8 * kc + 2 * j + 1) * co_p + co]);
+            u[j] = *reinterpret_cast<uint32_t *>(&v);
+        }
+        fwd[i] = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+    if (bwd && i < nb) {
+        const int ci = i % ci_p, kc = (i / ci_p) % (co_p / 8), t = i / (ci_p * (co_p / 8));
+        const int tf = 8 - t;     // (ky, kx) -> (2 - ky, 2 - kx)
+        uint32_t u[4];
+        for (int j = 0; j < 4; ++j) {
+            __nv_bfloat162 v = __floats2bfloat162_rn(w[((size_t)tf * ci_p + ci) * co_p + 8 * kc + 2 * j],
+                                                     w[((size_t)tf * ci_p + ci) * co_p + 8 * kc + 2 * j + 1]);
+            u[j] = *reinterpret_cast<uint32_t *>(&v);
+        }
+        bwd[i] = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+}
+
+// Training loss mean_p (y0 - delta_t / 0.01)^2 + lw (y1 - logit_t)^2 and its gradient,
+// written as the 16-channel bf16 output gradient (channels 0, 1; the rest zero).
+__global__ void k_loss(const float2 *__restrict__ y4, const float *__restrict__ td, const float *__restrict__ tl,
+                       float lw, uint4 *__restrict__ dy4, float *loss, size_t total)
+{
+    const float inv = 1.0f / (float)total;
+    float acc = 0.f;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const float2 y = y4[p];
+        const float e0 = y.x - td[p] * 100.0f, e1 = y.y - tl[p];
+        acc += e0 * e0 + lw * e1 * e1;
+        __nv_bfloat162 g = __floats2bfloat162_rn(2.0f * e0 * inv, 2.0f * lw * e1 * inv);
+        uint4 v = make_uint4(*reinterpret_cast<uint32_t *>(&g), 0u, 0u, 0u);
+        dy4[2 * p] = v;
+        dy4[2 * p + 1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (loss && (threadIdx.x & 31) == 0) atomicAdd(loss, acc * inv);
+}
+
+// ------------------------------------------------------------------ conv (forward / input gradient)
+
+template <int CI, int CO>
+struct ConvSmem {
+    static constexpr int kA = 3 * (CI / 8) * kRowUnits;   // uint4 units
+    static constexpr int kB = 9 * (CI / 8) * CO;
+    static constexpr size_t bytes = (size_t)(kA + kB) * 16;
+};
+
+__device__ __forceinline__ bool bf16_positive(uint32_t half_bits) { return (half_bits & 0x8000u) == 0 && (half_bits & 0x7FFFu) != 0; }
+
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(128) k_conv3x3(const ConvArgs a)
+{
+    static_assert(CI % 16 == 0 && (CO == 16 || CO == 32), "channel counts");
+    extern __shared__ uint4 smem[];
+    uint4 *sA = smem;
+    uint4 *sB = smem + ConvSmem<CI, CO>::kA;
+    __shared__ uint64_t bar;
+    __shared__ uint32_t taddr_s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int segs = (a.W + kTileM - 1) / kTileM;
+    const long long n_tiles = (long long)a.N * a.H * segs;
+
+    if (warp == 0) tc::tmem_alloc(&taddr_s, 32);
+    if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+    for (int i = threadIdx.x; i < ConvSmem<CI, CO>::kB; i += blockDim.x) sB[i] = a.wB[i];
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = taddr_s;
+    constexpr uint32_t idesc = tc::idesc_bf16(kTileM, CO);
+    const uint32_t a_base = tc::smem_u32(sA), b_base = tc::smem_u32(sB);
+    uint32_t phase = 0;
+    bool failed = false;
+
+    for (long long tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+        const int xs = (int)(tile % segs);
+        const long long ry = tile / segs;
+        const int y = (int)(ry % a.H), n = (int)(ry / a.H);
+        const int x0 = xs * kTileM;
+        // stage rows y-1, y, y+1, pixels x0-1 .. x0+128 (zero outside the image)
+        constexpr int kc_n = CI / 8;
+        for (int i = threadIdx.x; i < 3 * kRowUnits * kc_n; i += blockDim.x) {
+            const int kc = i % kc_n, px = (i / kc_n) % kRowUnits, dy = i / (kc_n * kRowUnits);
+            const int yy = y + dy - 1, xx = x0 + px - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+                v = __ldg(&a.in[(((size_t)n * a.H + yy) * a.W + xx) * kc_n + kc]);
+            sA[(dy * kc_n + kc) * kRowUnits + px] = v;
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const int dy = t / 3, dx = t % 3;
+#pragma unroll
+                for (int s = 0; s < CI / 16; ++s) {
+                    const uint32_t aa = a_base + (uint32_t)(((dy * kc_n + 2 * s) * kRowUnits + dx) * 16);
+                    const uint32_t bb = b_base + (uint32_t)(((t * kc_n + 2 * s) * CO) * 16);
+                    tc::mma_bf16(tmem, tc::sdesc(aa, kRowUnits * 16, 128), tc::sdesc(bb, CO * 16, 128), idesc,
+                                 (t | s) != 0);
+                }
+            }
+            tc::mma_commit(&bar);
+        }
+        const bool ok = tc::mbar_wait_bounded(&bar, phase, kSpinLimit);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) set_status(a.status, 1u);
+            failed = true;
+            // the MMAs may still be running: wait once more (bounded) before freeing TMEM
+            tc::mbar_wait_bounded(&bar, phase ^ 1u, kSpinLimit);
+            break;
+        }
+        tc::fence_after_sync();
+        // epilogue: warp w owns accumulator rows (pixels) 32w .. 32w + 31
+        const int m = warp * 32 + lane, x = x0 + m;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        uint32_t r[32];
+        {
+            uint32_t q[16];
+            tc::tmem_ld16(trow, q);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) r[c] = q[c];
+            if (CO == 32) {
+                tc::tmem_ld16(trow + 16, q);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) r[16 + c] = q[c];
+            }
+        }
+        tc::tmem_wait_ld();
+        if (x < a.W) {
+            const size_t p = ((size_t)n * a.H + y) * a.W + x;
+            if (MODE == kModeOut) {
+                const float y0 = __uint_as_float(r[0]) + a.bias[0], y1 = __uint_as_float(r[1]) + a.bias[1];
+                a.y4[p] = make_float2(y0, y1);
+                if (a.delta) a.delta[p] = 0.01f * y0;
+                if (a.logit) a.logit[p] = y1;
+            } else {
+                uint32_t packed[CO / 2];
+                if (MODE == kModeRelu) {
+#pragma unroll
+                    for (int c = 0; c < CO; c += 2) {
+                        const float v0 = fmaxf(__uint_as_float(r[c]) + a.bias[c], 0.0f);
+                        const float v1 = fmaxf(__uint_as_float(r[c + 1]) + a.bias[c + 1], 0.0f);
+                        __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                        packed[c / 2] = *reinterpret_cast<uint32_t *>(&h);
+                    }
+                } else {     // kModeMask: input gradient times [activation > 0]
+                    const uint4 *mk = a.mask + p * (CO / 8);
+#pragma unroll
+                    for (int u = 0; u < CO / 8; ++u) {
+                        const uint4 mm = __ldg(&mk[u]);
+                        const uint32_t mw[4] = {mm.x, mm.y, mm.z, mm.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int c = 8 * u + 2 * j;
+                            const float v0 = bf16_positive(mw[j] & 0xFFFFu) ? __uint_as_float(r[c]) : 0.0f;
+                            const float v1 = bf16_positive(mw[j] >> 16) ? __uint_as_float(r[c + 1]) : 0.0f;
+                            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                            packed[c / 2] = *reinterpret_cast<uint32_t *>(&h);
+                        }
+                    }
+                }
+                uint4 *dst = a.out + p * (CO / 8);
+#pragma unroll
+                for (int u = 0; u < CO / 8; ++u)
+                    dst[u] = make_uint4(packed[4 * u], packed[4 * u + 1], packed[4 * u + 2], packed[4 * u + 3]);
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();     // all reads of this tile's accumulator and staged rows are done
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+}
+
+// ------------------------------------------------------------------ weight gradient
+
+template <int CI, int CO>
+struct WgradSmem {
+    static constexpr int kRows = 9 * CI + 1;                       // (tap, channel) rows + the ones row
+    static constexpr int kGroups = (kRows + 127) / 128;
+    static constexpr int kRowsP = kGroups * 128;
+    static constexpr int kXStride = CI / 8 + 1;                    // padded pixel stride (uint4)
+    static constexpr int kYStride = CO / 8 + 1;
+    static constexpr int kNatX = 3 * (kKBlock + 2) * kXStride;
+    static constexpr int kNatY = kKBlock * kYStride;
+    static constexpr int kA = (kKBlock / 8) * kRowsP;
+    static constexpr int kB = (kKBlock / 8) * CO;
+    static constexpr size_t bytes = (size_t)(kNatX + kNatY + kA + kB) * 16;
+    static constexpr int kCols = kGroups * CO <= 32 ? 32 : (kGroups * CO <= 64 ? 64 : 128);
+};
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(128) k_conv3x3_wgrad(const WgradArgs a)
+{
+    using S = WgradSmem<CI, CO>;
+    extern __shared__ uint4 smem[];
+    uint4 *natx = smem;
+    uint4 *naty = natx + S::kNatX;
+    uint4 *sA = naty + S::kNatY;
+    uint4 *sB = sA + S::kA;
+    __shared__ uint64_t bar;
+    __shared__ uint32_t taddr_s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int segs = (a.W + kKBlock - 1) / kKBlock;
+    const long long n_blocks = (long long)a.N * a.H * segs;
+
+    if (warp == 0) tc::tmem_alloc(&taddr_s, S::kCols);
+    if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+    // rows past the (tap, channel) rows: zero, except the ones row (bias gradient)
+    for (int i = threadIdx.x; i < (kKBlock / 8) * (S::kRowsP - 9 * CI); i += blockDim.x) {
+        const int kc = i / (S::kRowsP - 9 * CI), r = 9 * CI + i % (S::kRowsP - 9 * CI);
+        const uint32_t one2 = 0x3F803F80u;     // two bf16 ones
+        sA[kc * S::kRowsP + r] = r == 9 * CI ? make_uint4(one2, one2, one2, one2) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = taddr_s;
+    constexpr uint32_t idesc = tc::idesc_bf16(128, CO);
+    const uint32_t a_base = tc::smem_u32(sA), b_base = tc::smem_u32(sB);
+    const uint32_t natx_base = tc::smem_u32(natx), naty_base = tc::smem_u32(naty);
+    uint32_t phase = 0;
+    bool any = false, failed = false;
+    constexpr int kcx = CI / 8, kcy = CO / 8;
+
+    for (long long kb = blockIdx.x; kb < n_blocks; kb += gridDim.x) {
+        const int xs = (int)(kb % segs);
+        const long long ry = kb / segs;
+        const int y = (int)(ry % a.H), n = (int)(ry / a.H);
+        const int x0 = xs * kKBlock;
+        // natural-layout staging: x rows y-1..y+1, pixels x0-1 .. x0+64; dy row y, x0 .. x0+63
+        for (int i = threadIdx.x; i < 3 * (kKBlock + 2) * kcx; i += blockDim.x) {
+            const int kc = i % kcx, px = (i / kcx) % (kKBlock + 2), dy = i / (kcx * (kKBlock + 2));
+            const int yy = y + dy - 1, xx = x0 + px - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) v = __ldg(&a.x[(((size_t)n * a.H + yy) * a.W + xx) * kcx + kc]);
+            natx[(dy * (kKBlock + 2) + px) * S::kXStride + kc] = v;
+        }
+        for (int i = threadIdx.x; i < kKBlock * kcy; i += blockDim.x) {
+            const int kc = i % kcy, px = i / kcy, xx = x0 + px;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (xx < a.W) v = __ldg(&a.dy[(((size_t)n * a.H + y) * a.W + xx) * kcy + kc]);
+            naty[px * S::kYStride + kc] = v;
+        }
+        __syncthreads();
+        // transposed copies: A[kp][(3 dy + dx) CI + 8 kcc + r] = x[y+dy-1][x0 + 8 kp + j + dx - 1][8 kcc + r], j = 0..7
+        constexpr int kABlocks = 9 * kcx * (kKBlock / 8);
+        constexpr int kBBlocks = kcy * (kKBlock / 8);
+        for (int op = warp; op < (kABlocks + kBBlocks) / 4; op += 4) {
+            const int blk = op * 4 + (lane >> 3), r = lane & 7;
+            uint32_t src, dst;
+            if (blk < kABlocks) {
+                const int kp = blk % (kKBlock / 8), kcc = (blk / (kKBlock / 8)) % kcx, t = blk / ((kKBlock / 8) * kcx);
+                const int dy = t / 3, dx = t % 3;
+                src = natx_base + (uint32_t)(((dy * (kKBlock + 2) + kp * 8 + dx + r) * S::kXStride + kcc) * 16);
+                dst = a_base + (uint32_t)((kp * S::kRowsP + t * CI + 8 * kcc + r) * 16);
+            } else {
+                const int b = blk - kABlocks, kp = b % (kKBlock / 8), kcc = b / (kKBlock / 8);
+                src = naty_base + (uint32_t)(((kp * 8 + r) * S::kYStride + kcc) * 16);
+                dst = b_base + (uint32_t)((kp * CO + 8 * kcc + r) * 16);
+            }
+            tc::transpose_copy_x4(src, dst);
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int s = 0; s < kKBlock / 16; ++s)
+#pragma unroll
+                for (int g = 0; g < S::kGroups; ++g) {
+                    const uint32_t aa = a_base + (uint32_t)((2 * s * S::kRowsP + 128 * g) * 16);
+                    const uint32_t bb = b_base + (uint32_t)(2 * s * CO * 16);
+                    tc::mma_bf16(tmem + (uint32_t)(g * CO), tc::sdesc(aa, S::kRowsP * 16, 128),
+                                 tc::sdesc(bb, CO * 16, 128), idesc, (any || s > 0) ? 1u : 0u);
+                }
+            tc::mma_commit(&bar);
+        }
+        any = true;
+        const bool ok = tc::mbar_wait_bounded(&bar, phase, kSpinLimit);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) set_status(a.status, 2u);
+            failed = true;
+            tc::mbar_wait_bounded(&bar, phase ^ 1u, kSpinLimit);
+            break;
+        }
+    }
+    tc::fence_after_sync();
+    if (any && !failed) {
+        for (int g = 0; g < S::kGroups; ++g) {
+            const int row = 128 * g + 32 * warp + lane;
+            const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(g * CO);
+#pragma unroll
+            for (int c0 = 0; c0 < CO; c0 += 16) {
+                uint32_t q[16];
+                tc::tmem_ld16(trow + c0, q);
+                tc::tmem_wait_ld();
+                if (row < 9 * CI) {
+                    float *dst = a.dw + (size_t)row * CO + c0;      // row = tap * CI + channel
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) atomicAdd(dst + c, __uint_as_float(q[c]));
+                } else if (row == 9 * CI) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) atomicAdd(a.db + c0 + c, __uint_as_float(q[c]));
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, S::kCols);
+}
+
+// ------------------------------------------------------------------ launchers
+
+namespace {
+
+int resident_grid(const void *fn, size_t smem, long long work)
+{
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 128, smem);
+    long long g = (long long)(occ > 0 ? occ : 1) * sms;
+    if (g > work) g = work;
+    return (int)(g > 0 ? g : 1);
+}
+
+template <class F>
+cudaError_t set_smem(F *fn, size_t bytes)
+{
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+template <int CI, int CO, int MODE>
+cudaError_t launch_conv(const ConvArgs &a, cudaStream_t st)
+{
+    const size_t smem = ConvSmem<CI, CO>::bytes;
+    cudaError_t e = set_smem(k_conv3x3<CI, CO, MODE>, smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)a.N * a.H * ((a.W + kTileM - 1) / kTileM);
+    if (tiles <= 0) return cudaSuccess;
+    const int grid = resident_grid((const void *)k_conv3x3<CI, CO, MODE>, smem, tiles);
+    k_conv3x3<CI, CO, MODE><<<grid, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int CI, int CO>
+cudaError_t launch_wgrad(const WgradArgs &a, cudaStream_t st)
+{
+    const size_t smem = WgradSmem<CI, CO>::bytes;
+    cudaError_t e = set_smem(k_conv3x3_wgrad<CI, CO>, smem);
+    if (e != cudaSuccess) return e;
+    const long long blocks = (long long)a.N * a.H * ((a.W + kKBlock - 1) / kKBlock);
+    if (blocks <= 0) return cudaSuccess;
+    // keep (resident blocks x TMEM columns) within the 512 columns of an SM
+    int grid = resident_grid((const void *)k_conv3x3_wgrad<CI, CO>, smem, blocks);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long cap = (long long)sms * (512 / WgradSmem<CI, CO>::kCols);
+    if (grid > cap) grid = (int)cap;
+    k_conv3x3_wgrad<CI, CO><<<grid, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_conv<16, 32, kModeRelu>(const ConvArgs &, cudaStream_t);
+template cudaError_t launch_conv<32, 32, kModeRelu>(const ConvArgs &, cudaStream_t);
+template cudaError_t launch_conv<32, 16, kModeOut>(const ConvArgs &, cudaStream_t);
+template cudaError_t launch_conv<16, 32, kModeMask>(const ConvArgs &, cudaStream_t);
+template cudaError_t launch_conv<32, 32, kModeMask>(const ConvArgs &, cudaStream_t);
+template cudaError_t launch_wgrad<16, 32>(const WgradArgs &, cudaStream_t);
+template cudaError_t launch_wgrad<32, 32>(const WgradArgs &, cudaStream_t);
+template cudaError_t launch_wgrad<32, 16>(const WgradArgs &, cudaStream_t);
+
+cudaError_t launch_pack_input(const float *rgb, const float *depth, uint4 *x0, int n, int h, int w, cudaStream_t st)
+{
+    const size_t total = (size_t)n * h * w;
+    if (!total) return cudaSuccess;
+    const int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    k_pack_input<<<grid, 256, 0, st>>>(rgb, depth, x0, n, h, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_weights(const float *w, uint4 *fwd, uint4 *bwd, int ci_p, int co_p, cudaStream_t st)
+{
+    const int n = 9 * ci_p * co_p / 8;
+    k_prep_weights<<<(n + 127) / 128, 128, 0, st>>>(w, fwd, bwd, ci_p, co_p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss(const float2 *y4, const float *td, const float *tl, float lw, uint4 *dy4, float *loss,
+                        size_t total, cudaStream_t st)
+{
+    if (!total) return cudaSuccess;
+    const int grid = (int)((total + 255) / 256 < 2048 ? (total + 255) / 256 : 2048);
+    k_loss<<<grid, 256, 0, st>>>(y4, td, tl, lw, dy4, loss, total);
+    return cudaGetLastError();
+}
+
+}  // namespace net
+}  // namespace sgad

@@ -13,7 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "sgad.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(sgad_[a-z0-9_]+)\s*\(", src)))
 
@@ -124,3 +125,19 @@ def test_host_validation_without_gpu():
     assert lib.sgad_workspace_size(ctx, kfs, 1, views, 1, -5, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
     assert lib.sgad_adam_step(10, None, None, None, None, 0.1, 0.9, 0.999, 1e-15, 1, 0, None) == B.SGAD_ERR_INVALID_ARG
     B.sgad_destroy(ctx)
+
+
+def test_net_shapes_and_workspace_on_the_host():
+    assert [B.sgad_net_layer_shape(l) for l in range(4)] == [(4, 32, 16, 32), (32, 32, 32, 32), (32, 32, 32, 32),
+                                                            (32, 2, 32, 16)]
+    n1 = B.sgad_net_workspace_size(1, 48, 64)
+    n2 = B.sgad_net_workspace_size(2, 48, 64)
+    # per pixel: packed input 32 B, three activations 3 x 64 B, outputs 8 B, output gradient
+    # 32 B, three pre-activation gradients 3 x 64 B
+    assert n2 - n1 == 48 * 64 * (32 + 192 + 8 + 32 + 192)
+    lib = B.load()
+    n = C.c_size_t()
+    assert lib.sgad_net_workspace_size(0, 48, 64, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
+    assert lib.sgad_net_layer_shape(4, None, None, None, None) == B.SGAD_ERR_INVALID_ARG
+    p = B.sgad_net_params()
+    assert lib.sgad_net_forward(C.byref(p), 1, 48, 64, None, None, None, None, None, 0, None) == B.SGAD_ERR_INVALID_ARG
