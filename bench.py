@@ -54,9 +54,17 @@ def parse():
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--json-out", default="")
-    p.add_argument("--workload", choices=["room8", "batching", "mapping"], default="room8",
+    p.add_argument("--workload", choices=["room8", "batching", "mapping", "learned", "net"], default="room8",
                    help="room8: the headline line (default); batching: 32 uneven views, batched vs per-view "
-                        "launches and the autotuner; mapping: 10 x 1200x680 keyframes, 100 Adam iterations")
+                        "launches and the autotuner; mapping: 10 x 1200x680 keyframes, 100 Adam iterations; "
+                        "learned: train the proposal net on plain-mapping targets and time mapping to 30 dB "
+                        "with learned vs zero initialisation; net: forward and backward of the proposal net "
+                        "on 8 frames of 640x480")
+    p.add_argument("--train-rooms", type=int, default=50)
+    p.add_argument("--eval-rooms", type=int, default=10)
+    p.add_argument("--frames", type=int, default=40, help="frames per room (learned workload)")
+    p.add_argument("--train-steps", type=int, default=3000)
+    p.add_argument("--workers", type=int, default=0, help="ray-casting processes (0: all cores)")
     return p.parse_args()
 
 
@@ -612,6 +620,178 @@ def run_mapping(args):
     _emit(line, args)
 
 
+def thresholds(arms, learned):
+    """Per PSNR target: windows reaching it and median / mean seconds and iterations for
+    both arms (a window that never reaches it counts as the full 100 iterations' time);
+    "plain_final-0.5" is, per window, the plain arm's final PSNR minus 0.5 dB."""
+    out = {}
+    for name in ("30", "35", "38", "40", "plain_final-0.5"):
+        sp, sl, ip, il, rp, rl = [], [], [], [], 0, 0
+        for plain, lrn in arms:
+            tgt = float(plain["psnr"][-1]) - 0.5 if name.startswith("plain") else float(name)
+            for arm, secs, its in ((plain, sp, ip), (lrn, sl, il)):
+                s_, i_ = learned.seconds_to(arm["psnr"], arm["times"], tgt)
+                if s_ is not None:
+                    if arm is plain:
+                        rp += 1
+                    else:
+                        rl += 1
+                secs.append(s_ if s_ is not None else float(arm["times"][-1]))
+                its.append(i_ if i_ is not None else len(arm["psnr"]))
+        out[name] = {"plain": {"reached": rp, "median_s": float(np.median(sp)), "mean_s": float(np.mean(sp)),
+                               "median_iters": float(np.median(ip))},
+                     "learned": {"reached": rl, "median_s": float(np.median(sl)), "mean_s": float(np.mean(sl)),
+                                 "median_iters": float(np.median(il))},
+                     "speedup_mean": float(np.mean(sp) / np.mean(sl))}
+    return out
+
+
+def run_learned(args):
+    """Learned initialisation (proposal net) against the zero initialisation: the net is
+    trained on the offsets and logits the plain mapping converges to in --train-rooms
+    seeded rooms (--frames frames each, windows of 5), then both initialisations map every
+    window of --eval-rooms held-out rooms; reported: seconds (and iterations) until the
+    window's mean PSNR reaches 30 dB, net inference included, and |delta_pred -
+    delta_plain| per pixel."""
+    import torch
+    from paper_2603_21055_gb300 import learned
+    from paper_2603_21055_gb300.proposal import ProposalNet
+    torch.cuda.set_device(0)
+    workers = args.workers or max(1, (os.cpu_count() or 2) - 1)
+    log = lambda m: print("[learned] " + m, file=sys.stderr, flush=True)
+    train_seeds = list(range(1000, 1000 + args.train_rooms))
+    eval_seeds = list(range(5000, 5000 + args.eval_rooms))
+    t0 = time.perf_counter()
+    ds = learned.build_dataset(train_seeds, args.frames, workers, log=log)
+    t_data = time.perf_counter() - t0
+    net = ProposalNet(seed=0)
+    t0 = time.perf_counter()
+    curve = learned.train(net, ds, args.train_steps, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    assert net.check() == 0
+    del ds
+    torch.cuda.empty_cache()
+    rows, arms = [], []
+    derr, zerr = [], []
+    for fr in learned.generate_rooms(eval_seeds, args.frames, workers):
+        for idx in learned.windows(args.frames):
+            plain = learned.time_to_psnr(fr, idx)
+            lrn = learned.time_to_psnr(fr, idx, net)
+            rows.append((plain["seconds"], lrn["seconds"], plain["iters_to_target"], lrn["iters_to_target"],
+                         float(plain["psnr"][0]), float(lrn["psnr"][0]), float(plain["psnr"][-1]),
+                         float(lrn["psnr"][-1]), plain["capacity_ok"] and lrn["capacity_ok"]))
+            arms.append((plain, lrn))
+            for a, b in zip(lrn["predicted"], plain["offsets"]):
+                derr.append((a - b).abs().flatten().cpu().numpy())
+                zerr.append(b.abs().flatten().cpu().numpy())
+        log("eval room %d done (%d windows)" % (fr["seed"], len(rows)))
+    d = np.concatenate(derr)
+    z = np.concatenate(zerr)
+    sec_p = [r[0] for r in rows if r[0] is not None]
+    sec_l = [r[1] for r in rows if r[1] is not None]
+    both = [(r[0], r[1]) for r in rows if r[0] is not None and r[1] is not None]
+    med = lambda v: float(np.median(v)) if v else None
+    line = {
+        "metric": "mapping secs to PSNR 30 dB, learned vs zero initialisation (5-frame windows, 640x480)",
+        "value": med(sec_l), "unit": "s", "n_gpus": 1, "higher_is_better": False, "dtype": "bf16 net / f32 splat",
+        "data": "synthetic",
+        "config": {"workload": "learned init: %d training rooms x %d frames, %d held-out rooms; windows of 5 "
+                               "learnable keyframes + 5 views at 640x480, fx 600; depth noise 1 cm + 2 mm "
+                               "quantisation" % (args.train_rooms, args.frames, args.eval_rooms),
+                   "train_steps": args.train_steps, "batch_frames": 8, "mapping_iterations_max": 100},
+        "plain": {"median_s": med(sec_p), "mean_s": float(np.mean(sec_p)) if sec_p else None,
+                  "reached": len(sec_p), "windows": len(rows),
+                  "median_iters": med([r[2] for r in rows if r[2] is not None]),
+                  "psnr_first_mean": float(np.mean([r[4] for r in rows])),
+                  "psnr_last_mean": float(np.mean([r[6] for r in rows]))},
+        "learned": {"median_s": med(sec_l), "mean_s": float(np.mean(sec_l)) if sec_l else None,
+                    "reached": len(sec_l), "windows": len(rows),
+                    "median_iters": med([r[3] for r in rows if r[3] is not None]),
+                    "psnr_first_mean": float(np.mean([r[5] for r in rows])),
+                    "psnr_last_mean": float(np.mean([r[7] for r in rows]))},
+        "speedup_median_paired": med([a / b for a, b in both]) if both else None,
+        "thresholds": thresholds(arms, learned),
+        "delta_abs_err_m": {"mean": float(d.mean()), "median": float(np.median(d)), "p90": float(np.quantile(d, 0.9))},
+        "delta_abs_err_zero_init_m": {"mean": float(z.mean()), "median": float(np.median(z)),
+                                      "p90": float(np.quantile(z, 0.9))},
+        "train": {"frames": int(len(train_seeds) * (args.frames // learned.WINDOW) * learned.WINDOW),
+                  "loss_first": curve[0][1], "loss_last": curve[-1][1], "seconds": round(t_train, 2)},
+        "data_seconds": round(t_data, 1), "capacity_ok": all(r[8] for r in rows),
+    }
+    _emit(line, args)
+
+
+# Proposal net: multiply-adds per pixel of the four layers (4*32 + 32*32 + 32*32 + 32*2)
+# x 9 taps, two flops each; the backward pass does the same work twice (input and
+# weight gradients; no input gradient for the first layer).
+NET_FLOPS_FWD_PX = 2 * 9 * (4 * 32 + 32 * 32 + 32 * 32 + 32 * 2)
+NET_FLOPS_BWD_PX = 2 * 9 * (2 * (32 * 32 + 32 * 32 + 32 * 2) + 4 * 32)
+# Algorithmic HBM bytes per pixel, each tensor read or written once at its real width:
+# forward: colour + depth in (16), packed input (8 out, 8 in), three bf16 activations
+# (64 out, 64 in each), outputs (8 raw + 8 planes); backward: output gradient (4 out,
+# 4 in, 4 in), per layer the pre-activation gradient out and in twice and the activation
+# read twice (input gradient mask and weight gradient).
+NET_BYTES_FWD_PX = 16 + 8 + 8 + 3 * (64 + 64) + 16
+NET_BYTES_BWD_PX = 12 + 3 * (64 + 2 * 64) + 3 * 2 * 64 + 2 * 8
+
+
+def run_net(args):
+    """Forward and backward of the proposal net on 8 frames of 640x480 (CUDA events,
+    median of --steps after --warmup), against the HBM and bf16 tensor roofline."""
+    import torch
+    from paper_2603_21055_gb300.proposal import ProposalNet
+    torch.cuda.set_device(0)
+    n, h, w = 8, 480, 640
+    g = torch.Generator(device="cpu").manual_seed(0)
+    rgb = torch.rand(n, 3, h, w, generator=g).cuda()
+    depth = (0.5 + 5.5 * torch.rand(n, h, w, generator=g)).cuda()
+    td = (0.01 * torch.randn(n, h, w, generator=g)).cuda()
+    tl = torch.randn(n, h, w, generator=g).cuda()
+    delta = torch.empty(n, h, w, device="cuda")
+    logit = torch.empty(n, h, w, device="cuda")
+    net = ProposalNet(seed=0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    fw, bw = [], []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        net.forward(rgb, depth, delta, logit)
+        e[1].record()
+        net.loss_grad(td, tl)
+        net.backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            fw.append(e[0].elapsed_time(e[1]))
+            bw.append(e[1].elapsed_time(e[2]))
+    assert net.check() == 0
+    peaks, src = measured_peaks()
+    px = n * h * w
+    f_ms, b_ms = statistics.median(fw), statistics.median(bw)
+    hbm = float(peaks["hbm_gbs"])
+    tc = float(peaks.get("bf16_tflops", 1900.0))
+
+    def roof(ms, flops_px, bytes_px):
+        t_hbm = px * bytes_px / (hbm * 1e9) * 1e3
+        t_tc = px * flops_px / (tc * 1e12) * 1e3
+        return {"ms": round(ms, 4), "tflops": round(px * flops_px / (ms / 1e3) / 1e12, 2),
+                "gbs_algorithmic": round(px * bytes_px / (ms / 1e3) / 1e9, 1),
+                "bound": "hbm" if t_hbm > t_tc else "tensor", "roof_ms": round(max(t_hbm, t_tc), 4),
+                "frac": round(max(t_hbm, t_tc) / ms, 4)}
+
+    line = {"metric": "proposal net fwd / bwd on 8 x 640x480 frames", "value": round(f_ms + b_ms, 4), "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "bf16 (f32 accumulate)", "data": "synthetic",
+            "config": {"workload": "proposal net 4-32-32-32-2, 3x3, 8 frames 640x480",
+                       "l2": "flushed (256 MB write) before every step"},
+            "forward": roof(f_ms, NET_FLOPS_FWD_PX, NET_BYTES_FWD_PX),
+            "backward": roof(b_ms, NET_FLOPS_BWD_PX, NET_BYTES_BWD_PX),
+            "peaks": {"hbm_gbs": hbm, "bf16_tflops": tc, "source": src}}
+    _emit(line, args)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -620,6 +800,10 @@ def main():
         run_batching(args)
     elif args.workload == "mapping":
         run_mapping(args)
+    elif args.workload == "learned":
+        run_learned(args)
+    elif args.workload == "net":
+        run_net(args)
     else:
         run_ours(args)
 

@@ -397,13 +397,28 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const WgradArgs a)
 
 namespace {
 
+// Blocks of a persistent grid: resident blocks per SM (from the kernel's registers and
+// shared memory and the SM's limits) times SMs, at most `work`.
 int resident_grid(const void *fn, size_t smem, long long work)
 {
-    int dev = 0, sms = 0, occ = 0;
+    int dev = 0, sms = 1, smem_sm = 0, regs_sm = 65536, reserved = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 128, smem);
-    long long g = (long long)(occ > 0 ? occ : 1) * sms;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaFuncAttributes fa;
+    int per_sm = 1;
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) {
+        const size_t block_smem = smem + fa.sharedSizeBytes + (size_t)reserved;
+        const int by_smem = block_smem ? (int)((size_t)smem_sm / block_smem) : 16;
+        const int regs = fa.numRegs > 0 ? fa.numRegs : 64;
+        const int by_regs = regs_sm / (((regs * 32 + 255) / 256) * 256 * 4);     // 4 warps per block
+        per_sm = by_smem < by_regs ? by_smem : by_regs;
+        if (per_sm > 16) per_sm = 16;                                           // 2048 threads per SM
+        if (per_sm < 1) per_sm = 1;
+    }
+    long long g = (long long)per_sm * sms;
     if (g > work) g = work;
     return (int)(g > 0 ? g : 1);
 }
@@ -411,7 +426,9 @@ int resident_grid(const void *fn, size_t smem, long long work)
 template <class F>
 cudaError_t set_smem(F *fn, size_t bytes)
 {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
 }
 
 }  // namespace
