@@ -176,6 +176,14 @@ def run_ours(args):
     for _ in range(args.warmup):
         mp.step_eager()
     torch.cuda.synchronize()
+    # the library's autotuner picks tile shape, batches, schedules and backward algorithm
+    tune_rows = mp.autotune(reps=3)
+    print("[autotune] " + json.dumps(sorted(([r["tile"][0], r["tile"][1], r["stage"], r["batch"], r["schedule"],
+                                              round(r["ms"], 3)] for r in tune_rows), key=lambda x: (x[2], x[5]))),
+          file=sys.stderr, flush=True)
+    for _ in range(2):
+        mp.step_eager()
+    torch.cuda.synchronize()
     if not mp.ensure_capacity():
         for _ in range(2):
             mp.step_eager()
@@ -238,14 +246,17 @@ def run_ours(args):
     e2e = run_e2e(mp, min(args.steps, 10), stream, flush)
 
     peaks, peak_src = measured_peaks()
-    roof = roofline(stages, stats, scene, peaks, peak_src)
+    from paper_2603_21055_gb300 import binding as B
+    pairs = mp.sp.options.bwd_algorithm == B.SGAD_BWD_PAIRS
+    roof = roofline(stages, stats, scene, peaks, peak_src,
+                    bwd_kernel="k_composite_bwdp" if pairs else "k_composite_bwd")
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "pixels_per_step": n_pix, "gaussians": scene.n_gaussians,
                    "keys": stats["n_keys"], "contributing_pairs": stats["n_pairs"],
-                   "evaluated_pairs": stats["n_evals"], "tile": "16x16",
+                   "evaluated_pairs": stats["n_evals"], "split": split_of(mp.sp),
                    "step": "forward + L1 loss grad + backward + Adam (all four parameter groups), "
                            "one CUDA graph replay",
                    "l2": "flushed (256 MB write) before every step, outside the timed events",
@@ -266,6 +277,16 @@ def run_ours(args):
                 f.write(out + "\n")
     if world > 1:
         dist.destroy_process_group()
+
+
+def split_of(sp):
+    """The work split a Splatter uses (after autotuning), for the JSON line."""
+    from paper_2603_21055_gb300 import binding as B
+    o = sp.options
+    bwd = ("pairs" if o.bwd_algorithm == B.SGAD_BWD_PAIRS else "warp_reduce batch %d" % o.bwd_batch)
+    return {"tile": "%dx%d" % (o.tile_w, o.tile_h), "fwd_batch": o.fwd_batch,
+            "fwd_schedule": B.SCHEDULE_NAMES[o.fwd_schedule], "bwd": bwd,
+            "bwd_schedule": B.SCHEDULE_NAMES[o.bwd_schedule], "chosen_by": "sgad_autotune"}
 
 
 def run_e2e(mp, steps, stream, flush):
@@ -324,7 +345,7 @@ def run_e2e(mp, steps, stream, flush):
             "eager_wall_ms_per_step": round(eager_ms, 3)}
 
 
-def roofline(stages, stats, scene, peaks, src):
+def roofline(stages, stats, scene, peaks, src, bwd_kernel="k_composite_bwdp"):
     """Roofline of the dominant kernel. The compositing kernels are bound by FP32
     arithmetic (peak = SMs x 128 FP32 lanes x 2 flop x max SM clock); the rest by HBM."""
     if not stages:
@@ -334,7 +355,7 @@ def roofline(stages, stats, scene, peaks, src):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     ng, nk = scene.n_gaussians, stats["n_keys"]
-    kernel_of = {"composite_bwd": "k_composite_bwd", "composite_fwd": "k_composite_fwd", "sort": "k_sort_tiles",
+    kernel_of = {"composite_bwd": bwd_kernel, "composite_fwd": "k_composite_fwd", "sort": "k_sort_tiles",
                  "emit": "k_emit", "binning": "k_project_count", "finalize": "k_finalize"}
     if name in ("composite_fwd", "composite_bwd"):
         per = FLOPS_FWD_PAIR if name == "composite_fwd" else FLOPS_BWD_PAIR

@@ -119,7 +119,20 @@ typedef struct {
                                        list length, longest first */
 #define SGAD_SCHEDULE_PER_VIEW 2    /* one launch per view (one block per tile) */
 
-/* Options fixed at sgad_create() (sgad_autotune() may change the last five). */
+/* Backward compositing algorithm (default WARP_REDUCE). Both give the same gradients up
+ * to the order of floating-point additions.
+ *   PAIRS: the forward records, per pixel and list chunk, which entries contributed
+ *     (4 bytes per pixel per 32 entries walked); the backward walks only those pairs, one
+ *     pixel per thread, and sums the per-pair moments per Gaussian with shared-memory
+ *     atomics.
+ *   WARP_REDUCE: the backward re-tests every (pixel, entry) pair whose alpha box reaches a
+ *     warp's pixel block and reduces the per-pair moments over the warp (bwd_batch
+ *     entries per barrier). */
+#define SGAD_BWD_WARP_REDUCE 0
+#define SGAD_BWD_PAIRS 1
+
+/* Options fixed at sgad_create() (sgad_autotune() may change tile shape, batches,
+ * schedules and the backward algorithm). */
 typedef struct {
     int32_t tile_w, tile_h;      /* 16x16 (default), 8x32 or 32x8 */
     float bg[3];                 /* background colour (default black) */
@@ -129,10 +142,11 @@ typedef struct {
                                     written as zeros */
     int32_t fwd_batch;           /* list entries staged per thread-block barrier in forward
                                     compositing: 128, 192, 256, 384 or 512; 0 = default (512) */
-    int32_t bwd_batch;           /* the same for backward compositing; 0 = default (256) */
+    int32_t bwd_batch;           /* the same for the warp-reduced backward; 0 = default (256) */
     int32_t fwd_schedule;        /* SGAD_SCHEDULE_* of forward compositing (default TILES) */
     int32_t bwd_schedule;        /* SGAD_SCHEDULE_* of backward compositing (default TILES) */
-    int32_t reserved[4];         /* must be zero */
+    int32_t bwd_algorithm;       /* SGAD_BWD_* (default WARP_REDUCE) */
+    int32_t reserved[3];         /* must be zero */
 } sgad_options;
 
 typedef struct sgad_ctx sgad_ctx;
@@ -151,7 +165,8 @@ const char *sgad_last_error(void);
  * (tile, Gaussian) keys. Host arithmetic only. The workspace holds the per-Gaussian
  * world records and gradient accumulators (64 B per Gaussian), per-tile offsets,
  * counters and heavy-first order (12 B per tile), the per-pixel state kept for the
- * backward pass (8 B per view pixel), and two key arrays (16 B per key). */
+ * backward pass (8 B per view pixel), two key arrays (16 B per key) and the per-pixel
+ * contribution words of the pair-parallel backward (32 B per key + 1 KB per tile). */
 sgad_status sgad_workspace_size(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                                 const sgad_camera *views, int32_t n_views, int64_t key_capacity,
                                 size_t *bytes);
@@ -186,7 +201,9 @@ sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
 
 /* Project-written autotuner for one problem shape (synchronous; not capturable).
  * Sweeps the tile shapes {16x16, 8x32, 32x8}, the batch sizes {128, 192, 256, 384, 512}
- * and the schedules {TILES, PERSISTENT} of both compositing passes, timing each candidate
+ * and the schedules {TILES, PERSISTENT} of both compositing passes (and, for the
+ * backward, the pair-parallel algorithm, reported with batch 0 and charged with the cost
+ * of the contribution words its forward writes), timing each candidate
  * with CUDA events on `stream` (median of `reps` runs after one warm-up), and stores the
  * fastest combination in ctx's options: per tile shape, binning + emission + sort is
  * timed once, then each (batch, schedule) of forward compositing, then of backward

@@ -75,7 +75,11 @@ class sgad_options(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("bg", C.c_float * 3),
                 ("sort_smem_cap", C.c_int32), ("freeze_offset", C.c_int32), ("fwd_batch", C.c_int32),
                 ("bwd_batch", C.c_int32), ("fwd_schedule", C.c_int32), ("bwd_schedule", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("bwd_algorithm", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+SGAD_BWD_WARP_REDUCE = 0
+SGAD_BWD_PAIRS = 1
 
 
 SGAD_TUNE_PREP = 0

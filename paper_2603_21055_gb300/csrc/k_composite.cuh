@@ -22,6 +22,12 @@
 // d opacity and d colour and adds them to the per-Gaussian accumulator with two 16-byte
 // vector atomics.
 //
+// A second backward, the pair-parallel variant further below (k_composite_bwdp), walks
+// only the pairs the forward marked as contributing and sums them with shared-memory
+// atomics; it is selectable (SGAD_BWD_PAIRS) but slower on the room workloads (same-
+// Gaussian atomic conflicts between neighbouring pixels), so the warp-reduced one above
+// is the default.
+//
 // Work split (CompositeArgs): either one block per tile (blockIdx.x + tile0), or a
 // persistent grid of resident blocks that take tiles from an atomic queue in the
 // heavy-first order written by the tile scan.
@@ -54,7 +60,17 @@ struct CompositeArgs {
     const uint32_t *order;        // persistent: heavy-first tile order; nullptr: one block per tile
     uint32_t *queue;              // persistent: next position in `order` (starts at 0)
     int32_t tile0;                // one block per tile: tile of block 0
+    // Contribution words (forward writes, pair-parallel backward reads; may be null):
+    // for tile t, list chunk c (entries 32c .. 32c + 31) and forward thread i (its
+    // pixel), word contrib[8 off[t] + 256 t + 256 c + i] has bit j set iff entry 32c + j
+    // contributed to that pixel. Written for every chunk the pixel's warp walked.
+    uint32_t *contrib;
 };
+
+__device__ __forceinline__ size_t contrib_base(const CompositeArgs &a, int tile, uint32_t s)
+{
+    return 8 * (size_t)s + 256 * (size_t)tile;
+}
 
 // Next tile of this block, or -1 when there is none. s_tile is a shared-memory slot.
 __device__ __forceinline__ int next_tile(const Scene &sc, const CompositeArgs &a, bool &first, int *s_tile)
@@ -120,7 +136,7 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
         for (int c0 = 0; c0 < nb; c0 += 32) {
             const int j = c0 + lane;
             const uint32_t hits = __ballot_sync(kFull, j < nb && overlaps(sm[j], wr));
-            uint32_t mask = hits;
+            uint32_t mask = hits, bits = 0;
             while (mask) {
                 const int jj = c0 + __ffs(mask) - 1;
                 mask &= mask - 1;
@@ -135,6 +151,7 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
                     continue;
                 }
                 ++n_pairs;
+                bits |= 1u << (jj - c0);
                 const float w = __fmul_rn(alpha, T);
                 cr = __fmaf_rn(w, st.c.x, cr);
                 cg = __fmaf_rn(w, st.c.y, cg);
@@ -144,6 +161,7 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
                 T = test;
                 last = (int)(b0 + jj - s);
             }
+            if (a.contrib) a.contrib[contrib_base(a, tile, s) + (size_t)((b0 - s + c0) >> 5) * 256 + threadIdx.x] = bits;
             if (__all_sync(kFull, done)) {
                 warp_done = true;
                 break;
@@ -413,6 +431,159 @@ __global__ void __launch_bounds__(kBwdThreads, SGAD_BWD_MINBLOCKS)
     }
 }
 
+// ------------------------------------------------------------------ pair-parallel backward
+//
+// 256 threads per tile with the forward's pixel map (one pixel per thread, 8x4 pixels per
+// warp). The list is staged in batches of 256 entries (one per thread, batch starts at
+// multiples of 256), walked from the tile's largest contributor count down. Each thread
+// walks only its own pixel's contributing entries, read from the forward's contribution
+// words (bit j of a chunk word), in reverse order: it recovers the transmittance by
+// division, keeps the suffix sums, forms the ten pair moments and adds them to the staged
+// entry's shared accumulator row with shared-memory atomics. No (pixel, entry) pair that
+// did not contribute is evaluated and no warp-wide reduction is needed. The staging
+// thread of each entry then applies the chain rule as in the warp-reduced backward.
+constexpr int kPairThreads = 256;
+constexpr int kPairBatch = 256;
+
+template <int TW, int TH>
+__device__ __forceinline__ void bwdp_tile(const Scene &sc, const CompositeArgs &a, int tile, Staged *sm, uint32_t *sg,
+                                          float (*acc)[11], int *s_nmax)
+{
+    static_assert(TW * TH == kPairThreads, "tile must hold 256 pixels");
+    const ViewDev &v = sc.view[find_view_of_tile(sc, tile)];
+    const int local = tile - v.tile_base;
+    const int tx = local % v.tiles_x, ty = local / v.tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = tx * TW + (warp % (TW / 8)) * 8 + (lane & 7);
+    const int py = ty * TH + (warp / (TW / 8)) * 4 + (lane >> 3);
+    const float qx = (float)px, qy = (float)py;
+    const uint32_t s = a.off[tile];
+    const int len = (int)(a.off[tile + 1] - s);
+    const size_t hw = (size_t)v.W * v.H;
+    const uint32_t *words = a.contrib + contrib_base(a, tile, s) + threadIdx.x;
+
+    float Tf = 1.0f, gr = 0.f, gg = 0.f, gb = 0.f, gD = 0.f, gA = 0.f;
+    int nc = 0;
+    if (px < v.W && py < v.H) {
+        const size_t q = (size_t)py * v.W + px;
+        Tf = a.pix_t[v.pix_base + q];
+        nc = min((int)a.pix_n[v.pix_base + q], len);
+        if (v.g_rgb) {
+            gr = v.g_rgb[q];
+            gg = v.g_rgb[hw + q];
+            gb = v.g_rgb[2 * hw + q];
+        }
+        if (v.g_depth) gD = v.g_depth[q];
+        if (v.g_alpha) gA = v.g_alpha[q];
+    }
+    __syncthreads();     // the previous tile's readers of *s_nmax are done
+    if (threadIdx.x == 0) *s_nmax = 0;
+    __syncthreads();
+    const int warp_nc = __reduce_max_sync(kFull, (unsigned)nc);
+    if (lane == 0) atomicMax(s_nmax, warp_nc);
+    __syncthreads();
+    const int nmax = *s_nmax;
+    const float bgdot = sc.bg[0] * gr + sc.bg[1] * gg + sc.bg[2] * gb;
+    float T = Tf, SCr = 0.f, SCg = 0.f, SCb = 0.f, SD = 0.f, SA = 0.f;
+
+    for (int b0 = nmax > 0 ? ((nmax - 1) / kPairBatch) * kPairBatch : -1; b0 >= 0; b0 -= kPairBatch) {
+        const int nb = min(kPairBatch, nmax - b0);
+        __syncthreads();
+        {
+            const int k = threadIdx.x;
+            if (k < nb) {
+                const uint64_t ent = a.entries[s + b0 + k];
+                stage_entry(sc, a, v, ent, sm[k]);
+                sg[k] = (uint32_t)ent;
+            }
+#pragma unroll
+            for (int q = 0; q < 10; ++q) acc[k][q] = 0.f;
+        }
+        __syncthreads();
+        // this pixel's contributing entries of the batch, last first, one per step of a
+        // warp-uniform loop (each lane advances through its own chunk words)
+        const int c_hi = min(b0 + nb, nc), c_lo = b0 >> 5;
+        bool active = c_hi > b0;
+        int c = active ? (c_hi - 1) >> 5 : c_lo;
+        uint32_t bits = active ? words[(size_t)c * 256] : 0u;
+        while (__any_sync(kFull, active)) {
+            int k = -1;
+            if (active) {
+                while (bits == 0u && c > c_lo) bits = words[(size_t)(--c) * 256];
+                if (bits) {
+                    const int bit = 31 - __clz(bits);
+                    bits &= ~(1u << bit);
+                    k = c * 32 + bit - b0;
+                } else {
+                    active = false;
+                }
+            }
+            if (k >= 0) {
+                const Staged st = sm[k];
+                float dx, dy, ep, alpha;
+                gauss_alpha(st, qx, qy, dx, dy, ep, alpha);     // contributes (forward decision)
+                const float om = __fsub_rn(1.0f, alpha);
+                const float rom = __fdividef(1.0f, om);          // om >= 0.01: fast reciprocal
+                const float Ti = T * rom;
+                const float w = alpha * Ti;
+                const float dal = Ti * ((st.c.x - SCr) * gr + (st.c.y - SCg) * gg + (st.c.z - SCb) * gb +
+                                        (st.c.w - SD) * gD + (1.0f - SA) * gA) -
+                                  (Tf * rom) * bgdot;
+                SCr = alpha * st.c.x + om * SCr;
+                SCg = alpha * st.c.y + om * SCg;
+                SCb = alpha * st.c.z + om * SCb;
+                SD = alpha * st.c.w + om * SD;
+                SA = alpha + om * SA;
+                T = Ti;
+                float *row = acc[k];
+                atomicAdd(row + 0, w * gr);
+                atomicAdd(row + 1, w * gg);
+                atomicAdd(row + 2, w * gb);
+                atomicAdd(row + 3, w * gD);
+                if (!(st.b.w * ep > kAlphaCap)) {
+                    const float G = dal * alpha;
+                    atomicAdd(row + 4, G);
+                    atomicAdd(row + 5, G * dx);
+                    atomicAdd(row + 6, G * dy);
+                    atomicAdd(row + 7, G * dx * dx);
+                    atomicAdd(row + 8, G * dx * dy);
+                    atomicAdd(row + 9, G * dy * dy);
+                }
+            }
+        }
+        __syncthreads();
+        {
+            const int k = threadIdx.x;
+            if (k < nb && sg[k] < sc.n_gauss) {
+                const float *A = acc[k];
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < 10; ++q) any |= A[q] != 0.f;
+                if (any) {
+                    const float4 w0 = a.world[sg[k]].w0;
+                    chain_and_accumulate(A, sm[k], project(w0, v), w0.w, v, a.gacc, sg[k]);
+                }
+            }
+        }
+    }
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(kPairThreads, 4) k_composite_bwdp(const __grid_constant__ Scene sc, const CompositeArgs a)
+{
+    __shared__ Staged sm[kPairBatch];
+    __shared__ uint32_t sg[kPairBatch];
+    __shared__ float acc[kPairBatch][11];
+    __shared__ int s_tile, s_nmax;
+    if (a.hdr->overflow) return;
+    bool first = true;
+    for (;;) {
+        const int tile = next_tile(sc, a, first, &s_tile);
+        if (tile < 0) break;
+        bwdp_tile<TW, TH>(sc, a, tile, sm, sg, acc, &s_nmax);
+    }
+}
+
 // ------------------------------------------------------------------ launch
 
 // Batch sizes the kernels are built for (entries staged per block-wide barrier).
@@ -452,12 +623,24 @@ cudaError_t occupancy_tb(bool fwd, int *blocks_per_sm)
                                                          bwd_smem_bytes<B>());
 }
 
+template <int TW, int TH>
+cudaError_t launch_bwdp(const Scene &sc, const CompositeArgs &a, int grid_blocks, int *occupancy, cudaStream_t st)
+{
+    if (occupancy)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_composite_bwdp<TW, TH>, kPairThreads, 0);
+    if (grid_blocks <= 0) return cudaSuccess;
+    k_composite_bwdp<TW, TH><<<grid_blocks, kPairThreads, 0, st>>>(sc, a);
+    return cudaGetLastError();
+}
+
 // Dispatch on the batch size for one tile shape (instantiated in one translation unit per
-// shape). occupancy != nullptr: only report the resident blocks per SM.
+// shape); batch 0 in the backward selects the pair-parallel kernel. occupancy != nullptr:
+// only report the resident blocks per SM.
 template <int TW, int TH>
 cudaError_t launch_composite_shape(bool fwd, int batch, const Scene &sc, const CompositeArgs &a, int grid_blocks,
                                    int *occupancy, cudaStream_t st)
 {
+    if (!fwd && batch == 0) return launch_bwdp<TW, TH>(sc, a, grid_blocks, occupancy, st);
 #define SGAD_BATCH_CASE(Bv)                                                                     \
     case Bv:                                                                                    \
         return occupancy ? occupancy_tb<TW, TH, Bv>(fwd, occupancy)                            \

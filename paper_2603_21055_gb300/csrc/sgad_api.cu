@@ -14,7 +14,7 @@ void launch_scan_tiles(uint32_t *, uint32_t *, int, uint64_t, WsHeader *, uint32
 void launch_emit(const Scene &, const World *, const uint32_t *, uint32_t *, uint64_t *, WsHeader *, cudaStream_t);
 cudaError_t launch_sort_tiles(const uint32_t *, uint64_t *, uint64_t *, int, int, const WsHeader *, cudaStream_t);
 cudaError_t launch_composite(bool, int, int, const Scene &, const World *, const uint32_t *, const uint64_t *, float *,
-                             uint32_t *, float4 *, WsHeader *, const uint32_t *, cudaStream_t);
+                             uint32_t *, float4 *, WsHeader *, const uint32_t *, uint32_t *, cudaStream_t);
 bool valid_batch(int);
 void launch_finalize(const Scene &, const World *, const float4 *, cudaStream_t);
 void launch_l1_batch(int, const float *const *, const float *const *, const float *const *, const float *const *,
@@ -173,6 +173,7 @@ struct Ws {
     uint32_t *pix_n() const { return reinterpret_cast<uint32_t *>(base + L.pix_n); }
     uint64_t *keys() const { return reinterpret_cast<uint64_t *>(base + L.keys); }
     uint64_t *keys_alt() const { return reinterpret_cast<uint64_t *>(base + L.keys_alt); }
+    uint32_t *contrib() const { return reinterpret_cast<uint32_t *>(base + L.contrib); }
 };
 
 sgad_status get_ws(const Scene &sc, uint64_t n_pix, void *workspace, size_t ws_bytes, int64_t key_cap, Ws &ws)
@@ -235,14 +236,19 @@ sgad_status run_forward_prep(sgad_ctx *ctx, const Scene &sc, const Ws &ws, int64
     return last_launch("binning / emission / sort");
 }
 
+// One compositing pass. batch 0 in the backward selects the pair-parallel kernel; the
+// forward records contribution words when the context's backward is pair-parallel.
 sgad_status run_composite(const sgad_ctx *ctx, bool fwd, int batch, int schedule, const Scene &sc, const Ws &ws,
                           cudaStream_t st)
 {
+    uint32_t *contrib = (!fwd || ctx->opt.bwd_algorithm == SGAD_BWD_PAIRS) ? ws.contrib() : nullptr;
     const cudaError_t e = launch_composite(fwd, batch, schedule, sc, ws.world(), ws.tile_off(), ws.keys(), ws.pix_t(),
-                                           ws.pix_n(), fwd ? nullptr : ws.gacc(), ws.hdr(), ws.tile_order(), st);
-    (void)ctx;
+                                           ws.pix_n(), fwd ? nullptr : ws.gacc(), ws.hdr(), ws.tile_order(), contrib,
+                                           st);
     return e == cudaSuccess ? SGAD_OK : cuda_fail(e, fwd ? "forward compositing launch" : "backward compositing launch");
 }
+
+int bwd_batch_of(const sgad_options &o) { return o.bwd_algorithm == SGAD_BWD_PAIRS ? 0 : o.bwd_batch; }
 
 // Output images of sgad_forward into the launch parameters.
 sgad_status bind_images(Scene &sc, const sgad_images *out, int n_views)
@@ -346,6 +352,7 @@ sgad_status sgad_default_options(sgad_options *opt)
     opt->bwd_batch = 256;
     opt->fwd_schedule = SGAD_SCHEDULE_TILES;
     opt->bwd_schedule = SGAD_SCHEDULE_TILES;
+    opt->bwd_algorithm = SGAD_BWD_WARP_REDUCE;
     return SGAD_OK;
 }
 
@@ -368,8 +375,10 @@ sgad_status sgad_create(sgad_ctx **out, const sgad_options *opt)
     const bool shape_ok = (o.tile_w == 16 && o.tile_h == 16) || (o.tile_w == 8 && o.tile_h == 32) ||
                           (o.tile_w == 32 && o.tile_h == 8);
     if (!shape_ok) return fail(SGAD_ERR_UNSUPPORTED, "tile shape %dx%d not supported", o.tile_w, o.tile_h);
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i] != 0) return fail(SGAD_ERR_INVALID_ARG, "reserved options must be zero");
+    if (o.bwd_algorithm != SGAD_BWD_PAIRS && o.bwd_algorithm != SGAD_BWD_WARP_REDUCE)
+        return fail(SGAD_ERR_INVALID_ARG, "unknown backward algorithm %d", o.bwd_algorithm);
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(o.bg[c])) return fail(SGAD_ERR_INVALID_ARG, "background must be finite");
     if (o.fwd_batch == 0) o.fwd_batch = 512;
@@ -519,7 +528,7 @@ sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
     mark(ctx, 5, st);
     cudaError_t e = cudaMemsetAsync(ws.gacc(), 0, (size_t)sc.n_gauss * 32, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    s = run_composite(ctx, false, ctx->opt.bwd_batch, ctx->opt.bwd_schedule, sc, ws, st);
+    s = run_composite(ctx, false, bwd_batch_of(ctx->opt), ctx->opt.bwd_schedule, sc, ws, st);
     if (s) return s;
     mark(ctx, 6, st);
     launch_finalize(sc, ws.world(), ws.gacc(), st);
@@ -696,6 +705,7 @@ sgad_status sgad_autotune(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
         log.add(shape[0], shape[1], SGAD_TUNE_PREP, 0, 0, prep);
         float best_f = -1.f, best_b = -1.f;
         int fb = 0, fs = 0, bb = 0, bs = 0;
+        trial.opt.bwd_algorithm = SGAD_BWD_WARP_REDUCE;     // forwards without contribution words
         for (int sched : kScheds)
             for (int batch : kBatches) {
                 float ms = 0.f;
@@ -708,8 +718,16 @@ sgad_status sgad_autotune(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                     fs = sched;
                 }
             }
+        // The pair-parallel backward needs the best forward to record contribution words;
+        // that extra forward cost is charged to the pair-parallel candidates.
+        trial.opt.bwd_algorithm = SGAD_BWD_PAIRS;
+        float fwd_words = 0.f;
+        s = timer.median(reps, st, [&] { return run_composite(&trial, true, fb, fs, sc, ws, st); }, &fwd_words);
+        if (s) return s;
+        const float words_cost = fwd_words > best_f ? fwd_words - best_f : 0.f;
+        static const int kBwdBatches[6] = {0, 128, 192, 256, 384, 512};     // 0: pair-parallel
         for (int sched : kScheds)
-            for (int batch : kBatches) {
+            for (int batch : kBwdBatches) {
                 float ms = 0.f;
                 auto run = [&] {
                     const cudaError_t e = cudaMemsetAsync(ws.gacc(), 0, (size_t)sc.n_gauss * 32, st);
@@ -718,6 +736,7 @@ sgad_status sgad_autotune(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                 };
                 s = timer.median(reps, st, run, &ms);
                 if (s) return s;
+                if (batch == 0) ms += words_cost;
                 log.add(shape[0], shape[1], SGAD_TUNE_BWD, batch, sched, ms);
                 if (best_b < 0.f || ms < best_b) {
                     best_b = ms;
@@ -732,7 +751,8 @@ sgad_status sgad_autotune(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
             best.tile_h = shape[1];
             best.fwd_batch = fb;
             best.fwd_schedule = fs;
-            best.bwd_batch = bb;
+            best.bwd_algorithm = bb == 0 ? SGAD_BWD_PAIRS : SGAD_BWD_WARP_REDUCE;
+            best.bwd_batch = bb == 0 ? ctx->opt.bwd_batch : bb;
             best.bwd_schedule = bs;
         }
     }

@@ -320,7 +320,7 @@ __device__ __forceinline__ bool overlaps(const Staged &s, const WarpRect &r)
 // Workspace layout (byte offsets, 256-aligned sections). Shared by the host API and the
 // kernels' launch code.
 struct Layout {
-    size_t header, world, gacc, tile_off, tile_cnt, tile_order, pix_t, pix_n, keys, keys_alt, total;
+    size_t header, world, gacc, tile_off, tile_cnt, tile_order, pix_t, pix_n, keys, keys_alt, contrib, total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -339,6 +339,7 @@ inline Layout make_layout(uint64_t n_gauss, uint64_t n_tiles, uint64_t n_pix, ui
     L.pix_n = o; o = align256(o + n_pix * 4);
     L.keys = o; o = align256(o + key_cap * 8);
     L.keys_alt = o; o = align256(o + key_cap * 8);
+    L.contrib = o; o = align256(o + (key_cap * 8 + (n_tiles + 1) * 256) * 4);
     L.total = o;
     return L;
 }

@@ -79,7 +79,8 @@ class Splatter:
     """A library context plus a workspace sized for one problem shape."""
 
     def __init__(self, tile=(16, 16), bg=(0.0, 0.0, 0.0), sort_smem_cap: int = 0, freeze_offset: bool = False,
-                 fwd_batch: int = 0, bwd_batch: int = 0, fwd_schedule="tiles", bwd_schedule="tiles"):
+                 fwd_batch: int = 0, bwd_batch: int = 0, fwd_schedule="tiles", bwd_schedule="tiles",
+                 bwd_algorithm: str = "warp_reduce"):
         o = B.sgad_default_options()
         o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
         for i in range(3):
@@ -92,6 +93,7 @@ class Splatter:
             o.bwd_batch = int(bwd_batch)
         o.fwd_schedule = _schedule(fwd_schedule)
         o.bwd_schedule = _schedule(bwd_schedule)
+        o.bwd_algorithm = {"pairs": B.SGAD_BWD_PAIRS, "warp_reduce": B.SGAD_BWD_WARP_REDUCE}[bwd_algorithm]
         self.options = o
         self.ctx = B.sgad_create(o)
         self.workspace: Optional[torch.Tensor] = None

@@ -33,6 +33,7 @@ def test_default_options_and_create():
     assert (o.tile_w, o.tile_h) == (16, 16) and o.freeze_offset == 0
     assert (o.fwd_batch, o.bwd_batch) == (512, 256)
     assert o.fwd_schedule == o.bwd_schedule == B.SGAD_SCHEDULE_TILES
+    assert o.bwd_algorithm == B.SGAD_BWD_WARP_REDUCE
     ctx = B.sgad_create(o)
     B.sgad_destroy(ctx)
     for w, h in ((8, 32), (32, 8)):
@@ -78,6 +79,7 @@ def test_autotune_validates_on_the_host():
     ("bwd_batch", 1024, B.SGAD_ERR_UNSUPPORTED),
     ("fwd_schedule", 3, B.SGAD_ERR_INVALID_ARG),
     ("bwd_schedule", -1, B.SGAD_ERR_INVALID_ARG),
+    ("bwd_algorithm", 2, B.SGAD_ERR_INVALID_ARG),
 ])
 def test_create_rejects_bad_options(field, value, status):
     o = B.sgad_default_options()
@@ -96,15 +98,17 @@ def _cam(w=64, h=48):
 
 
 def test_workspace_size_arithmetic():
-    """Workspace = header + 64 B per Gaussian + tile offsets/counters + 8 B per view pixel
-    + 16 B per key, each section rounded to 256 B."""
+    """Workspace = header + 64 B per Gaussian + tile offsets/counters/order + 8 B per view
+    pixel + 16 B per key of key arrays + 32 B per key (+ 1 KB per tile) of contribution
+    words, each section rounded to 256 B."""
     ctx = B.sgad_create()
     kfs = (B.sgad_keyframe * 1)()
     kfs[0].cam = _cam()
     views = (B.sgad_camera * 2)(_cam(), _cam(100, 70))
     n0 = B.sgad_workspace_size(ctx, kfs, views, 0)
     n1 = B.sgad_workspace_size(ctx, kfs, views, 1000)
-    assert n1 - n0 == 2 * ((1000 * 8 + 255) // 256 * 256)
+    # two 8-byte key arrays and 32 bytes of contribution words per key
+    assert n1 - n0 == 2 * ((1000 * 8 + 255) // 256 * 256) + 1000 * 32
     ng, npx = 64 * 48, 64 * 48 + 100 * 70
     assert n0 >= 256 + 64 * ng + 8 * npx
     B.sgad_destroy(ctx)

@@ -59,10 +59,11 @@ def test_every_split_matches_default(uneven, uneven_grads, tile):
     base = gpu_run(uneven, grads_in=uneven_grads, tile=tile)
     for sched in SCHEDULES:
         for fb, bb in zip(BATCHES, BATCHES[::-1]):
-            res = gpu_run(uneven, grads_in=uneven_grads, tile=tile, fwd_batch=fb, bwd_batch=bb,
-                          fwd_schedule=sched, bwd_schedule=sched)
-            _same_forward(res, base)
-            _close_grads(res, base)
+            for algo in ("pairs", "warp_reduce"):
+                res = gpu_run(uneven, grads_in=uneven_grads, tile=tile, fwd_batch=fb, bwd_batch=bb,
+                              fwd_schedule=sched, bwd_schedule=sched, bwd_algorithm=algo)
+                _same_forward(res, base)
+                _close_grads(res, base)
 
 
 @pytest.mark.parametrize("tile", SHAPES)
@@ -95,10 +96,13 @@ def test_autotune_times_every_candidate(uneven, uneven_grads):
     gout = [dict(d_offset=torch.empty_like(k.offset), d_rgb=torch.empty_like(k.rgb), d_logit=torch.empty_like(k.logit),
                  d_scale=torch.empty_like(k.scale)) for k in kfs]
     rows = sp.autotune(kfs, uneven.views, images, gin, gout, reps=2)
-    assert len(rows) == 3 * (1 + 2 * 2 * len(BATCHES))
+    # per tile shape: the prep row, forward batches x schedules, backward (pair-parallel
+    # as batch 0, then the warp-reduced batches) x schedules
+    assert len(rows) == 3 * (1 + 2 * len(BATCHES) + 2 * (len(BATCHES) + 1))
     assert all(r["ms"] > 0 for r in rows)
     o = sp.options
     assert (o.tile_w, o.tile_h) in SHAPES and o.fwd_batch in BATCHES and o.bwd_batch in BATCHES
+    assert o.bwd_algorithm in (B.SGAD_BWD_PAIRS, B.SGAD_BWD_WARP_REDUCE)
     assert o.fwd_schedule in (B.SGAD_SCHEDULE_TILES, B.SGAD_SCHEDULE_PERSISTENT)
     # the chosen split renders what the default split of that tile shape renders
     sp.forward(kfs, uneven.views, images)

@@ -58,6 +58,14 @@ def test_crop_forward_backward(crop):
     assert e <= 1.0
 
 
+def test_crop_pair_parallel_backward(crop):
+    """The pair-parallel backward (the non-default algorithm) against the oracle."""
+    ref, g = _grads_for(crop)
+    res = gpu_run(crop, grads_in=g, bwd_algorithm="pairs")
+    og = oracle.backward(crop, [{k: v.astype(np.float64) for k, v in x.items()} for x in g])
+    assert compare_grads(res, og) <= 1.0
+
+
 @pytest.mark.parametrize("tile", [(8, 32), (32, 8)])
 def test_crop_other_tile_shapes(crop, tile):
     o = oracle.opts(tile_w=tile[0], tile_h=tile[1])
