@@ -141,7 +141,8 @@ typedef struct {
     int32_t freeze_offset;       /* 1: delta is held fixed (Table 9 "Mode3"): d_offset is
                                     written as zeros */
     int32_t fwd_batch;           /* list entries staged per thread-block barrier in forward
-                                    compositing: 128, 192, 256, 384 or 512; 0 = default (512) */
+                                    compositing: 128, 192, 256, 384, 512, 768 or 1024;
+                                    0 = default (512) */
     int32_t bwd_batch;           /* the same for the warp-reduced backward; 0 = default (256) */
     int32_t fwd_schedule;        /* SGAD_SCHEDULE_* of forward compositing (default TILES) */
     int32_t bwd_schedule;        /* SGAD_SCHEDULE_* of backward compositing (default TILES) */
@@ -201,6 +202,7 @@ sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
 
 /* Project-written autotuner for one problem shape (synchronous; not capturable).
  * Sweeps the tile shapes {16x16, 8x32, 32x8}, the batch sizes {128, 192, 256, 384, 512}
+ * (forward also 768 and 1024)
  * and the schedules {TILES, PERSISTENT} of both compositing passes (and, for the
  * backward, the pair-parallel algorithm, reported with batch 0 and charged with the cost
  * of the contribution words its forward writes), timing each candidate

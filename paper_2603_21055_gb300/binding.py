@@ -67,7 +67,8 @@ SGAD_SCHEDULE_TILES = 0
 SGAD_SCHEDULE_PERSISTENT = 1
 SGAD_SCHEDULE_PER_VIEW = 2
 SCHEDULE_NAMES = {0: "tiles", 1: "persistent", 2: "per_view"}
-BATCH_SIZES = (128, 192, 256, 384, 512)
+BATCH_SIZES = (128, 192, 256, 384, 512)          # both compositing passes
+FWD_BATCH_SIZES = BATCH_SIZES + (768, 1024)      # forward only
 TILE_SHAPES = ((16, 16), (8, 32), (32, 8))
 
 

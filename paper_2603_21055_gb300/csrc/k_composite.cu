@@ -24,10 +24,13 @@ cudaError_t dispatch(bool fwd, int batch, const Scene &sc, const CompositeArgs &
 
 }  // namespace
 
-bool valid_batch(int batch)
+bool valid_batch(int batch, bool fwd)
 {
     for (int b : kBatchSizes)
         if (b == batch) return true;
+    if (fwd)
+        for (int b : kFwdOnlyBatchSizes)
+            if (b == batch) return true;
     return false;
 }
 

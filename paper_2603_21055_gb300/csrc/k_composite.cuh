@@ -103,6 +103,85 @@ __device__ __forceinline__ void stage_entry(const Scene &sc, const CompositeArgs
 
 // ------------------------------------------------------------------ forward
 
+// Double-buffered staging (one block barrier per batch instead of two) measured slower
+// on the room workload (the prefetched last batch and the halved occupancy cost more than
+// the barrier saves); it stays available at build time.
+#ifndef SGAD_FWD_DOUBLE_BUFFER
+#define SGAD_FWD_DOUBLE_BUFFER 0
+#endif
+constexpr int kFwdBuffers = SGAD_FWD_DOUBLE_BUFFER ? 2 : 1;
+
+// Resident-block target of the forward kernel for batch B: as many blocks as the staging
+// buffers let share an SM (227 KB), at most SGAD_FWD_MINBLOCKS; it bounds the registers.
+template <int B>
+constexpr int fwd_min_blocks()
+{
+    const int fit = (227 * 1024) / (kFwdBuffers * B * (int)sizeof(Staged) + 1024);
+    return fit < 1 ? 1 : (fit > SGAD_FWD_MINBLOCKS ? SGAD_FWD_MINBLOCKS : fit);
+}
+
+// Stage entries [b0, min(b0 + B, e)) of the tile list into buf (one or more per thread).
+template <int B>
+__device__ __forceinline__ void stage_batch(const Scene &sc, const CompositeArgs &a, const ViewDev &v, uint32_t b0,
+                                            uint32_t e, Staged *buf)
+{
+#pragma unroll
+    for (int r = 0; r < (B + kFwdThreads - 1) / kFwdThreads; ++r) {
+        const int k = r * kFwdThreads + threadIdx.x;
+        if (k < B && b0 + k < e) stage_entry(sc, a, v, a.entries[b0 + k], buf[k]);
+    }
+}
+
+// Per-pixel running state of the forward walk.
+struct FwdPixel {
+    float T, cr, cg, cb, dd, aa;
+    int last;
+    bool done;
+};
+
+// The warp walks nb staged entries (list positions b0 - s ...) against its pixel block:
+// 32 entries at a time, a ballot of those whose alpha box reaches the block, then each
+// of them in order for every pixel not yet done.
+__device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0, uint32_t s, int tile,
+                                           const CompositeArgs &a, const WarpRect &wr, float qx, float qy, int lane,
+                                           FwdPixel &px, bool &warp_done, uint32_t &n_pairs, uint32_t &n_evals)
+{
+    for (int c0 = 0; c0 < nb; c0 += 32) {
+        const int j = c0 + lane;
+        const uint32_t hits = __ballot_sync(kFull, j < nb && overlaps(sm[j], wr));
+        uint32_t mask = hits, bits = 0;
+        while (mask) {
+            const int jj = c0 + __ffs(mask) - 1;
+            mask &= mask - 1;
+            if (px.done) continue;
+            const Staged st = sm[jj];
+            float dx, dy, ep, alpha;
+            ++n_evals;
+            if (!gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) continue;
+            const float test = __fmul_rn(px.T, __fsub_rn(1.0f, alpha));
+            if (test < kTStop) {
+                px.done = true;
+                continue;
+            }
+            ++n_pairs;
+            bits |= 1u << (jj - c0);
+            const float w = __fmul_rn(alpha, px.T);
+            px.cr = __fmaf_rn(w, st.c.x, px.cr);
+            px.cg = __fmaf_rn(w, st.c.y, px.cg);
+            px.cb = __fmaf_rn(w, st.c.z, px.cb);
+            px.dd = __fmaf_rn(w, st.c.w, px.dd);
+            px.aa = __fadd_rn(px.aa, w);
+            px.T = test;
+            px.last = (int)(b0 + jj - s);
+        }
+        if (a.contrib) a.contrib[contrib_base(a, tile, s) + (size_t)((b0 - s + c0) >> 5) * 256 + threadIdx.x] = bits;
+        if (__all_sync(kFull, px.done)) {
+            warp_done = true;
+            break;
+        }
+    }
+}
+
 template <int TW, int TH, int B>
 __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a, int tile, Staged *sm,
                                          uint32_t &n_pairs, uint32_t &n_evals)
@@ -118,73 +197,51 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
     const WarpRect wr = {(float)bx, (float)by, (float)(bx + 7), (float)(by + 3)};
     const float qx = (float)px, qy = (float)py;
 
-    float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f, aa = 0.f;
-    int last = -1;
-    bool done = !inside;
-    bool warp_done = __all_sync(kFull, done);
+    FwdPixel st = {1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, !inside};
+    bool warp_done = __all_sync(kFull, st.done);
     const uint32_t s = a.off[tile], e = a.off[tile + 1];
-    for (uint32_t b0 = s; b0 < e; b0 += B) {
-        if (__syncthreads_and(done)) break;
-#pragma unroll
-        for (int r = 0; r < (B + kFwdThreads - 1) / kFwdThreads; ++r) {
-            const int k = r * kFwdThreads + threadIdx.x;
-            if (k < B && b0 + k < e) stage_entry(sc, a, v, a.entries[b0 + k], sm[k]);
-        }
+#if SGAD_FWD_DOUBLE_BUFFER
+    // Two staging buffers: batch k + 1 is staged into the other buffer before batch k is
+    // walked, so one block barrier per batch both publishes the next batch and ends the
+    // walk of this one (and tests for the early exit).
+    if (!__syncthreads_and(st.done) && s < e) {
+        stage_batch<B>(sc, a, v, s, e, sm);
         __syncthreads();
-        const int nb = (int)min((uint32_t)B, e - b0);
-        if (warp_done) continue;
-        for (int c0 = 0; c0 < nb; c0 += 32) {
-            const int j = c0 + lane;
-            const uint32_t hits = __ballot_sync(kFull, j < nb && overlaps(sm[j], wr));
-            uint32_t mask = hits, bits = 0;
-            while (mask) {
-                const int jj = c0 + __ffs(mask) - 1;
-                mask &= mask - 1;
-                if (done) continue;
-                const Staged st = sm[jj];
-                float dx, dy, ep, alpha;
-                ++n_evals;
-                if (!gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) continue;
-                const float test = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-                if (test < kTStop) {
-                    done = true;
-                    continue;
-                }
-                ++n_pairs;
-                bits |= 1u << (jj - c0);
-                const float w = __fmul_rn(alpha, T);
-                cr = __fmaf_rn(w, st.c.x, cr);
-                cg = __fmaf_rn(w, st.c.y, cg);
-                cb = __fmaf_rn(w, st.c.z, cb);
-                dd = __fmaf_rn(w, st.c.w, dd);
-                aa = __fadd_rn(aa, w);
-                T = test;
-                last = (int)(b0 + jj - s);
-            }
-            if (a.contrib) a.contrib[contrib_base(a, tile, s) + (size_t)((b0 - s + c0) >> 5) * 256 + threadIdx.x] = bits;
-            if (__all_sync(kFull, done)) {
-                warp_done = true;
-                break;
-            }
+        int parity = 0;
+        for (uint32_t b0 = s; b0 < e; b0 += B, parity ^= 1) {
+            if (b0 + B < e) stage_batch<B>(sc, a, v, b0 + B, e, sm + (parity ^ 1) * B);
+            const int nb = (int)min((uint32_t)B, e - b0);
+            if (!warp_done) walk_batch(sm + parity * B, nb, b0, s, tile, a, wr, qx, qy, lane, st, warp_done, n_pairs, n_evals);
+            if (__syncthreads_and(st.done)) break;
         }
     }
+#else
+    for (uint32_t b0 = s; b0 < e; b0 += B) {
+        if (__syncthreads_and(st.done)) break;
+        stage_batch<B>(sc, a, v, b0, e, sm);
+        __syncthreads();
+        const int nb = (int)min((uint32_t)B, e - b0);
+        if (!warp_done) walk_batch(sm, nb, b0, s, tile, a, wr, qx, qy, lane, st, warp_done, n_pairs, n_evals);
+    }
+#endif
     if (inside) {
         const size_t hw = (size_t)v.W * v.H, p = (size_t)py * v.W + px;
-        v.rgb[p] = cr + T * sc.bg[0];
-        v.rgb[hw + p] = cg + T * sc.bg[1];
-        v.rgb[2 * hw + p] = cb + T * sc.bg[2];
-        v.depth[p] = dd;
-        v.alpha[p] = aa;
-        a.pix_t[v.pix_base + p] = T;
-        a.pix_n[v.pix_base + p] = (uint32_t)(last + 1);
+        v.rgb[p] = st.cr + st.T * sc.bg[0];
+        v.rgb[hw + p] = st.cg + st.T * sc.bg[1];
+        v.rgb[2 * hw + p] = st.cb + st.T * sc.bg[2];
+        v.depth[p] = st.dd;
+        v.alpha[p] = st.aa;
+        a.pix_t[v.pix_base + p] = st.T;
+        a.pix_n[v.pix_base + p] = (uint32_t)(st.last + 1);
     }
 }
 
 template <int TW, int TH, int B>
-__global__ void __launch_bounds__(kFwdThreads, SGAD_FWD_MINBLOCKS)
+__global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks<B>())
     k_composite_fwd(const __grid_constant__ Scene sc, const CompositeArgs a)
 {
-    __shared__ Staged sm[B];
+    extern __shared__ float4 fwd_smem[];
+    Staged *sm = reinterpret_cast<Staged *>(fwd_smem);     // kFwdBuffers x B staged entries
     __shared__ int s_tile;
     if (a.hdr->overflow) return;
     uint32_t n_pairs = 0, n_evals = 0;
@@ -587,7 +644,8 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_composite_bwdp(const __grid
 // ------------------------------------------------------------------ launch
 
 // Batch sizes the kernels are built for (entries staged per block-wide barrier).
-constexpr int kBatchSizes[] = {128, 192, 256, 384, 512};
+constexpr int kBatchSizes[] = {128, 192, 256, 384, 512};          // both passes
+constexpr int kFwdOnlyBatchSizes[] = {768, 1024};                 // forward only
 
 // Launches one direction for tile shape TW x TH with batch B. grid_blocks > 0: that many
 // blocks (one per tile from tile0, or the persistent grid); returns the launch error.
@@ -596,8 +654,21 @@ cudaError_t launch_composite_tb(bool fwd, const Scene &sc, const CompositeArgs &
 {
     if (grid_blocks <= 0) return cudaSuccess;
     if (fwd) {
-        k_composite_fwd<TW, TH, B><<<grid_blocks, kFwdThreads, 0, st>>>(sc, a);
-    } else {
+        // the dynamic staging buffers plus the kernel's static slot may pass the 48 KB
+        // default: raise the limit (once per device)
+        constexpr size_t smem = (size_t)kFwdBuffers * B * sizeof(Staged);
+        static int configured[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64 || !configured[dev]) {
+            e = cudaFuncSetAttribute(k_composite_fwd<TW, TH, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) configured[dev] = 1;
+        }
+        k_composite_fwd<TW, TH, B><<<grid_blocks, kFwdThreads, smem, st>>>(sc, a);
+    } else if constexpr (B <= 512) {
         constexpr size_t smem = bwd_smem_bytes<B>();
         static int configured[64] = {};
         int dev = 0;
@@ -609,6 +680,8 @@ cudaError_t launch_composite_tb(bool fwd, const Scene &sc, const CompositeArgs &
             if (dev >= 0 && dev < 64) configured[dev] = 1;
         }
         k_composite_bwd<TW, TH, B><<<grid_blocks, kBwdThreads, smem, st>>>(sc, a);
+    } else {
+        return cudaErrorInvalidValue;     // the backward is built for batches up to 512
     }
     return cudaGetLastError();
 }
@@ -617,10 +690,18 @@ cudaError_t launch_composite_tb(bool fwd, const Scene &sc, const CompositeArgs &
 template <int TW, int TH, int B>
 cudaError_t occupancy_tb(bool fwd, int *blocks_per_sm)
 {
-    if (fwd)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_composite_fwd<TW, TH, B>, kFwdThreads, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_composite_bwd<TW, TH, B>, kBwdThreads,
-                                                         bwd_smem_bytes<B>());
+    if (fwd) {
+        constexpr size_t smem = (size_t)kFwdBuffers * B * sizeof(Staged);
+        const cudaError_t e = cudaFuncSetAttribute(k_composite_fwd<TW, TH, B>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_composite_fwd<TW, TH, B>, kFwdThreads,
+                                                             smem);
+    }
+    if constexpr (B <= 512)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_composite_bwd<TW, TH, B>, kBwdThreads,
+                                                             bwd_smem_bytes<B>());
+    return cudaErrorInvalidValue;
 }
 
 template <int TW, int TH>
@@ -651,6 +732,14 @@ cudaError_t launch_composite_shape(bool fwd, int batch, const Scene &sc, const C
         SGAD_BATCH_CASE(256)
         SGAD_BATCH_CASE(384)
         SGAD_BATCH_CASE(512)
+    case 768:
+        if (!fwd) return cudaErrorInvalidValue;
+        return occupancy ? occupancy_tb<TW, TH, 768>(true, occupancy)
+                         : launch_composite_tb<TW, TH, 768>(true, sc, a, grid_blocks, st);
+    case 1024:
+        if (!fwd) return cudaErrorInvalidValue;
+        return occupancy ? occupancy_tb<TW, TH, 1024>(true, occupancy)
+                         : launch_composite_tb<TW, TH, 1024>(true, sc, a, grid_blocks, st);
     default:
         return cudaErrorInvalidValue;
     }

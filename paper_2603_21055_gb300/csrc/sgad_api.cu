@@ -15,7 +15,7 @@ void launch_emit(const Scene &, const World *, const uint32_t *, uint32_t *, uin
 cudaError_t launch_sort_tiles(const uint32_t *, uint64_t *, uint64_t *, int, int, const WsHeader *, cudaStream_t);
 cudaError_t launch_composite(bool, int, int, const Scene &, const World *, const uint32_t *, const uint64_t *, float *,
                              uint32_t *, float4 *, WsHeader *, const uint32_t *, uint32_t *, cudaStream_t);
-bool valid_batch(int);
+bool valid_batch(int, bool);
 void launch_finalize(const Scene &, const World *, const float4 *, cudaStream_t);
 void launch_l1_batch(int, const float *const *, const float *const *, const float *const *, const float *const *,
                      float *const *, float *const *, uint32_t *, const uint32_t *, float, float, float *, cudaStream_t);
@@ -383,8 +383,9 @@ sgad_status sgad_create(sgad_ctx **out, const sgad_options *opt)
         if (!std::isfinite(o.bg[c])) return fail(SGAD_ERR_INVALID_ARG, "background must be finite");
     if (o.fwd_batch == 0) o.fwd_batch = 512;
     if (o.bwd_batch == 0) o.bwd_batch = 256;
-    if (!valid_batch(o.fwd_batch) || !valid_batch(o.bwd_batch))
-        return fail(SGAD_ERR_UNSUPPORTED, "batch sizes must be 128, 192, 256, 384 or 512");
+    if (!valid_batch(o.fwd_batch, true) || !valid_batch(o.bwd_batch, false))
+        return fail(SGAD_ERR_UNSUPPORTED,
+                    "batch sizes must be 128, 192, 256, 384 or 512 (forward also 768 or 1024)");
     for (int sch : {o.fwd_schedule, o.bwd_schedule})
         if (sch != SGAD_SCHEDULE_TILES && sch != SGAD_SCHEDULE_PERSISTENT && sch != SGAD_SCHEDULE_PER_VIEW)
             return fail(SGAD_ERR_INVALID_ARG, "unknown schedule %d", sch);
@@ -657,7 +658,7 @@ sgad_status sgad_autotune(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
     if (reps < 1 || reps > 100) return fail(SGAD_ERR_INVALID_ARG, "reps must be in [1, 100]");
     if (max_entries < 0 || (max_entries > 0 && !entries)) return fail(SGAD_ERR_INVALID_ARG, "bad entries buffer");
     static const int kShapes[3][2] = {{16, 16}, {8, 32}, {32, 8}};
-    static const int kBatches[5] = {128, 192, 256, 384, 512};
+    static const int kBatches[7] = {128, 192, 256, 384, 512, 768, 1024};     // forward
     static const int kScheds[2] = {SGAD_SCHEDULE_TILES, SGAD_SCHEDULE_PERSISTENT};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     TuneTimer timer;

@@ -44,7 +44,7 @@ def test_default_options_and_create():
 def test_work_split_options_round_trip():
     """Every batch size and schedule is accepted and read back unchanged; 0 batches take
     the defaults."""
-    for fb in B.BATCH_SIZES:
+    for fb in B.FWD_BATCH_SIZES:
         for sched in (B.SGAD_SCHEDULE_TILES, B.SGAD_SCHEDULE_PERSISTENT, B.SGAD_SCHEDULE_PER_VIEW):
             o = B.sgad_default_options()
             o.fwd_batch, o.bwd_batch, o.fwd_schedule, o.bwd_schedule = fb, B.BATCH_SIZES[-1], sched, sched
@@ -76,6 +76,7 @@ def test_autotune_validates_on_the_host():
     ("tile_w", 12, B.SGAD_ERR_UNSUPPORTED),
     ("sort_smem_cap", 8, B.SGAD_ERR_INVALID_ARG),
     ("fwd_batch", 100, B.SGAD_ERR_UNSUPPORTED),
+    ("fwd_batch", 2048, B.SGAD_ERR_UNSUPPORTED),
     ("bwd_batch", 1024, B.SGAD_ERR_UNSUPPORTED),
     ("fwd_schedule", 3, B.SGAD_ERR_INVALID_ARG),
     ("bwd_schedule", -1, B.SGAD_ERR_INVALID_ARG),

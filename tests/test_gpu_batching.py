@@ -58,7 +58,7 @@ def _close_grads(a, b):
 def test_every_split_matches_default(uneven, uneven_grads, tile):
     base = gpu_run(uneven, grads_in=uneven_grads, tile=tile)
     for sched in SCHEDULES:
-        for fb, bb in zip(BATCHES, BATCHES[::-1]):
+        for fb, bb in zip(BATCHES + (768, 1024), BATCHES[::-1] + (256, 128)):
             for algo in ("pairs", "warp_reduce"):
                 res = gpu_run(uneven, grads_in=uneven_grads, tile=tile, fwd_batch=fb, bwd_batch=bb,
                               fwd_schedule=sched, bwd_schedule=sched, bwd_algorithm=algo)
@@ -98,10 +98,10 @@ def test_autotune_times_every_candidate(uneven, uneven_grads):
     rows = sp.autotune(kfs, uneven.views, images, gin, gout, reps=2)
     # per tile shape: the prep row, forward batches x schedules, backward (pair-parallel
     # as batch 0, then the warp-reduced batches) x schedules
-    assert len(rows) == 3 * (1 + 2 * len(BATCHES) + 2 * (len(BATCHES) + 1))
+    assert len(rows) == 3 * (1 + 2 * (len(BATCHES) + 2) + 2 * (len(BATCHES) + 1))
     assert all(r["ms"] > 0 for r in rows)
     o = sp.options
-    assert (o.tile_w, o.tile_h) in SHAPES and o.fwd_batch in BATCHES and o.bwd_batch in BATCHES
+    assert (o.tile_w, o.tile_h) in SHAPES and o.fwd_batch in BATCHES + (768, 1024) and o.bwd_batch in BATCHES
     assert o.bwd_algorithm in (B.SGAD_BWD_PAIRS, B.SGAD_BWD_WARP_REDUCE)
     assert o.fwd_schedule in (B.SGAD_SCHEDULE_TILES, B.SGAD_SCHEDULE_PERSISTENT)
     # the chosen split renders what the default split of that tile shape renders
