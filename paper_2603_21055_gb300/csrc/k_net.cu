@@ -20,6 +20,7 @@
 // ldmatrix.trans / stmatrix (one copy per dx shift); the accumulators stay in tensor
 // memory across all K blocks of the persistent block and are added to the output with
 // one atomic per (row, column) at the end.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "sgad_net_device.cuh"
@@ -123,6 +124,48 @@ struct ConvSmem {
 
 __device__ __forceinline__ bool bf16_positive(uint32_t half_bits) { return (half_bits & 0x8000u) == 0 && (half_bits & 0x7FFFu) != 0; }
 
+// Epilogue of one output pixel p from its accumulator row r (CO f32 values).
+template <int CO, int MODE>
+__device__ __forceinline__ void conv_epilogue(const ConvArgs &a, size_t p, const uint32_t (&r)[32])
+{
+    if (MODE == kModeOut) {
+        const float y0 = __uint_as_float(r[0]) + a.bias[0], y1 = __uint_as_float(r[1]) + a.bias[1];
+        a.y4[p] = make_float2(y0, y1);
+        if (a.delta) a.delta[p] = 0.01f * y0;
+        if (a.logit) a.logit[p] = y1;
+    } else {
+        uint32_t packed[CO / 2];
+        if (MODE == kModeRelu) {
+#pragma unroll
+            for (int c = 0; c < CO; c += 2) {
+                const float v0 = fmaxf(__uint_as_float(r[c]) + a.bias[c], 0.0f);
+                const float v1 = fmaxf(__uint_as_float(r[c + 1]) + a.bias[c + 1], 0.0f);
+                __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                packed[c / 2] = *reinterpret_cast<uint32_t *>(&h);
+            }
+        } else {     // kModeMask: input gradient times [activation > 0]
+            const uint4 *mk = a.mask + p * (CO / 8);
+#pragma unroll
+            for (int u = 0; u < CO / 8; ++u) {
+                const uint4 mm = __ldg(&mk[u]);
+                const uint32_t mw[4] = {mm.x, mm.y, mm.z, mm.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = 8 * u + 2 * j;
+                    const float v0 = bf16_positive(mw[j] & 0xFFFFu) ? __uint_as_float(r[c]) : 0.0f;
+                    const float v1 = bf16_positive(mw[j] >> 16) ? __uint_as_float(r[c + 1]) : 0.0f;
+                    __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                    packed[c / 2] = *reinterpret_cast<uint32_t *>(&h);
+                }
+            }
+        }
+        uint4 *dst = a.out + p * (CO / 8);
+#pragma unroll
+        for (int u = 0; u < CO / 8; ++u)
+            dst[u] = make_uint4(packed[4 * u], packed[4 * u + 1], packed[4 * u + 2], packed[4 * u + 3]);
+    }
+}
+
 template <int CI, int CO, int MODE>
 __global__ void __launch_bounds__(128) k_conv3x3(const ConvArgs a)
 {
@@ -206,51 +249,165 @@ __global__ void __launch_bounds__(128) k_conv3x3(const ConvArgs a)
             }
         }
         tc::tmem_wait_ld();
-        if (x < a.W) {
-            const size_t p = ((size_t)n * a.H + y) * a.W + x;
-            if (MODE == kModeOut) {
-                const float y0 = __uint_as_float(r[0]) + a.bias[0], y1 = __uint_as_float(r[1]) + a.bias[1];
-                a.y4[p] = make_float2(y0, y1);
-                if (a.delta) a.delta[p] = 0.01f * y0;
-                if (a.logit) a.logit[p] = y1;
-            } else {
-                uint32_t packed[CO / 2];
-                if (MODE == kModeRelu) {
-#pragma unroll
-                    for (int c = 0; c < CO; c += 2) {
-                        const float v0 = fmaxf(__uint_as_float(r[c]) + a.bias[c], 0.0f);
-                        const float v1 = fmaxf(__uint_as_float(r[c + 1]) + a.bias[c + 1], 0.0f);
-                        __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                        packed[c / 2] = *reinterpret_cast<uint32_t *>(&h);
-                    }
-                } else {     // kModeMask: input gradient times [activation > 0]
-                    const uint4 *mk = a.mask + p * (CO / 8);
-#pragma unroll
-                    for (int u = 0; u < CO / 8; ++u) {
-                        const uint4 mm = __ldg(&mk[u]);
-                        const uint32_t mw[4] = {mm.x, mm.y, mm.z, mm.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int c = 8 * u + 2 * j;
-                            const float v0 = bf16_positive(mw[j] & 0xFFFFu) ? __uint_as_float(r[c]) : 0.0f;
-                            const float v1 = bf16_positive(mw[j] >> 16) ? __uint_as_float(r[c + 1]) : 0.0f;
-                            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                            packed[c / 2] = *reinterpret_cast<uint32_t *>(&h);
-                        }
-                    }
-                }
-                uint4 *dst = a.out + p * (CO / 8);
-#pragma unroll
-                for (int u = 0; u < CO / 8; ++u)
-                    dst[u] = make_uint4(packed[4 * u], packed[4 * u + 1], packed[4 * u + 2], packed[4 * u + 3]);
-            }
-        }
+        if (x < a.W) conv_epilogue<CO, MODE>(a, ((size_t)n * a.H + y) * a.W + x, r);
         tc::fence_before_sync();
         __syncthreads();     // all reads of this tile's accumulator and staged rows are done
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 32);
+}
+
+// ------------------------------------------------------------------ conv, TMA-fed pipeline
+//
+// The same tiles, operands and epilogues as k_conv3x3, with the work split between warps
+// so that loads, MMAs and epilogues of consecutive tiles overlap:
+//   warp 0 (one lane)  TMA producer: the three input rows of a tile arrive as 3 x CI/8
+//                      boxes (8 channels x 130 pixels, zero-filled outside the image)
+//                      into one of kStages shared-memory stages; an mbarrier counts the
+//                      bytes;
+//   warp 1 (one lane)  MMA issuer: waits for a full stage and a free accumulator, issues
+//                      the 9 x CI/16 MMAs into one of two TMEM accumulators, and commits
+//                      to the stage's "empty" and the accumulator's "full" barriers;
+//   warps 2-5          epilogue: wait for a full accumulator, read their 32 rows (warp
+//                      w reads lanes 32 (w % 4) ...), release the accumulator, store.
+// Every wait is bounded; a wait that gives up records a status and ends the block's loop.
+constexpr int kStages = 2;
+constexpr int kSlabUnits = 136;        // 16-byte units per staged (row, chunk) slab: 130 used, 128-byte aligned
+
+template <int CI, int CO>
+struct TmaConvSmem {
+    static constexpr int kB = 9 * (CI / 8) * CO * 16;                 // weights (bytes)
+    static constexpr int kStage = 3 * (CI / 8) * kSlabUnits * 16;     // one stage of input rows
+    static constexpr int kStageTx = 3 * (CI / 8) * kRowUnits * 16;    // bytes the TMA boxes deliver
+    static constexpr size_t bytes = (size_t)kB + (size_t)kStages * kStage + 1024;   // + alignment slack
+};
+
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(192) k_conv3x3_tma(const __grid_constant__ CUtensorMap tmap, const ConvArgs a)
+{
+    static_assert(CI % 16 == 0 && (CO == 16 || CO == 32), "channel counts");
+    using S = TmaConvSmem<CI, CO>;
+    constexpr int kcn = CI / 8;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint4 *sB = reinterpret_cast<uint4 *>(base);
+    uint8_t *sA = base + S::kB;
+    __shared__ uint64_t full[kStages], empty[kStages], tfull[2], tempty[2];
+    __shared__ uint32_t taddr_s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int segs = (a.W + kTileM - 1) / kTileM;
+    const long long n_tiles = (long long)a.N * a.H * segs;
+
+    if (warp == 0) tc::tmem_alloc(&taddr_s, 64);
+    if (threadIdx.x == 32) {
+        for (int i = 0; i < kStages; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&tfull[i], 1);
+            tc::mbar_init(&tempty[i], 4);
+        }
+    }
+    for (int i = threadIdx.x; i < S::kB / 16; i += blockDim.x) sB[i] = a.wB[i];
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = taddr_s;
+    constexpr uint32_t idesc = tc::idesc_bf16(kTileM, CO);
+
+    if (warp == 0) {
+        if (lane == 0) {                                       // TMA producer
+            int k = 0;
+            for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+                // (the stage's previous box landed before the MMA that freed it ran)
+                const int st = k % kStages;
+                if (!tc::mbar_wait_bounded(&empty[st], ((k / kStages) & 1) ^ 1, kSpinLimit)) {
+                    set_status(a.status, 3u);
+                    break;
+                }
+                const int xs = (int)(tile % segs);
+                const long long ry = tile / segs;
+                const int y = (int)(ry % a.H), n = (int)(ry / a.H);
+                tc::mbar_arrive_expect_tx(&full[st], (uint32_t)S::kStageTx);
+                const uint32_t dst0 = tc::smem_u32(sA + (size_t)st * S::kStage);
+                for (int dy = 0; dy < 3; ++dy)
+                    for (int kc = 0; kc < kcn; ++kc)
+                        tc::tma_load_4d(dst0 + (uint32_t)((dy * kcn + kc) * kSlabUnits * 16), &tmap, 8 * kc,
+                                        xs * kTileM - 1, y + dy - 1, n, &full[st]);
+            }
+            // drain: the last boxes have landed before the block may exit
+            if (k > 0) tc::mbar_wait_bounded(&full[(k - 1) % kStages], ((k - 1) / kStages) & 1, kSpinLimit);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                                       // MMA issuer
+            int k = 0;
+            for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+                const int st = k % kStages, acc = k & 1;
+                if (!tc::mbar_wait_bounded(&full[st], (k / kStages) & 1, kSpinLimit) ||
+                    !tc::mbar_wait_bounded(&tempty[acc], ((k >> 1) & 1) ^ 1, kSpinLimit)) {
+                    set_status(a.status, 3u);
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t a_base = tc::smem_u32(sA + (size_t)st * S::kStage), b_base = tc::smem_u32(sB);
+                const uint32_t d = tmem + (uint32_t)(acc * 32);
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    const int dy = t / 3, dx = t % 3;
+#pragma unroll
+                    for (int sk = 0; sk < CI / 16; ++sk) {
+                        const uint32_t aa = a_base + (uint32_t)(((dy * kcn + 2 * sk) * kSlabUnits + dx) * 16);
+                        const uint32_t bb = b_base + (uint32_t)(((t * kcn + 2 * sk) * CO) * 16);
+                        tc::mma_bf16(d, tc::sdesc(aa, kSlabUnits * 16, 128), tc::sdesc(bb, CO * 16, 128), idesc,
+                                     (t | sk) != 0);
+                    }
+                }
+                tc::mma_commit(&empty[st]);
+                tc::mma_commit(&tfull[acc]);
+            }
+            // drain: the last committed MMAs finish before the accumulators are freed
+            if (k > 0) tc::mbar_wait_bounded(&tfull[(k - 1) & 1], ((k - 1) >> 1) & 1, kSpinLimit);
+        }
+    } else {                                                   // epilogue warps 2..5
+        const int quarter = warp & 3;
+        int k = 0;
+        for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+            const int acc = k & 1;
+            if (!tc::mbar_wait_bounded(&tfull[acc], (k >> 1) & 1, kSpinLimit)) {
+                if (lane == 0) set_status(a.status, 3u);
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 32);
+            uint32_t r[32];
+            {
+                uint32_t q[16];
+                tc::tmem_ld16(trow, q);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) r[c] = q[c];
+                if (CO == 32) {
+                    tc::tmem_ld16(trow + 16, q);
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) r[16 + c] = q[c];
+                }
+            }
+            tc::tmem_wait_ld();
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[acc]);
+            const int xs = (int)(tile % segs);
+            const long long ry = tile / segs;
+            const int y = (int)(ry % a.H), n = (int)(ry / a.H);
+            const int x = xs * kTileM + quarter * 32 + lane;
+            if (x < a.W) conv_epilogue<CO, MODE>(a, ((size_t)n * a.H + y) * a.W + x, r);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
 // ------------------------------------------------------------------ weight gradient
@@ -399,7 +556,7 @@ namespace {
 
 // Blocks of a persistent grid: resident blocks per SM (from the kernel's registers and
 // shared memory and the SM's limits) times SMs, at most `work`.
-int resident_grid(const void *fn, size_t smem, long long work)
+int resident_grid(const void *fn, size_t smem, long long work, int threads = 128)
 {
     int dev = 0, sms = 1, smem_sm = 0, regs_sm = 65536, reserved = 0;
     cudaGetDevice(&dev);
@@ -413,9 +570,10 @@ int resident_grid(const void *fn, size_t smem, long long work)
         const size_t block_smem = smem + fa.sharedSizeBytes + (size_t)reserved;
         const int by_smem = block_smem ? (int)((size_t)smem_sm / block_smem) : 16;
         const int regs = fa.numRegs > 0 ? fa.numRegs : 64;
-        const int by_regs = regs_sm / (((regs * 32 + 255) / 256) * 256 * 4);     // 4 warps per block
+        const int warps = (threads + 31) / 32;
+        const int by_regs = regs_sm / (((regs * 32 + 255) / 256) * 256 * warps);
         per_sm = by_smem < by_regs ? by_smem : by_regs;
-        if (per_sm > 16) per_sm = 16;                                           // 2048 threads per SM
+        if (per_sm > 2048 / (warps * 32)) per_sm = 2048 / (warps * 32);         // 2048 threads per SM
         if (per_sm < 1) per_sm = 1;
     }
     long long g = (long long)per_sm * sms;
@@ -433,9 +591,66 @@ cudaError_t set_smem(F *fn, size_t bytes)
 
 }  // namespace
 
+// cuTensorMapEncodeTiled from the driver, fetched once through the runtime.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encode_tiled(EncodeTiledFn *out)
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    *out = fn;
+    return cudaSuccess;
+}
+
+// Tensor map of an NHWC bf16 activation with CI channels, as dims (CI, W, H, N), boxes of
+// 8 channels x 130 pixels x 1 row x 1 frame, zero fill outside.
+cudaError_t input_map(const void *base, int ci, int n, int h, int w, CUtensorMap *m)
+{
+    EncodeTiledFn fn = nullptr;
+    cudaError_t e = encode_tiled(&fn);
+    if (e != cudaSuccess) return e;
+    const cuuint64_t dims[4] = {(cuuint64_t)ci, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
+    const cuuint64_t strides[3] = {(cuuint64_t)ci * 2, (cuuint64_t)w * ci * 2, (cuuint64_t)h * w * ci * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)(kTileM + 2), 1, 1};
+    const cuuint32_t elem[4] = {1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, elem,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+#ifndef SGAD_NET_CONV_TMA
+#define SGAD_NET_CONV_TMA 1
+#endif
+
 template <int CI, int CO, int MODE>
 cudaError_t launch_conv(const ConvArgs &a, cudaStream_t st)
 {
+#if SGAD_NET_CONV_TMA
+    {
+        const size_t smem = TmaConvSmem<CI, CO>::bytes;
+        cudaError_t e = set_smem(k_conv3x3_tma<CI, CO, MODE>, smem);
+        if (e != cudaSuccess) return e;
+        const long long tiles = (long long)a.N * a.H * ((a.W + kTileM - 1) / kTileM);
+        if (tiles <= 0) return cudaSuccess;
+        CUtensorMap m;
+        e = input_map(a.in, CI, a.N, a.H, a.W, &m);
+        if (e != cudaSuccess) return e;
+        // TMEM: 64 columns per block, at most 8 blocks of 512 columns per SM
+        const int grid = resident_grid((const void *)k_conv3x3_tma<CI, CO, MODE>, smem, tiles, 192);
+        k_conv3x3_tma<CI, CO, MODE><<<grid, 192, smem, st>>>(m, a);
+        return cudaGetLastError();
+    }
+#endif
     const size_t smem = ConvSmem<CI, CO>::bytes;
     cudaError_t e = set_smem(k_conv3x3<CI, CO, MODE>, smem);
     if (e != cudaSuccess) return e;

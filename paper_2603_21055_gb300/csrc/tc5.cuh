@@ -130,5 +130,31 @@ __device__ __forceinline__ void transpose_copy_x4(uint32_t src_row, uint32_t dst
                  : "memory");
 }
 
+// Arrive once on *bar (count 1 per call).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Arrive once on *bar and expect `bytes` more bytes of asynchronous copies to land on it.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA: copy one box of a rank-4 tiled tensor map at coordinates (c0 .. c3), innermost
+// first, into shared memory at dst (128-byte aligned); completion is counted in bytes on
+// *bar. Elements outside the tensor are filled with zeros.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
 }  // namespace tc
 }  // namespace sgad
