@@ -104,6 +104,7 @@ def lib():
             l.orc_render_pixels.argtypes = [P, C.c_int32, P, C.c_int32, P, C.c_int64, P, P, P, P, P, P,
                                             P, P, P]
             l.orc_backward.argtypes = [P, C.c_int32, P, C.c_int32, P, P, P, P, P]
+            l.orc_backward_pose.argtypes = [P, C.c_int32, P, C.c_int32, P, P, P, P]
             l.orc_backward_gaussians.argtypes = [P, C.c_int32, P, C.c_int32, P, P, C.c_int64, P, P, P, P]
             l.orc_decision_hash.restype = C.c_uint64
             l.orc_decision_hash.argtypes = [P, C.c_int32, P, C.c_int32, P]
@@ -249,6 +250,21 @@ def backward(scene, grads_in, o: Opts = None):
         base += n
     del keep
     return outs
+
+
+def backward_pose(scene, grads_in, o: Opts = None):
+    """Adjoint into the view poses: (d_pose, abs) as (n_views, 3, 4) arrays, d loss / d of
+    each view's world->cam 3x4 matrix and the sum of the magnitudes of the per-pixel
+    contributions."""
+    o = o or opts()
+    inp = _Inputs(scene)
+    gi, keep = _image_grads(scene, grads_in)
+    nv = len(scene.views)
+    d = np.zeros((nv, 12))
+    a = np.zeros((nv, 12))
+    lib().orc_backward_pose(inp.kfs, inp.n_kf, inp.views, inp.n_views, C.byref(o), gi, _ptr(d), _ptr(a))
+    del keep
+    return d.reshape(nv, 3, 4), a.reshape(nv, 3, 4)
 
 
 def backward_gaussians(scene, grads_in, sel, o: Opts = None):

@@ -542,7 +542,7 @@ static void pixel_adjoint(const orc_proj *proj, const walk_rec *rec, int32_t nre
  * conic -> Sigma_2D -> (s, J) -> t (with the mean and the depth) -> mu -> |D + delta|
  * -> delta; o -> logit. out = (d_offset, d_r, d_g, d_b, d_logit, d_scale). */
 static void chain_params(const orc_kf *kf, int64_t j, const orc_cam *view, const orc_proj *P,
-                         const double g[G_N], double out[6])
+                         const double g[G_N], double out[6], double gt_out[3])
 {
     const double fx = view->fx, fy = view->fy;
     const double tx = P->t[0], ty = P->t[1], tz = P->t[2];
@@ -568,6 +568,11 @@ static void chain_params(const orc_kf *kf, int64_t j, const orc_cam *view, const
     const double gtz = gJ00 * (-fx / (tz * tz)) + gJ02 * (2.0 * fx * tx / (tz * tz * tz))
                      + gJ11 * (-fy / (tz * tz)) + gJ12 * (2.0 * fy * ty / (tz * tz * tz))
                      + g[G_PX] * (-fx * tx / (tz * tz)) + g[G_PY] * (-fy * ty / (tz * tz)) + g[G_Z];
+    if (gt_out) {                 /* d loss / d t, the view-space centre */
+        gt_out[0] = gtx;
+        gt_out[1] = gty;
+        gt_out[2] = gtz;
+    }
     /* t = R_k mu + t_k */
     const double *V = view->pose;
     double gmu[3];
@@ -595,7 +600,7 @@ static void chain_params(const orc_kf *kf, int64_t j, const orc_cam *view, const
 static void view_adjoint_tiles(const orc_kf *kfs, int32_t n_kf, const orc_proj *proj, const tile_lists *L,
                                const orc_cam *view, const orc_opts *opt, const orc_image_grads *gi,
                                const int32_t *tiles, int32_t n_tiles, const int64_t *slot, double (*g2d)[G_N],
-                               double (*gabs)[6], uint8_t *near_out)
+                               double (*gabs)[6], uint8_t *near_out, double *pose_abs)
 {
     const int32_t W = view->width, H = view->height;
     const int64_t hw = (int64_t)W * H;
@@ -605,6 +610,7 @@ static void view_adjoint_tiles(const orc_kf *kfs, int32_t n_kf, const orc_proj *
         double (**acc)[G_N] = (double (**)[G_N])calloc((size_t)(c1 - c0), sizeof(*acc));
         double (**aacc)[6] = (double (**)[6])calloc((size_t)(c1 - c0), sizeof(*aacc));
         uint8_t **nacc = (uint8_t **)calloc((size_t)(c1 - c0), sizeof(*nacc));
+        double (*pacc)[12] = pose_abs ? (double (*)[12])calloc((size_t)(c1 - c0), sizeof(*pacc)) : NULL;
 #pragma omp parallel for schedule(dynamic, 1)
         for (int32_t ci = c0; ci < c1; ++ci) {
             const int32_t t = tiles[ci];
@@ -612,6 +618,7 @@ static void view_adjoint_tiles(const orc_kf *kfs, int32_t n_kf, const orc_proj *
             const list_entry *list = L->e + L->off[t];
             double (*a)[G_N] = (double (*)[G_N])calloc((size_t)(n + 1), sizeof(*a));
             double (*ab)[6] = gabs ? (double (*)[6])calloc((size_t)(n + 1), sizeof(*ab)) : NULL;
+            double *pab = pacc ? pacc[ci - c0] : NULL;
             uint8_t *nf = (uint8_t *)calloc((size_t)(n + 1), 1);
             double (*pa)[G_N] = (double (*)[G_N])calloc((size_t)(n + 1), sizeof(*pa));
             walk_rec *rec = (walk_rec *)malloc(sizeof(walk_rec) * (size_t)(n + 1));
@@ -626,14 +633,24 @@ static void view_adjoint_tiles(const orc_kf *kfs, int32_t n_kf, const orc_proj *
                     pixel_adjoint(proj, rec, o.n_rec, o.T, gC, gi->d_depth[pix], gi->d_alpha[pix], opt, pa);
                     for (int32_t r = 0; r < o.n_rec; ++r)
                         for (int q = 0; q < G_N; ++q) a[rec[r].pos][q] += pa[r][q];
-                    if (ab) {
-                        /* magnitude of this pixel's contribution to each parameter gradient */
+                    if (ab || pab) {
+                        /* magnitude of this pixel's contribution to each parameter gradient
+                         * and to the view pose gradient */
                         for (int32_t r = 0; r < o.n_rec; ++r) {
                             int64_t j;
                             const int32_t ki = owner(kfs, n_kf, rec[r].g, &j);
                             double o6[6];
-                            chain_params(&kfs[ki], j, view, &proj[rec[r].g], pa[r], o6);
-                            for (int q = 0; q < 6; ++q) ab[rec[r].pos][q] += fabs(o6[q]);
+                            double gt[3];
+                            chain_params(&kfs[ki], j, view, &proj[rec[r].g], pa[r], o6, gt);
+                            if (ab)
+                                for (int q = 0; q < 6; ++q) ab[rec[r].pos][q] += fabs(o6[q]);
+                            if (pab) {
+                                const double *mu = proj[rec[r].g].mu;
+                                for (int c = 0; c < 3; ++c) {
+                                    for (int b = 0; b < 3; ++b) pab[4 * c + b] += fabs(gt[c] * mu[b]);
+                                    pab[4 * c + 3] += fabs(gt[c]);
+                                }
+                            }
                         }
                     }
                     if (o.near) {
@@ -669,7 +686,10 @@ static void view_adjoint_tiles(const orc_kf *kfs, int32_t n_kf, const orc_proj *
             free(acc[ci - c0]);
             free(aacc[ci - c0]);
             free(nacc[ci - c0]);
+            if (pacc)
+                for (int q = 0; q < 12; ++q) pose_abs[q] += pacc[ci - c0][q];
         }
+        free(pacc);
         free(acc);
         free(aacc);
         free(nacc);
@@ -695,13 +715,14 @@ int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int3
         int32_t *tiles = (int32_t *)malloc(sizeof(int32_t) * (size_t)nt);
         for (int32_t t = 0; t < nt; ++t) tiles[t] = t;
         memset(g2d, 0, sizeof(*g2d) * (size_t)nG);
-        view_adjoint_tiles(kfs, n_kf, proj, &L, &views[k], opt, &grad_in[k], tiles, nt, NULL, g2d, gabs, near_gauss);
+        view_adjoint_tiles(kfs, n_kf, proj, &L, &views[k], opt, &grad_in[k], tiles, nt, NULL, g2d, gabs, near_gauss,
+                           NULL);
         for (int64_t g = 0; g < nG; ++g) {
             if (!(proj[g].ntiles > 0)) continue;
             int64_t j;
             const int32_t i = owner(kfs, n_kf, g, &j);
             double o6[6];
-            chain_params(&kfs[i], j, &views[k], &proj[g], g2d[g], o6);
+            chain_params(&kfs[i], j, &views[k], &proj[g], g2d[g], o6, NULL);
             for (int q = 0; q < 6; ++q) gp[g][q] += o6[q];
         }
         free(tiles);
@@ -724,6 +745,45 @@ int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int3
         base += n;
     }
     free(gp);
+    free(g2d);
+    free(proj);
+    return 0;
+}
+
+int32_t orc_backward_pose(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int32_t n_views,
+                          const orc_opts *opt, const orc_image_grads *grad_in, double *d_pose, double *abs_pose)
+{
+    const int64_t nG = orc_num_gaussians(kfs, n_kf);
+    orc_proj *proj = (orc_proj *)malloc(sizeof(orc_proj) * (size_t)nG);
+    double (*g2d)[G_N] = (double (*)[G_N])malloc(sizeof(*g2d) * (size_t)nG);
+    for (int32_t k = 0; k < n_views; ++k) {
+        double *dp = d_pose + 12 * (size_t)k;
+        double *ap = abs_pose ? abs_pose + 12 * (size_t)k : NULL;
+        memset(dp, 0, 12 * sizeof(double));
+        if (ap) memset(ap, 0, 12 * sizeof(double));
+        orc_project(kfs, n_kf, &views[k], opt, proj);
+        tile_lists L;
+        build_lists(proj, nG, &views[k], opt, &L);
+        const int32_t nt = L.ntx * L.nty;
+        int32_t *tiles = (int32_t *)malloc(sizeof(int32_t) * (size_t)nt);
+        for (int32_t t = 0; t < nt; ++t) tiles[t] = t;
+        memset(g2d, 0, sizeof(*g2d) * (size_t)nG);
+        view_adjoint_tiles(kfs, n_kf, proj, &L, &views[k], opt, &grad_in[k], tiles, nt, NULL, g2d, NULL, NULL, ap);
+        for (int64_t g = 0; g < nG; ++g) {
+            if (!(proj[g].ntiles > 0)) continue;
+            int64_t j;
+            const int32_t i = owner(kfs, n_kf, g, &j);
+            double o6[6], gt[3];
+            chain_params(&kfs[i], j, &views[k], &proj[g], g2d[g], o6, gt);
+            /* t = R mu + t_k: d t_a / d R_ab = mu_b, d t_a / d t_k,a = 1 */
+            for (int a = 0; a < 3; ++a) {
+                for (int b = 0; b < 3; ++b) dp[4 * a + b] += gt[a] * proj[g].mu[b];
+                dp[4 * a + 3] += gt[a];
+            }
+        }
+        free(tiles);
+        free_lists(&L);
+    }
     free(g2d);
     free(proj);
     return 0;
@@ -761,7 +821,7 @@ int32_t orc_backward_gaussians(const orc_kf *kfs, int32_t n_kf, const orc_cam *v
             if (want[t]) tiles[nw++] = t;
         memset(g2d, 0, sizeof(*g2d) * (size_t)(n_sel + 1));
         view_adjoint_tiles(kfs, n_kf, proj, &L, &views[k], opt, &grad_in[k], tiles, nw, slot, g2d,
-                           (double (*)[6])abs_sel, near_sel);
+                           (double (*)[6])abs_sel, near_sel, NULL);
         for (int64_t s = 0; s < n_sel; ++s) {
             const int64_t g = sel[s];
             if (!(proj[g].ntiles > 0)) continue;
@@ -769,7 +829,7 @@ int32_t orc_backward_gaussians(const orc_kf *kfs, int32_t n_kf, const orc_cam *v
             const int32_t i = owner(kfs, n_kf, g, &j);
             if (!kfs[i].learnable) continue;
             double o6[6];
-            chain_params(&kfs[i], j, &views[k], &proj[g], g2d[s], o6);
+            chain_params(&kfs[i], j, &views[k], &proj[g], g2d[s], o6, NULL);
             for (int q = 0; q < 6; ++q) out[6 * s + q] += o6[q];
         }
         free(tiles);

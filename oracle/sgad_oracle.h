@@ -159,6 +159,19 @@ int32_t orc_backward(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int3
                      const orc_opts *opt, const orc_image_grads *grad_in, orc_kf_grads *grads,
                      uint8_t *near_gauss, double *abs_out);
 
+/* Adjoint into the view poses: d_pose[k][12] = d loss / d W_k for the row-major 3x4
+ * world->cam matrix W_k = [R_k | t_k] of view k. Through t = R_k mu + t_k only (the 2D
+ * covariance s^2 J J^T + 0.3 I does not involve R_k for an isotropic Gaussian):
+ * d L / d R_k[a][b] = sum_g d L / d t_g[a] mu_g[b], d L / d t_k[a] = sum_g d L / d t_g[a].
+ * abs_pose (optional, [n_views][12]): the sum over pixels and Gaussians of the magnitude
+ * of each pixel's contribution (the scale of the sum's rounding error). This is the
+ * gradient the rendering-based camera initialisation of tracking (Sec. 3.3,
+ * "Initialization": minimise the rendering error of the new frame against the previous
+ * frame's Gaussians) descends. */
+int32_t orc_backward_pose(const orc_kf *kfs, int32_t n_kf, const orc_cam *views, int32_t n_views,
+                          const orc_opts *opt, const orc_image_grads *grad_in, double *d_pose,
+                          double *abs_pose);
+
 /* Adjoint restricted to a list of Gaussians (global indices): out[n][6] =
  * (d_offset, d_r, d_g, d_b, d_logit, d_scale). Only the tiles these Gaussians touch are
  * walked, so it runs on full-size scenes. near_sel (optional, n bytes) and abs_sel

@@ -470,3 +470,45 @@ def test_adam_two_steps_closed_form():
     v2 = 0.999 * 0.001 * g1 ** 2 + 0.001 * g2 ** 2
     step = lr * (m2 / (1 - 0.81)) / (np.sqrt(v2 / (1 - 0.999 ** 2)) + eps)
     np.testing.assert_allclose(p, np.array([0.99, -1.99, 0.5]) - step, rtol=1e-14)
+
+
+def test_pose_adjoint_matches_central_differences():
+    """d L / d W for the 12 entries of the view's world->cam matrix, L = <g, render>, on
+    the 200-Gaussian subscene: the oracle's adjoint against FP64 central differences of
+    its own forward (h = 1e-6), above the FD rounding floor. The translation column moves
+    every Gaussian, so a perturbation that changes a discrete decision is set aside; most
+    entries must be checked. The reported magnitudes bound the gradient (triangle
+    inequality)."""
+    from paper_2603_21055_gb300.synth import fd_subscene
+    sc = _as64(fd_subscene())
+    v0 = sc.views[0]
+    view = Camera(v0.width, v0.height, v0.fx, v0.fy, v0.cx, v0.cy, np.asarray(v0.pose, np.float64).copy())
+    sc = Scene(sc.keyframes, [view], sc.target_rgb, sc.target_depth, sc.depth_weight)
+    rng = np.random.default_rng(8)
+    g = [dict(rgb=rng.normal(size=(3, view.height, view.width)), depth=rng.normal(size=(view.height, view.width)),
+              alpha=rng.normal(size=(view.height, view.width)))]
+    ana, absum = oracle.backward_pose(sc, g)
+    assert np.all(absum[0] >= np.abs(ana[0]) * (1 - 1e-12))
+    outs = oracle.render(sc)
+    l_abs = sum(float(np.abs(gi[q] * o[q]).sum()) for gi, o in zip(g, outs) for q in ("rgb", "depth", "alpha"))
+    h0 = oracle.decision_hash(sc)
+    checked, worst = 0, 0.0
+    for a in range(3):
+        for b in range(4):
+            x0 = view.pose[a, b]
+            for h in (1e-6, 1e-7, 1e-8):      # a smaller step where a decision flips
+                view.pose[a, b] = x0 + h
+                lp, hp = _loss(sc, g), oracle.decision_hash(sc)
+                view.pose[a, b] = x0 - h
+                lm, hm = _loss(sc, g), oracle.decision_hash(sc)
+                view.pose[a, b] = x0
+                if hp == h0 and hm == h0:
+                    break
+            else:
+                continue
+            fd = (lp - lm) / (2 * h)
+            noise = np.finfo(np.float64).eps * l_abs / h * 10.0
+            worst = max(worst, abs(ana[0, a, b] - fd) / (1e-6 * abs(fd) + noise))
+            checked += 1
+    assert checked >= 10, checked
+    assert worst <= 1.0, worst
