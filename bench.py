@@ -177,7 +177,7 @@ def run_ours(args):
         mp.step_eager()
     torch.cuda.synchronize()
     # the library's autotuner picks tile shape, batches, schedules and backward algorithm
-    tune_rows = mp.autotune(reps=3)
+    tune_rows = mp.autotune(reps=5)
     print("[autotune] " + json.dumps(sorted(([r["tile"][0], r["tile"][1], r["stage"], r["batch"], r["schedule"],
                                               round(r["ms"], 3)] for r in tune_rows), key=lambda x: (x[2], x[5]))),
           file=sys.stderr, flush=True)

@@ -93,11 +93,18 @@ typedef struct {
     float *alpha;                /* [H][W] A = sum_i w_i */
 } sgad_images;
 
-/* d loss / d (rgb, depth, alpha) of one view (device). A NULL plane means zero. */
+/* d loss / d (rgb, depth, alpha) of one view (device). A NULL plane means zero.
+ * d_pose (device, 12 floats, optional): when not NULL, sgad_backward writes
+ * d loss / d W of this view's world->cam matrix W = [R | t] (row-major 3x4, the layout of
+ * sgad_camera.pose), through t = R mu + t of every Gaussian's view-space centre (the 2D
+ * covariance of an isotropic Gaussian does not involve R). This is the gradient the
+ * rendering-based camera initialisation of tracking descends (Sec. 3.3,
+ * "Initialization"). */
 typedef struct {
     const float *d_rgb;
     const float *d_depth;
     const float *d_alpha;
+    float *d_pose;
 } sgad_image_grads;
 
 /* Gradients of one keyframe's parameters (device, caller-owned). For learnable

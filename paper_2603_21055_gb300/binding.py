@@ -55,7 +55,7 @@ class sgad_images(C.Structure):
 
 
 class sgad_image_grads(C.Structure):
-    _fields_ = [("d_rgb", C.c_void_p), ("d_depth", C.c_void_p), ("d_alpha", C.c_void_p)]
+    _fields_ = [("d_rgb", C.c_void_p), ("d_depth", C.c_void_p), ("d_alpha", C.c_void_p), ("d_pose", C.c_void_p)]
 
 
 class sgad_keyframe_grads(C.Structure):

@@ -55,6 +55,8 @@ cudaError_t launch_composite(bool fwd, int batch, int schedule, const Scene &sc,
     if (sc.n_tiles <= 0) return cudaSuccess;
     CompositeArgs a = {};
     a.contrib = contrib;
+    for (int i = 0; i < sc.n_views && !fwd; ++i)
+        if (sc.view[i].d_pose) a.pose = 1;
     a.world = world;
     a.off = off;
     a.entries = entries;

@@ -65,6 +65,7 @@ struct CompositeArgs {
     // pixel), word contrib[8 off[t] + 256 t + 256 c + i] has bit j set iff entry 32c + j
     // contributed to that pixel. Written for every chunk the pixel's warp walked.
     uint32_t *contrib;
+    int32_t pose;                 // some view wants its pose gradient (selects the kernel variant)
 };
 
 __device__ __forceinline__ size_t contrib_base(const CompositeArgs &a, int tile, uint32_t s)
@@ -283,8 +284,8 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
 // Chain rule of one staged Gaussian from its ten accumulated pair moments (colour (3),
 // depth, G, G dx, G dy, G dx^2, G dx dy, G dy^2 with G = dL/dpower) down to d mu, d s,
 // d opacity and d colour, added to its accumulator.
-__device__ __forceinline__ void chain_and_accumulate(const float *A, const Staged &st, const Proj &pr, float s_,
-                                                     const ViewDev &v, float4 *gacc, uint32_t g)
+__device__ __forceinline__ float3 chain_and_accumulate(const float *A, const Staged &st, const Proj &pr, float s_,
+                                                       const ViewDev &v, float4 *gacc, uint32_t g)
 {
     const float ca = st.b.x, cbb = st.b.y, cc = st.b.z, o = st.b.w;
     const float G = A[4], Gx = A[5], Gy = A[6], Gxx = A[7], Gxy = A[8], Gyy = A[9];
@@ -318,6 +319,23 @@ __device__ __forceinline__ void chain_and_accumulate(const float *A, const Stage
                                   v.R[2] * gtx + v.R[5] * gty + v.R[8] * gtz, ds);
     atomicAdd(&gacc[2 * (size_t)g], ga);
     atomicAdd(&gacc[2 * (size_t)g + 1], make_float4(d_o, A[0], A[1], A[2]));
+    return make_float3(gtx, gty, gtz);
+}
+
+// View-pose terms of one Gaussian per lane (zero for lanes without one): t = R mu + t_k,
+// so d L / d R[a][b] += dL/dt[a] mu[b] and d L / d t_k[a] += dL/dt[a] (row-major 3x4);
+// summed over the warp and added to the block's shared accumulator. Whole warp.
+__device__ __forceinline__ void pose_reduce(const float3 gt, const float4 mu, float *s_pose)
+{
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        const float g = (q >> 2) == 0 ? gt.x : ((q >> 2) == 1 ? gt.y : gt.z);
+        const int c = q & 3;
+        float x = c == 3 ? g : g * (c == 0 ? mu.x : (c == 1 ? mu.y : mu.z));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if ((threadIdx.x & 31) == 0 && x != 0.f) atomicAdd(&s_pose[q], x);
+    }
 }
 
 // Shared memory of the backward pass for a batch of B entries: the staged records, their
@@ -329,9 +347,9 @@ constexpr size_t bwd_smem_bytes()
     return (size_t)B * (sizeof(Staged) + sizeof(uint32_t) + 11 * sizeof(float));
 }
 
-template <int TW, int TH, int B>
+template <int TW, int TH, int B, bool POSE>
 __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a, int tile, Staged *sm, uint32_t *sg,
-                                         float (*acc)[11], int *s_nmax)
+                                         float (*acc)[11], int *s_nmax, float *s_pose)
 {
     static_assert(TW * TH == 2 * kBwdThreads, "tile must hold 256 pixels");
     const ViewDev &v = sc.view[find_view_of_tile(sc, tile)];
@@ -372,6 +390,7 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
     }
     const int warp_nc = __reduce_max_sync(kFull, (unsigned)max(nc[0], nc[1]));
     __syncthreads();     // the previous tile's readers of *s_nmax are done
+    if (POSE && threadIdx.x < 12) s_pose[threadIdx.x] = 0.f;
     if (threadIdx.x == 0) *s_nmax = 0;
     __syncthreads();
     if (lane == 0) atomicMax(s_nmax, warp_nc);
@@ -458,19 +477,28 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
 #pragma unroll
         for (int r = 0; r < (B + kBwdThreads - 1) / kBwdThreads; ++r) {
             const int k = r * kBwdThreads + threadIdx.x;
-            if (k >= nb || sg[k] >= sc.n_gauss) continue;
-            const float *A = acc[k];
-            bool any = false;
+            float3 gt = make_float3(0.f, 0.f, 0.f);
+            float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < nb && sg[k] < sc.n_gauss) {
+                const float *A = acc[k];
+                bool any = false;
 #pragma unroll
-            for (int q = 0; q < 10; ++q) any |= A[q] != 0.f;
-            if (!any) continue;
-            const float4 w0 = a.world[sg[k]].w0;
-            chain_and_accumulate(A, sm[k], project(w0, v), w0.w, v, a.gacc, sg[k]);
+                for (int q = 0; q < 10; ++q) any |= A[q] != 0.f;
+                if (any) {
+                    w0 = a.world[sg[k]].w0;
+                    gt = chain_and_accumulate(A, sm[k], project(w0, v), w0.w, v, a.gacc, sg[k]);
+                }
+            }
+            if (POSE && v.d_pose) pose_reduce(gt, w0, s_pose);
         }
+    }
+    if (POSE && v.d_pose) {
+        __syncthreads();
+        if (threadIdx.x < 12 && s_pose[threadIdx.x] != 0.f) atomicAdd(&v.d_pose[threadIdx.x], s_pose[threadIdx.x]);
     }
 }
 
-template <int TW, int TH, int B>
+template <int TW, int TH, int B, bool POSE>
 __global__ void __launch_bounds__(kBwdThreads, SGAD_BWD_MINBLOCKS)
     k_composite_bwd(const __grid_constant__ Scene sc, const CompositeArgs a)
 {
@@ -479,12 +507,13 @@ __global__ void __launch_bounds__(kBwdThreads, SGAD_BWD_MINBLOCKS)
     uint32_t *sg = reinterpret_cast<uint32_t *>(sm + B);
     float(*acc)[11] = reinterpret_cast<float(*)[11]>(sg + B);
     __shared__ int s_tile, s_nmax;
+    __shared__ float s_pose[12];
     if (a.hdr->overflow) return;
     bool first = true;
     for (;;) {
         const int tile = next_tile(sc, a, first, &s_tile);
         if (tile < 0) break;
-        bwd_tile<TW, TH, B>(sc, a, tile, sm, sg, acc, &s_nmax);
+        bwd_tile<TW, TH, B, POSE>(sc, a, tile, sm, sg, acc, &s_nmax, s_pose);
     }
 }
 
@@ -502,9 +531,9 @@ __global__ void __launch_bounds__(kBwdThreads, SGAD_BWD_MINBLOCKS)
 constexpr int kPairThreads = 256;
 constexpr int kPairBatch = 256;
 
-template <int TW, int TH>
+template <int TW, int TH, bool POSE>
 __device__ __forceinline__ void bwdp_tile(const Scene &sc, const CompositeArgs &a, int tile, Staged *sm, uint32_t *sg,
-                                          float (*acc)[11], int *s_nmax)
+                                          float (*acc)[11], int *s_nmax, float *s_pose)
 {
     static_assert(TW * TH == kPairThreads, "tile must hold 256 pixels");
     const ViewDev &v = sc.view[find_view_of_tile(sc, tile)];
@@ -534,6 +563,7 @@ __device__ __forceinline__ void bwdp_tile(const Scene &sc, const CompositeArgs &
         if (v.g_alpha) gA = v.g_alpha[q];
     }
     __syncthreads();     // the previous tile's readers of *s_nmax are done
+    if (POSE && threadIdx.x < 12) s_pose[threadIdx.x] = 0.f;
     if (threadIdx.x == 0) *s_nmax = 0;
     __syncthreads();
     const int warp_nc = __reduce_max_sync(kFull, (unsigned)nc);
@@ -611,33 +641,41 @@ __device__ __forceinline__ void bwdp_tile(const Scene &sc, const CompositeArgs &
         __syncthreads();
         {
             const int k = threadIdx.x;
+            float3 gt = make_float3(0.f, 0.f, 0.f);
+            float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (k < nb && sg[k] < sc.n_gauss) {
                 const float *A = acc[k];
                 bool any = false;
 #pragma unroll
                 for (int q = 0; q < 10; ++q) any |= A[q] != 0.f;
                 if (any) {
-                    const float4 w0 = a.world[sg[k]].w0;
-                    chain_and_accumulate(A, sm[k], project(w0, v), w0.w, v, a.gacc, sg[k]);
+                    w0 = a.world[sg[k]].w0;
+                    gt = chain_and_accumulate(A, sm[k], project(w0, v), w0.w, v, a.gacc, sg[k]);
                 }
             }
+            if (POSE && v.d_pose) pose_reduce(gt, w0, s_pose);
         }
+    }
+    if (POSE && v.d_pose) {
+        __syncthreads();
+        if (threadIdx.x < 12 && s_pose[threadIdx.x] != 0.f) atomicAdd(&v.d_pose[threadIdx.x], s_pose[threadIdx.x]);
     }
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool POSE>
 __global__ void __launch_bounds__(kPairThreads, 4) k_composite_bwdp(const __grid_constant__ Scene sc, const CompositeArgs a)
 {
     __shared__ Staged sm[kPairBatch];
     __shared__ uint32_t sg[kPairBatch];
     __shared__ float acc[kPairBatch][11];
     __shared__ int s_tile, s_nmax;
+    __shared__ float s_pose[12];
     if (a.hdr->overflow) return;
     bool first = true;
     for (;;) {
         const int tile = next_tile(sc, a, first, &s_tile);
         if (tile < 0) break;
-        bwdp_tile<TW, TH>(sc, a, tile, sm, sg, acc, &s_nmax);
+        bwdp_tile<TW, TH, POSE>(sc, a, tile, sm, sg, acc, &s_nmax, s_pose);
     }
 }
 
@@ -675,11 +713,18 @@ cudaError_t launch_composite_tb(bool fwd, const Scene &sc, const CompositeArgs &
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         if (dev < 0 || dev >= 64 || !configured[dev]) {
-            e = cudaFuncSetAttribute(k_composite_bwd<TW, TH, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaFuncSetAttribute(k_composite_bwd<TW, TH, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_composite_bwd<TW, TH, B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
             if (e != cudaSuccess) return e;
             if (dev >= 0 && dev < 64) configured[dev] = 1;
         }
-        k_composite_bwd<TW, TH, B><<<grid_blocks, kBwdThreads, smem, st>>>(sc, a);
+        if (a.pose)
+            k_composite_bwd<TW, TH, B, true><<<grid_blocks, kBwdThreads, smem, st>>>(sc, a);
+        else
+            k_composite_bwd<TW, TH, B, false><<<grid_blocks, kBwdThreads, smem, st>>>(sc, a);
     } else {
         return cudaErrorInvalidValue;     // the backward is built for batches up to 512
     }
@@ -699,8 +744,8 @@ cudaError_t occupancy_tb(bool fwd, int *blocks_per_sm)
                                                              smem);
     }
     if constexpr (B <= 512)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_composite_bwd<TW, TH, B>, kBwdThreads,
-                                                             bwd_smem_bytes<B>());
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_composite_bwd<TW, TH, B, false>,
+                                                             kBwdThreads, bwd_smem_bytes<B>());
     return cudaErrorInvalidValue;
 }
 
@@ -708,9 +753,12 @@ template <int TW, int TH>
 cudaError_t launch_bwdp(const Scene &sc, const CompositeArgs &a, int grid_blocks, int *occupancy, cudaStream_t st)
 {
     if (occupancy)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_composite_bwdp<TW, TH>, kPairThreads, 0);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_composite_bwdp<TW, TH, false>, kPairThreads, 0);
     if (grid_blocks <= 0) return cudaSuccess;
-    k_composite_bwdp<TW, TH><<<grid_blocks, kPairThreads, 0, st>>>(sc, a);
+    if (a.pose)
+        k_composite_bwdp<TW, TH, true><<<grid_blocks, kPairThreads, 0, st>>>(sc, a);
+    else
+        k_composite_bwdp<TW, TH, false><<<grid_blocks, kPairThreads, 0, st>>>(sc, a);
     return cudaGetLastError();
 }
 

@@ -273,6 +273,7 @@ sgad_status bind_grads(Scene &sc, const sgad_image_grads *grad_in, sgad_keyframe
         sc.view[i].g_rgb = grad_in[i].d_rgb;
         sc.view[i].g_depth = grad_in[i].d_depth;
         sc.view[i].g_alpha = grad_in[i].d_alpha;
+        sc.view[i].d_pose = grad_in[i].d_pose;
     }
     for (int i = 0; i < n_kf; ++i) {
         KfDev &d = sc.kf[i];
@@ -528,6 +529,8 @@ sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     mark(ctx, 5, st);
     cudaError_t e = cudaMemsetAsync(ws.gacc(), 0, (size_t)sc.n_gauss * 32, st);
+    for (int i = 0; i < n_views && e == cudaSuccess; ++i)
+        if (sc.view[i].d_pose) e = cudaMemsetAsync(sc.view[i].d_pose, 0, 12 * sizeof(float), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     s = run_composite(ctx, false, bwd_batch_of(ctx->opt), ctx->opt.bwd_schedule, sc, ws, st);
     if (s) return s;

@@ -39,6 +39,7 @@ struct KfDev {
 struct ViewDev {
     float *rgb, *depth, *alpha;
     const float *g_rgb, *g_depth, *g_alpha;
+    float *d_pose;               // [12] d loss / d (world -> cam 3x4), or null
     float fx, fy, cx, cy;
     float R[9], t[3];            // world -> cam
     int32_t W, H;

@@ -131,6 +131,8 @@ class Splatter:
         key = ("views", tuple(id(v) for v in views))
         arr = self._cache.get(key)
         if arr is None:
+            if len(self._cache) > 256:
+                self._cache.clear()
             arr = (B.sgad_camera * len(views))()
             for i, v in enumerate(views):
                 arr[i] = _cam(v)
@@ -190,7 +192,8 @@ class Splatter:
     def _grads(grads_in, grads_out):
         gi = (B.sgad_image_grads * len(grads_in))()
         for i, g in enumerate(grads_in):
-            gi[i] = B.sgad_image_grads(_ptr(g.get("rgb")), _ptr(g.get("depth")), _ptr(g.get("alpha")))
+            gi[i] = B.sgad_image_grads(_ptr(g.get("rgb")), _ptr(g.get("depth")), _ptr(g.get("alpha")),
+                                       _ptr(g.get("pose")))
         go = (B.sgad_keyframe_grads * len(grads_out))()
         for i, g in enumerate(grads_out):
             if g is not None:
@@ -204,7 +207,8 @@ class Splatter:
                        self.stream())
 
     def backward(self, kfs, views, grads_in, grads_out) -> None:
-        """grads_in: per view dict of d_rgb / d_depth / d_alpha tensors (missing = 0);
+        """grads_in: per view dict of d_rgb / d_depth / d_alpha tensors (missing = 0) and
+        optionally "pose", a 12-float tensor that receives d loss / d (world->cam 3x4);
         grads_out: per keyframe dict of d_offset / d_rgb / d_logit / d_scale tensors
         (None for fixed keyframes)."""
         ka, va = self.kf_structs(kfs), self.view_structs(views)

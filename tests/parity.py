@@ -11,10 +11,11 @@ GRAD_RTOL = 1e-3           # spec tolerance for gradients (relative)
 
 
 def gpu_run(scene, grads_in=None, tile=(16, 16), sort_smem_cap=0, freeze_offset=False, bg=(0.0, 0.0, 0.0),
-            **work_split):
+            pose=False, **work_split):
     """Forward (and backward when grads_in is given) through libsgad. Returns a dict of
-    numpy results plus the raw forward state. work_split: fwd_batch, bwd_batch,
-    fwd_schedule, bwd_schedule of the Splatter."""
+    numpy results plus the raw forward state. pose: also request each view's pose
+    gradient (res["pose"], (n_views, 3, 4)). work_split: fwd_batch, bwd_batch,
+    fwd_schedule, bwd_schedule, bwd_algorithm of the Splatter."""
     import torch
     from paper_2603_21055_gb300 import splat
     sp = splat.Splatter(tile=tile, sort_smem_cap=sort_smem_cap, freeze_offset=freeze_offset, bg=bg, **work_split)
@@ -32,6 +33,9 @@ def gpu_run(scene, grads_in=None, tile=(16, 16), sort_smem_cap=0, freeze_offset=
     if grads_in is not None:
         gin = [{k: torch.as_tensor(np.ascontiguousarray(v, np.float32)).cuda() for k, v in g.items()}
                for g in grads_in]
+        if pose:
+            for g in gin:
+                g["pose"] = torch.full((12,), float("nan"), device="cuda")
         gout = []
         for k in kfs:
             if k.learnable:
@@ -42,6 +46,8 @@ def gpu_run(scene, grads_in=None, tile=(16, 16), sort_smem_cap=0, freeze_offset=
         sp.backward(kfs, scene.views, gin, gout)
         torch.cuda.synchronize()
         res["grads"] = [None if g is None else {k: v.cpu().numpy() for k, v in g.items()} for g in gout]
+        if pose:
+            res["pose"] = np.stack([g["pose"].cpu().numpy().reshape(3, 4) for g in gin])
     return res
 
 
@@ -143,3 +149,12 @@ def compare_grads(res, ref_grads, rtol=GRAD_RTOL, abs_rtol=GRAD_ABS_RTOL, floor=
 def l1_grads(scene, renders):
     loss, g = oracle.l1_loss(scene, renders)
     return loss, [dict(rgb=x["rgb"].astype(np.float32), depth=x["depth"].astype(np.float32)) for x in g]
+
+
+def compare_pose(res, ref, absum, rtol=GRAD_RTOL, abs_rtol=GRAD_ABS_RTOL, floor=1e-6):
+    """View-pose gradients within rtol |ref| + abs_rtol A + floor max|ref| (A: the
+    oracle's sum of per-pixel contribution magnitudes). Returns the worst ratio."""
+    g = res["pose"].astype(np.float64)
+    assert np.all(np.isfinite(g))
+    ratio = np.abs(g - ref) / (rtol * np.abs(ref) + abs_rtol * absum + floor * np.abs(ref).max() + 1e-30)
+    return float(ratio.max())

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import (compare_grads, compare_images, compare_keys, gpu_run, l1_grads)
+from parity import (compare_grads, compare_images, compare_keys, compare_pose, gpu_run, l1_grads)
 
 pytestmark = pytest.mark.gpu
 
@@ -167,3 +167,16 @@ def test_invalid_arguments_return_status(scene1):
         B.SGAD_ERR_WORKSPACE_TOO_SMALL
     assert lib.sgad_forward(sp.ctx, ka, 1, va, 1, out, sp.ws_ptr, sp.ws_bytes, sp.key_capacity, None) == \
         B.SGAD_ERR_INVALID_ARG            # NULL output images
+
+
+@pytest.mark.parametrize("algo", ["warp_reduce", "pairs"])
+def test_view_pose_gradient(scene1, crop, algo):
+    """d loss / d (world->cam 3x4) of every view against the oracle's pose adjoint, on the
+    plane and on the two-view room crop, with both backward algorithms."""
+    for sc in (scene1, crop):
+        ref, g = _grads_for(sc)
+        res = gpu_run(sc, grads_in=g, pose=True, bwd_algorithm=algo)
+        dp, ab = oracle.backward_pose(sc, [{k: v.astype(np.float64) for k, v in x.items()} for x in g])
+        e = compare_pose(res, dp, ab)
+        print("%s %s pose grad ratio %.3f" % (sc.name, algo, e))
+        assert e <= 1.0
