@@ -54,12 +54,13 @@ def parse():
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--json-out", default="")
-    p.add_argument("--workload", choices=["room8", "batching", "mapping", "learned", "net"], default="room8",
+    p.add_argument("--workload", choices=["room8", "batching", "mapping", "learned", "net", "ssim"],
+                   default="room8",
                    help="room8: the headline line (default); batching: 32 uneven views, batched vs per-view "
                         "launches and the autotuner; mapping: 10 x 1200x680 keyframes, 100 Adam iterations; "
                         "learned: train the proposal net on plain-mapping targets and time mapping to 30 dB "
                         "with learned vs zero initialisation; net: forward and backward of the proposal net "
-                        "on 8 frames of 640x480")
+                        "on 8 frames of 640x480; ssim: the SSIM term's two passes on 8 x 640x480")
     p.add_argument("--train-rooms", type=int, default=50)
     p.add_argument("--eval-rooms", type=int, default=10)
     p.add_argument("--frames", type=int, default=40, help="frames per room (learned workload)")
@@ -246,6 +247,7 @@ def run_ours(args):
     e2e = run_e2e(mp, min(args.steps, 10), stream, flush)
 
     peaks, peak_src = measured_peaks()
+    ssim = ssim_term(mp.sp, mp.views, mp.images, mp.trgb, flush, peaks, peak_src)
     from paper_2603_21055_gb300 import binding as B
     pairs = mp.sp.options.bwd_algorithm == B.SGAD_BWD_PAIRS
     roof = roofline(stages, stats, scene, peaks, peak_src,
@@ -263,6 +265,7 @@ def run_ours(args):
                    "parallelism": "independent keyframe window per GPU" if world > 1 else "1 GPU"},
         "stage_ms": {k: round(v, 4) for k, v in stages.items()},
         "roofline": roof,
+        "ssim_term": ssim,
         "e2e": e2e,
         "gpu_launches": mp.launches_per_step() * args.steps,
         "clocks": clk,
@@ -375,6 +378,42 @@ def roofline(stages, stats, scene, peaks, src, bwd_kernel="k_composite_bwdp"):
     return {"kernel": kernel_of[name], "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2),
             "unit": unit, "frac": round(achieved / peak, 4), "peak_source": peak_note,
             "traffic": (tr["dram_bytes_per_launch"] if tr else None), "avg_ms": round(ms, 4)}
+
+
+# Algorithmic HBM bytes per pixel of the SSIM term's two passes (3 colour channels, FP32):
+# pass 1 reads V' and V (24 B) and writes the three d S / d m maps (36 B); pass 2 reads the
+# maps (36 B), V' and V (24 B) and reads and writes d V' (24 B).
+SSIM_BYTES_PER_PX = 144
+
+
+def ssim_term(sp, views, images, targets, flush, peaks, src, reps=20, warmup=3):
+    """The SSIM term of Eq. 1 (tau = 0.2) over `views`: both passes timed together with
+    CUDA events on the launching stream, L2 flushed before each repetition."""
+    import torch
+    stream = torch.cuda.current_stream()
+    d = [torch.zeros_like(t) for t in targets]
+    loss = torch.zeros(1, device="cuda")
+    for _ in range(warmup):
+        sp.ssim_loss_grad(views, images, targets, 0.2, d, loss)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        sp.ssim_loss_grad(views, images, targets, 0.2, d, loss)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)[reps // 2]
+    n_pix = sum(v.width * v.height for v in views)
+    byts = SSIM_BYTES_PER_PX * n_pix
+    gbs = byts / (ms / 1e3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    tr = ncu_traffic("k_ssim_maps"), ncu_traffic("k_ssim_grad")
+    traffic = (tr[0]["dram_bytes_per_launch"] + tr[1]["dram_bytes_per_launch"]) if all(tr) else None
+    return {"kernels": ["k_ssim_maps", "k_ssim_grad"], "median_ms": round(ms, 4), "bound": "hbm",
+            "achieved": round(gbs, 1), "peak": round(peak, 1), "unit": "GB/s", "frac": round(gbs / peak, 4),
+            "peak_source": "HBM copy bandwidth (%s)" % src, "algorithmic_bytes": byts, "traffic": traffic,
+            "loss_per_call": round(loss.item() / (reps + warmup), 6)}
 
 
 def cpu_baseline(scene):
@@ -584,7 +623,8 @@ def run_batching(args):
 def run_mapping(args):
     """Full mapping optimisation of 10 keyframes at 1200x680 (8,160,000 Gaussians) against
     10 views at the keyframe poses: 100 Adam iterations on offset, colour, opacity and
-    scale, each one CUDA graph replay (forward, L1 loss gradient, backward, Adam). Reports
+    scale, each one CUDA graph replay (forward, the Eq. 1 loss gradient with the
+    supplementary weights, backward, Adam). Reports
     iterations/s, peak device memory and the PSNR before and after."""
     import torch
     from paper_2603_21055_gb300 import synth
@@ -592,6 +632,8 @@ def run_mapping(args):
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
     scene = synth.config4_mapping(seed=4)
+    # the full Eq. 1 with the supplementary weights rho = 0.8, tau = 0.2, sigma = 1.0
+    scene.rgb_weight, scene.ssim_weight, scene.depth_weight = 0.8, 0.2, 1.0
     gen_s = time.perf_counter() - t0
     torch.cuda.reset_peak_memory_stats()
     mp = Mapper(scene)
@@ -625,12 +667,13 @@ def run_mapping(args):
     peak = torch.cuda.max_memory_allocated()
     free, total = torch.cuda.mem_get_info()
     line = {
-        "metric": "mapping iterations/s (forward + L1 grad + backward + Adam), 10 x 1200x680 keyframes",
+        "metric": "mapping iterations/s (forward + Eq. 1 loss grad + backward + Adam), 10 x 1200x680 keyframes",
         "value": round(iters / (ms / 1e3), 2), "unit": "iter/s", "n_gpus": 1, "steps": iters, "warmup": 3,
         "ms_per_step": round(ms / iters, 4), "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "room10x1200x680: 10 keyframes x 1200x680 (8,160,000 Gaussians) -> 10 views at "
                                "the keyframe poses, fx 600", "pixels_per_step": scene.n_pixels,
                    "iterations": iters, "step": "one CUDA graph replay per iteration, back to back (no flush)",
+                   "loss": "Eq. 1: 0.8 L1 colour + 0.2 SSIM + 1.0 L1 depth (valid pixels)",
                    "generation_s": round(gen_s, 1)},
         "wall_s_100_iterations": round(wall, 3),
         "mpix_per_s": round(scene.n_pixels * iters / (ms / 1e3) / 1e6, 2),
@@ -813,6 +856,33 @@ def run_net(args):
     _emit(line, args)
 
 
+def run_ssim(args):
+    """The SSIM term alone (both passes) on 8 views of 640x480: seeded images, no scene
+    generation; the small case the ncu captures of its kernels run on."""
+    import torch
+    from paper_2603_21055_gb300 import splat
+    from paper_2603_21055_gb300.synth import Camera
+    import numpy as np
+    torch.cuda.set_device(0)
+    n, h, w = 8, 480, 640
+    g = torch.Generator(device="cpu").manual_seed(args.seed)
+    views = [Camera(w, h, 600.0, 600.0, w / 2, h / 2, np.eye(4, dtype=np.float32)[:3].copy()) for _ in range(n)]
+    targets = [torch.rand(3, h, w, generator=g).cuda() for _ in range(n)]
+    images = [dict(rgb=(t + 0.1 * torch.randn(3, h, w, generator=g).cuda()).clamp(0, 1).contiguous(),
+                   depth=torch.zeros(h, w, device="cuda"), alpha=torch.zeros(h, w, device="cuda")) for t in targets]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    peaks, src = measured_peaks()
+    sp = splat.Splatter()
+    t = ssim_term(sp, views, images, targets, flush, peaks, src, reps=args.steps, warmup=args.warmup)
+    line = {"metric": "SSIM term (Eq. 1) loss + gradient, 8 x 640x480 views", "value": t["median_ms"], "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "ssim 8x640x480: uniform targets, renderings = target + "
+                                                        "N(0, 0.1) clamped", "l2": "flushed (256 MB write) before "
+                                                                                   "every step"},
+            "roofline": t, "gpu_launches": 2 * args.steps}
+    _emit(line, args)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -825,6 +895,8 @@ def main():
         run_learned(args)
     elif args.workload == "net":
         run_net(args)
+    elif args.workload == "ssim":
+        run_ssim(args)
     else:
         run_ours(args)
 

@@ -313,6 +313,31 @@ sgad_status sgad_l1_loss_grad(int32_t n_views, const sgad_camera *views,
                               float depth_weight, float *const *d_rgb, float *const *d_depth,
                               float *loss_accum, uint32_t *valid_count, void *stream);
 
+/* SSIM term of the mapping loss Eq. 1 (tau L_S, L_S the SSIM loss between the observed
+ * colour V_k and the rendering V'_k; Sec. 3.2). The paper cites the SSIM of Wang et
+ * al. 2004 without window details; this library reads it as: per colour channel, an
+ * 11 x 11 Gaussian window of standard deviation 1.5 (weights normalised to sum 1), zero
+ * padding outside the image, C1 = 0.01^2, C2 = 0.03^2, and
+ *   L_S = 1 - mean over pixels and channels of SSIM(V', V).
+ *
+ * sgad_ssim_workspace_size: bytes of device scratch sgad_ssim_loss_grad needs for these
+ * views (9 floats per pixel per view, each view's block 256-byte aligned).
+ *
+ * sgad_ssim_loss_grad: for every view k (device pointers, [3][H][W] FP32 planar, W and H
+ * from views[k]) adds weight * L_S(rendered[k].rgb, target_rgb[k]) to *loss_accum (one
+ * device float; may be NULL) and ADDS weight * d L_S / d V'_k into d_rgb[k], so it runs
+ * after sgad_l1_loss_grad, which overwrites d_rgb. Only rendered[k].rgb is read.
+ * workspace: caller-owned device memory of at least the size above, 256-byte aligned,
+ * overwritten. Two kernel launches on `stream`, no host synchronisation.
+ * Errors: SGAD_ERR_INVALID_ARG for a NULL pointer, a view count outside
+ * [1, SGAD_MAX_VIEWS], a view size outside [1, 16384], a misaligned workspace or a
+ * non-finite weight; SGAD_ERR_WORKSPACE_TOO_SMALL; SGAD_ERR_CUDA when a launch fails. */
+sgad_status sgad_ssim_workspace_size(int32_t n_views, const sgad_camera *views, size_t *bytes);
+sgad_status sgad_ssim_loss_grad(int32_t n_views, const sgad_camera *views,
+                                const sgad_images *rendered, const float *const *target_rgb,
+                                float weight, float *const *d_rgb, float *loss_accum,
+                                void *workspace, size_t ws_bytes, void *stream);
+
 /* One bias-corrected Adam step (PyTorch convention) on `n` FP32 parameters in place:
  *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
  *   p <- p - lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).

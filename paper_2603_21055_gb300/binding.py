@@ -26,6 +26,7 @@ EXPORTS = ["sgad_default_options", "sgad_create", "sgad_destroy", "sgad_last_err
            "sgad_count_keys", "sgad_forward", "sgad_backward", "sgad_check", "sgad_state", "sgad_read_stats",
            "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_adam_step",
            "sgad_adam_step_multi", "sgad_forward_noalloc", "sgad_autotune", "sgad_get_options",
+           "sgad_ssim_workspace_size", "sgad_ssim_loss_grad",
            # include/sgad_net.h
            "sgad_net_layer_shape", "sgad_net_workspace_size", "sgad_net_forward", "sgad_net_loss_grad",
            "sgad_net_backward", "sgad_net_check", "sgad_net_buffers_view"]
@@ -162,6 +163,8 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         "sgad_forward_noalloc": (st, [P, P, I32, P, I32, P, P]),
         "sgad_autotune": (st, [P, P, I32, P, I32, P, P, P, P, C.c_size_t, I32, P, I32, P, P]),
         "sgad_get_options": (st, [P, P]),
+        "sgad_ssim_workspace_size": (st, [I32, P, P]),
+        "sgad_ssim_loss_grad": (st, [I32, P, P, P, C.c_float, P, P, P, C.c_size_t, P]),
         "sgad_net_layer_shape": (st, [I32, P, P, P, P]),
         "sgad_net_workspace_size": (st, [I32, I32, I32, P]),
         "sgad_net_forward": (st, [P, I32, I32, I32, P, P, P, P, P, C.c_size_t, P]),
@@ -265,6 +268,18 @@ def sgad_l1_loss_grad(views, rendered, target_rgb, target_depth, rgb_weight, dep
                       loss_accum: int, valid_count: int, stream: int) -> None:
     _call("sgad_l1_loss_grad", len(views), views, rendered, target_rgb, target_depth, float(rgb_weight),
           float(depth_weight), d_rgb, d_depth, loss_accum, valid_count, stream)
+
+
+def sgad_ssim_workspace_size(views) -> int:
+    n = C.c_size_t(0)
+    _call("sgad_ssim_workspace_size", len(views), views, C.byref(n))
+    return n.value
+
+
+def sgad_ssim_loss_grad(views, rendered, target_rgb, weight, d_rgb, loss_accum: int, workspace: int,
+                        ws_bytes: int, stream: int) -> None:
+    _call("sgad_ssim_loss_grad", len(views), views, rendered, target_rgb, float(weight), d_rgb, loss_accum,
+          workspace, C.c_size_t(ws_bytes), stream)
 
 
 SGAD_ADAM_PLAIN = 0

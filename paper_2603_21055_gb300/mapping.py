@@ -1,7 +1,8 @@
-"""Mapping iterations (Sec. 3.2, Eq. 1 with the SSIM term left out) on the GPU.
+"""Mapping iterations (Sec. 3.2, Eq. 1) on the GPU.
 
 One iteration renders every keyframe of the window into every view (forward splatting),
-takes the L1 colour + depth loss gradient against the observed RGB-D, runs the adjoint
+takes the L1 colour + depth loss gradient against the observed RGB-D (plus the SSIM term
+when the scene's ssim_weight is nonzero), runs the adjoint
 into offset, colour, opacity logit and scale of the learnable keyframes, and applies one
 Adam step with the learning rates of the supplementary Sec. A (colour 0.0025, radius
 0.005, opacity 0.05, offset 0.01; the radius rate is applied to log s). All of it is
@@ -73,6 +74,8 @@ class Mapper:
         self.loss.zero_()
         sp.l1_loss_grad(self.views, self.images, self.trgb, self.tdep, self.scene.rgb_weight, self.scene.depth_weight,
                         self.d_rgb, self.d_dep, self.loss, self.valid)
+        if self.scene.ssim_weight != 0:
+            sp.ssim_loss_grad(self.views, self.images, self.trgb, self.scene.ssim_weight, self.d_rgb, self.loss)
         sp.backward(self.kfs, self.views, self.gin, self.grads)
         if self.n_adam:
             B.sgad_adam_step_multi(self.adam, 0.9, 0.999, 1e-15, self.step_counter.data_ptr(), sp.stream())
@@ -98,11 +101,12 @@ class Mapper:
     def launches_per_step(self) -> int:
         """Library kernels per iteration: projection+count, scan, emission, sort, forward
         compositing (one launch per view with the per-view schedule); valid-depth count and
-        L1 gradient; backward compositing, finalisation; multi-tensor Adam and its step
-        counter."""
+        L1 gradient; the two SSIM passes when that term is on; backward compositing,
+        finalisation; multi-tensor Adam and its step counter."""
         o = self.sp.options
         per = lambda sched: len(self.views) if sched == B.SGAD_SCHEDULE_PER_VIEW else 1
         n = 4 + per(o.fwd_schedule) + (2 if self.scene.depth_weight != 0 else 1) + per(o.bwd_schedule) + 1
+        n += 2 if self.scene.ssim_weight != 0 else 0
         return n + (2 if self.n_adam else 0)
 
     def autotune(self, reps: int = 5):

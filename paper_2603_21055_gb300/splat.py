@@ -99,6 +99,7 @@ class Splatter:
         self.workspace: Optional[torch.Tensor] = None
         self.key_capacity = 0
         self._cache = {}
+        self._ssim_ws: Optional[torch.Tensor] = None
 
     def __del__(self):
         try:
@@ -287,6 +288,20 @@ class Splatter:
         B.sgad_l1_loss_grad(va, rend, tr, td, rgb_weight, depth_weight, dr, dd,
                             _ptr(loss_accum) if loss_accum is not None else None,
                             valid_count.data_ptr() if valid_count is not None else None, self.stream())
+
+    def ssim_loss_grad(self, views, images, target_rgb, weight, d_rgb, loss_accum: Optional[torch.Tensor] = None):
+        """tau L_S of Eq. 1 for every view, ADDED to d_rgb (call after l1_loss_grad)."""
+        va = self.view_structs(views)
+        need = B.sgad_ssim_workspace_size(va)
+        if self._ssim_ws is None or self._ssim_ws.numel() < need:
+            self._ssim_ws = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
+        rend = (B.sgad_images * len(views))()
+        for i, im in enumerate(images):
+            rend[i] = B.sgad_images(_ptr(im["rgb"]), _ptr(im["depth"]), _ptr(im["alpha"]))
+        tr = B.ptr_array([_ptr(t) for t in target_rgb])
+        dr = B.ptr_array([_ptr(t) for t in d_rgb])
+        B.sgad_ssim_loss_grad(va, rend, tr, weight, dr, _ptr(loss_accum) if loss_accum is not None else None,
+                              self._ssim_ws.data_ptr(), self._ssim_ws.numel(), self.stream())
 
 
 class SplatFn(torch.autograd.Function):

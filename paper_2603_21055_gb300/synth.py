@@ -77,6 +77,7 @@ class Scene:
     depth_weight: float = 0.0               # weight of the L1 depth term
     rgb_weight: float = 1.0                 # weight of the L1 colour term
     name: str = ""
+    ssim_weight: float = 0.0                # weight of the SSIM term (tau of Eq. 1)
 
     @property
     def n_gaussians(self) -> int:
@@ -405,7 +406,8 @@ def crop_scene(scene: Scene, kf_box: Tuple[int, int, int, int], view_box: Tuple[
         sl = (slice(vy, vy + vh), slice(vx, vx + vw))
         tr.append(np.ascontiguousarray(r[(slice(None),) + sl]))
         td.append(np.ascontiguousarray(d[sl]))
-    return Scene(kfs, views, tr, td, scene.depth_weight, scene.rgb_weight, scene.name + "_crop")
+    return Scene(kfs, views, tr, td, scene.depth_weight, scene.rgb_weight, scene.name + "_crop",
+                 scene.ssim_weight)
 
 
 def fd_subscene(seed: int = 5, kw: int = 20, kh: int = 10, vw: int = 32, vh: int = 32) -> Scene:

@@ -146,3 +146,32 @@ def test_net_shapes_and_workspace_on_the_host():
     assert lib.sgad_net_layer_shape(4, None, None, None, None) == B.SGAD_ERR_INVALID_ARG
     p = B.sgad_net_params()
     assert lib.sgad_net_forward(C.byref(p), 1, 48, 64, None, None, None, None, None, 0, None) == B.SGAD_ERR_INVALID_ARG
+
+
+def test_ssim_workspace_and_validation_on_the_host():
+    """SSIM scratch: 9 floats per pixel per view, each view's block rounded to 256 B; bad
+    arguments are refused before any launch."""
+    views = (B.sgad_camera * 2)(_cam(), _cam(100, 70))
+    r = lambda x: (x + 255) // 256 * 256
+    assert B.sgad_ssim_workspace_size(views) == r(9 * 4 * 64 * 48) + r(9 * 4 * 100 * 70)
+    lib = B.load()
+    n = C.c_size_t()
+    assert lib.sgad_ssim_workspace_size(0, views, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
+    assert lib.sgad_ssim_workspace_size(65, views, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
+    bad = (B.sgad_camera * 1)(_cam(0, 10))
+    assert lib.sgad_ssim_workspace_size(1, bad, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
+    one = (B.sgad_camera * 1)(_cam())
+    rend = (B.sgad_images * 1)()
+    arr = B.ptr_array([0])
+    # NULL images, a missing workspace, a misaligned one and a non-finite weight
+    assert lib.sgad_ssim_loss_grad(1, one, rend, arr, C.c_float(0.2), arr, None, None, 0, None) == B.SGAD_ERR_INVALID_ARG
+    assert lib.sgad_ssim_loss_grad(1, one, None, arr, C.c_float(0.2), arr, None, None, 0, None) == B.SGAD_ERR_INVALID_ARG
+    fake = B.ptr_array([4096])
+    rend[0] = B.sgad_images(4096, 0, 0)
+    need = B.sgad_ssim_workspace_size(one)
+    assert lib.sgad_ssim_loss_grad(1, one, rend, fake, C.c_float(0.2), fake, None, None, need,
+                                   None) == B.SGAD_ERR_WORKSPACE_TOO_SMALL
+    assert lib.sgad_ssim_loss_grad(1, one, rend, fake, C.c_float(0.2), fake, None, 4096 + 16, need,
+                                   None) == B.SGAD_ERR_INVALID_ARG
+    assert lib.sgad_ssim_loss_grad(1, one, rend, fake, C.c_float(float("inf")), fake, None, 4096, need,
+                                   None) == B.SGAD_ERR_INVALID_ARG
