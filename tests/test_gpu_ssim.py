@@ -73,8 +73,10 @@ def _check(sizes, xs, ys, weight, got_loss, got_d, base=None):
 @pytest.mark.parametrize("close", [False, True])
 def test_ssim_uneven_views_match_oracle(close):
     rng = np.random.default_rng(11 + close)
-    # ragged tiles, a view narrower and shorter than the 11 x 11 window, one exactly 2 x 2 tiles
-    sizes = [(70, 45), (33, 64), (7, 5), (64, 64), (1, 1)]
+    # ragged tiles, a view narrower and shorter than the 11 x 11 window, one exactly 2 x 2
+    # tiles; widths that are multiples of 4 take the 16-byte staging path, the others the
+    # 4-byte one
+    sizes = [(70, 45), (33, 64), (7, 5), (64, 64), (1, 1), (100, 45), (4, 3)]
     xs, ys = _images(rng, sizes, close)
     loss, d = _run(sizes, xs, ys, 0.2)
     _check(sizes, xs, ys, 0.2, loss, d)
