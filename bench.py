@@ -54,16 +54,18 @@ def parse():
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--json-out", default="")
-    p.add_argument("--workload", choices=["room8", "batching", "mapping", "learned", "net", "ssim"],
+    p.add_argument("--workload", choices=["room8", "batching", "mapping", "learned", "net", "ssim", "sequence"],
                    default="room8",
                    help="room8: the headline line (default); batching: 32 uneven views, batched vs per-view "
                         "launches and the autotuner; mapping: 10 x 1200x680 keyframes, 100 Adam iterations; "
                         "learned: train the proposal net on plain-mapping targets and time mapping to 30 dB "
                         "with learned vs zero initialisation; net: forward and backward of the proposal net "
-                        "on 8 frames of 640x480; ssim: the SSIM term's two passes on 8 x 640x480")
+                        "on 8 frames of 640x480; ssim: the SSIM term's two passes on 8 x 640x480; sequence: "
+                        "mapping s/frame of a 1200x680 sequence, frames sharded over the ranks")
     p.add_argument("--train-rooms", type=int, default=50)
     p.add_argument("--eval-rooms", type=int, default=10)
     p.add_argument("--frames", type=int, default=40, help="frames per room (learned workload)")
+    p.add_argument("--seq-frames", type=int, default=16, help="frames of the sequence workload")
     p.add_argument("--train-steps", type=int, default=3000)
     p.add_argument("--workers", type=int, default=0, help="ray-casting processes (0: all cores)")
     return p.parse_args()
@@ -881,6 +883,74 @@ def run_ssim(args):
     _emit(line, args)
 
 
+def run_sequence(args):
+    """Mapping seconds per frame of an RGB-D sequence of 1200x680 frames (Replica-sized;
+    100 iterations of Eq. 1 per frame, each frame's Gaussians with its 4 previous frames
+    as fixed neighbours, views = the frame and those neighbours), frames sharded over the
+    ranks in waves with an all-gather of each wave's mapped parameters; and the same with
+    each frame's own Gaussians only (the paper's parallel mode). Wall time from the first
+    frame's arrival to every rank holding every mapped frame, after one warm-up frame."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2603_21055_gb300 import learned, parallel
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    size = (1200, 680, 600.0, 600.0, 340.0)
+    t0 = time.perf_counter()
+    fr = learned.room_frames(args.seed + 100, n_frames=args.seq_frames, size=size)
+    gen_s = time.perf_counter() - t0
+    seq = parallel.Sequence(fr["poses"], fr["rgb"], fr["obs"], size)
+    out = {}
+    clk = None
+    for mode, views in (("neighbours", "one"), ("own_only", "one"), ("neighbours", "all"), ("own_only", "all")):
+        fm = parallel.FrameMapper(seq, nn=parallel.NN, iters=100, views_per_iter=views)
+        fm(0, {})                                       # warm-up: library, allocator, caches
+        fm.psnr.clear()
+        fm.losses.clear()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        w0 = time.perf_counter()
+        sm = parallel.ShardedMapping(seq.n_frames, seq.hw, fm, own_only=(mode.startswith("own")))
+        sm.run()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        wall = time.perf_counter() - w0
+        c = clocks.stop()
+        clk = clk or c
+        if world > 1:
+            t = torch.tensor([wall], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        mine = sorted(fm.psnr)
+        out["%s/%s" % (mode, views)] = {"s_per_frame": round(wall / seq.n_frames, 4), "wall_s": round(wall, 3),
+                     "psnr_db_own_view_mean": round(float(np.mean([fm.psnr[i] for i in mine])), 3),
+                     "loss_drop_mean": round(float(np.mean([fm.losses[i][1] / fm.losses[i][0] for i in mine])), 4),
+                     "frames_mapped_on_rank0": len(mine)}
+    line = {"metric": "mapping s/frame, 1200x680 RGB-D sequence, 100 iterations of Eq. 1 per frame",
+            "value": out["neighbours/one"]["s_per_frame"], "unit": "s/frame", "n_gpus": world,
+            "steps": seq.n_frames, "warmup": 1, "higher_is_better": False, "scaling": "strong", "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sequence %d x 1200x680 (fx 600), %d previous frames as fixed neighbours, "
+                                   "views = frame + neighbours, loss 0.8 L1 + 0.2 SSIM + 1.0 L1 depth; value: "
+                                   "neighbours fixed, one view per iteration (own view on 40 %%)"
+                                   % (seq.n_frames, parallel.NN),
+                       "parallelism": "frames in waves of %d, all-gather per wave" % world,
+                       "generation_s": round(gen_s, 1)},
+            "modes": out, "clocks": clk,
+            "paper_context": "0.89 s/frame on 1 RTX 4090, 0.15 s/frame on 8 (own Gaussians only), Replica"}
+    if rank == 0:
+        _emit(line, args)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -895,6 +965,8 @@ def main():
         run_net(args)
     elif args.workload == "ssim":
         run_ssim(args)
+    elif args.workload == "sequence":
+        run_sequence(args)
     else:
         run_ours(args)
 

@@ -69,14 +69,24 @@ class Mapper:
         self.sp.forward(self.kfs, self.views, self.images)
 
     def step_eager(self):
+        self._step(range(len(self.views)))
+
+    def step_views(self, idx):
+        """One iteration that renders, and takes the loss of, only the views `idx` (indices
+        into the scene's views); the workspace planned for all views serves any subset."""
+        self._step(list(idx))
+
+    def _step(self, idx):
         sp = self.sp
-        sp.forward(self.kfs, self.views, self.images)
+        pick = lambda xs: [xs[k] for k in idx]
+        views, images, d_rgb = pick(self.views), pick(self.images), pick(self.d_rgb)
+        sp.forward(self.kfs, views, images)
         self.loss.zero_()
-        sp.l1_loss_grad(self.views, self.images, self.trgb, self.tdep, self.scene.rgb_weight, self.scene.depth_weight,
-                        self.d_rgb, self.d_dep, self.loss, self.valid)
+        sp.l1_loss_grad(views, images, pick(self.trgb), pick(self.tdep), self.scene.rgb_weight,
+                        self.scene.depth_weight, d_rgb, pick(self.d_dep), self.loss, self.valid)
         if self.scene.ssim_weight != 0:
-            sp.ssim_loss_grad(self.views, self.images, self.trgb, self.scene.ssim_weight, self.d_rgb, self.loss)
-        sp.backward(self.kfs, self.views, self.gin, self.grads)
+            sp.ssim_loss_grad(views, images, pick(self.trgb), self.scene.ssim_weight, d_rgb, self.loss)
+        sp.backward(self.kfs, views, pick(self.gin), self.grads)
         if self.n_adam:
             B.sgad_adam_step_multi(self.adam, 0.9, 0.999, 1e-15, self.step_counter.data_ptr(), sp.stream())
 
