@@ -13,7 +13,8 @@ Readings (the paper is silent or garbled):
   * Selection: the pixels (u, v) with u and v multiples of R and depth > 0, in raster
     order, back-projected to p = d ((u - cx) / fx, (v - cy) / fy, 1).
   * Neighbours: the K_c nearest selected points of the same frame, the point itself
-    included, by FP32 squared distance ((dx dx + dy dy) + dz dz), ties by index.
+    included, by FP32 squared distance ((dx dx + dy dy) + dz dz), ties by index (all of
+    them when the frame has fewer than K_c points).
   * Covariance: (1 / K_c) sum (p - m)(p - m)^T over those points; its eigen-decomposition
     (the SVD of a symmetric PSD matrix) gives scales s_k = sqrt(lambda_k) and rotation.
   * Scale normalisation: s <- s / max(s), each normalised scale floored at sqrt(1e-3)
@@ -76,9 +77,10 @@ def sqdist32(a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 
 def knn(points: np.ndarray, K: int, chunk: int = 512) -> np.ndarray:
-    """(M, K) indices of each point's K nearest points (itself included), FP32 distances,
-    ties by index."""
+    """(M, min(K, M)) indices of each point's K nearest points (itself included), FP32
+    distances, ties by index (all M points when there are fewer than K)."""
     P = np.asarray(points, F32)
+    K = min(K, len(P))
     out = np.empty((len(P), K), np.int64)
     for s in range(0, len(P), chunk):
         D = sqdist32(P[s:s + chunk], P)

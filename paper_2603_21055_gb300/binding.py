@@ -27,6 +27,10 @@ EXPORTS = ["sgad_default_options", "sgad_create", "sgad_destroy", "sgad_last_err
            "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_adam_step",
            "sgad_adam_step_multi", "sgad_forward_noalloc", "sgad_autotune", "sgad_get_options",
            "sgad_ssim_workspace_size", "sgad_ssim_loss_grad",
+           # include/sgad_gicp.h
+           "sgad_gicp_default_params", "sgad_gicp_workspace_size", "sgad_gicp_frame", "sgad_gicp_index",
+           "sgad_gicp_correspond", "sgad_gicp_linearize", "sgad_gicp_set_pose", "sgad_gicp_track",
+           "sgad_gicp_insert", "sgad_gicp_result",
            # include/sgad_net.h
            "sgad_net_layer_shape", "sgad_net_workspace_size", "sgad_net_forward", "sgad_net_loss_grad",
            "sgad_net_backward", "sgad_net_check", "sgad_net_buffers_view"]
@@ -57,6 +61,21 @@ class sgad_images(C.Structure):
 
 class sgad_image_grads(C.Structure):
     _fields_ = [("d_rgb", C.c_void_p), ("d_depth", C.c_void_p), ("d_alpha", C.c_void_p), ("d_pose", C.c_void_p)]
+
+
+class sgad_gicp_params(C.Structure):
+    _fields_ = [("stride", C.c_int32), ("k_cov", C.c_int32), ("k_match", C.c_int32), ("max_iters", C.c_int32),
+                ("r_max", C.c_float), ("d_overlap", C.c_float), ("tol", C.c_float), ("eps", C.c_float)]
+
+
+class sgad_gaussian_set(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("cov", C.c_void_p), ("normal", C.c_void_p), ("count", C.c_void_p),
+                ("capacity", C.c_int32)]
+
+
+class sgad_gicp_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("n_matches", C.c_int32),
+                ("status", C.c_int32), ("cost", C.c_double), ("step", C.c_double)]
 
 
 class sgad_keyframe_grads(C.Structure):
@@ -165,6 +184,16 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         "sgad_get_options": (st, [P, P]),
         "sgad_ssim_workspace_size": (st, [I32, P, P]),
         "sgad_ssim_loss_grad": (st, [I32, P, P, P, C.c_float, P, P, P, C.c_size_t, P]),
+        "sgad_gicp_default_params": (st, [P]),
+        "sgad_gicp_workspace_size": (st, [P, I32, I32, P]),
+        "sgad_gicp_frame": (st, [P, P, P, P, P, P, P, C.c_size_t, P]),
+        "sgad_gicp_index": (st, [P, P, P, C.c_size_t, P]),
+        "sgad_gicp_correspond": (st, [P, P, P, P, P, P, C.c_size_t, P]),
+        "sgad_gicp_linearize": (st, [P, P, P, P, P, P, C.c_size_t, P]),
+        "sgad_gicp_set_pose": (st, [P, P, C.c_size_t, P]),
+        "sgad_gicp_track": (st, [P, P, P, P, P, C.c_size_t, P]),
+        "sgad_gicp_insert": (st, [P, P, P, P, C.c_size_t, P]),
+        "sgad_gicp_result": (st, [P, C.c_size_t, P, P, P]),
         "sgad_net_layer_shape": (st, [I32, P, P, P, P]),
         "sgad_net_workspace_size": (st, [I32, I32, I32, P]),
         "sgad_net_forward": (st, [P, I32, I32, I32, P, P, P, P, P, C.c_size_t, P]),
@@ -280,6 +309,71 @@ def sgad_ssim_loss_grad(views, rendered, target_rgb, weight, d_rgb, loss_accum: 
                         ws_bytes: int, stream: int) -> None:
     _call("sgad_ssim_loss_grad", len(views), views, rendered, target_rgb, float(weight), d_rgb, loss_accum,
           workspace, C.c_size_t(ws_bytes), stream)
+
+
+def sgad_gicp_default_params() -> sgad_gicp_params:
+    p = sgad_gicp_params()
+    _call("sgad_gicp_default_params", C.byref(p))
+    return p
+
+
+def sgad_gicp_workspace_size(p: sgad_gicp_params, src_capacity: int, map_capacity: int) -> int:
+    n = C.c_size_t(0)
+    _call("sgad_gicp_workspace_size", C.byref(p), int(src_capacity), int(map_capacity), C.byref(n))
+    return n.value
+
+
+def sgad_gicp_frame(p, cam, depth: int, out: sgad_gaussian_set, pix_out: int, knn_out: int, ws: int, ws_bytes: int,
+                    stream: int) -> None:
+    _call("sgad_gicp_frame", C.byref(p), C.byref(cam), depth, C.byref(out), pix_out or None, knn_out or None, ws,
+          C.c_size_t(ws_bytes), stream)
+
+
+def sgad_gicp_index(p, map_: sgad_gaussian_set, ws: int, ws_bytes: int, stream: int) -> None:
+    _call("sgad_gicp_index", C.byref(p), C.byref(map_), ws, C.c_size_t(ws_bytes), stream)
+
+
+def _f12(pose):
+    a = (C.c_float * 12)()
+    for i, v in enumerate(list(pose)):
+        a[i] = float(v)
+    return a
+
+
+def _d12(pose):
+    a = (C.c_double * 12)()
+    for i, v in enumerate(list(pose)):
+        a[i] = float(v)
+    return a
+
+
+def sgad_gicp_correspond(p, src, map_, pose, idx_out: int, ws: int, ws_bytes: int, stream: int) -> None:
+    _call("sgad_gicp_correspond", C.byref(p), C.byref(src), C.byref(map_), _f12(pose), idx_out, ws,
+          C.c_size_t(ws_bytes), stream)
+
+
+def sgad_gicp_linearize(p, src, map_, pose, system_out: int, ws: int, ws_bytes: int, stream: int) -> None:
+    _call("sgad_gicp_linearize", C.byref(p), C.byref(src), C.byref(map_), _f12(pose), system_out, ws,
+          C.c_size_t(ws_bytes), stream)
+
+
+def sgad_gicp_set_pose(pose, ws: int, ws_bytes: int, stream: int) -> None:
+    _call("sgad_gicp_set_pose", _d12(pose), ws, C.c_size_t(ws_bytes), stream)
+
+
+def sgad_gicp_track(p, src, map_, pose0, ws: int, ws_bytes: int, stream: int) -> None:
+    _call("sgad_gicp_track", C.byref(p), C.byref(src), C.byref(map_), _d12(pose0), ws, C.c_size_t(ws_bytes), stream)
+
+
+def sgad_gicp_insert(p, src, map_, ws: int, ws_bytes: int, stream: int) -> None:
+    _call("sgad_gicp_insert", C.byref(p), C.byref(src), C.byref(map_), ws, C.c_size_t(ws_bytes), stream)
+
+
+def sgad_gicp_result(ws: int, ws_bytes: int, stream: int):
+    pose = (C.c_double * 12)()
+    st = sgad_gicp_stats()
+    _call("sgad_gicp_result", ws, C.c_size_t(ws_bytes), pose, C.byref(st), stream)
+    return list(pose), st
 
 
 SGAD_ADAM_PLAIN = 0
