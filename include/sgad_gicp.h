@@ -49,6 +49,8 @@ typedef struct {
     float d_overlap;      /* map update: overlap distance in metres (>= 0) */
     float tol;            /* stop when |xi| < tol (>= 0) */
     float eps;            /* floor of the normalised variances, in (0, 1] */
+    int32_t src_capacity; /* largest source set the workspace serves, in [1, 2^24] */
+    int32_t map_capacity; /* largest map the workspace serves, in [1, 2^24] */
 } sgad_gicp_params;
 
 /* A set of geometry Gaussians (caller-owned device arrays, `capacity` records each). */
@@ -71,13 +73,14 @@ typedef struct {
 } sgad_gicp_stats;
 
 /* R 10, K_c 10, k_match 5, 30 iterations, r_max 0.1 m, d_overlap 0.02 m, tol 1e-6,
- * eps 1e-3. */
+ * eps 1e-3, capacities 2^16 (source) and 2^20 (map). */
 sgad_status sgad_gicp_default_params(sgad_gicp_params *out);
 
-/* Workspace bytes for source sets of up to src_capacity and maps of up to map_capacity
- * Gaussians (state, per-block partial sums, the map's hash grid, scratch). */
-sgad_status sgad_gicp_workspace_size(const sgad_gicp_params *p, int32_t src_capacity, int32_t map_capacity,
-                                     size_t *bytes);
+/* Workspace bytes for these parameters (state, the map's and the source's hash grids,
+ * per-block partial sums, scratch). Every call computes the workspace's layout from the
+ * parameters it is given, so all calls on one workspace take the same capacities; a set
+ * passed to a call may be smaller than its capacity in the parameters. */
+sgad_status sgad_gicp_workspace_size(const sgad_gicp_params *p, size_t *bytes);
 
 /* T_i of a depth map (device [H][W] FP32, z-depth, 0 = invalid) in the camera frame into
  * `out` (its count is written). pix_out (device int32 [capacity], may be NULL) receives
@@ -88,8 +91,9 @@ sgad_status sgad_gicp_frame(const sgad_gicp_params *p, const sgad_camera *cam, c
                             const sgad_gaussian_set *out, int32_t *pix_out, int32_t *knn_out, void *workspace,
                             size_t ws_bytes, void *stream);
 
-/* The map's spatial hash grid (cells of max(r_max, d_overlap) x 1.001 m). Required after
- * the caller changes the map; sgad_gicp_insert rebuilds it itself. */
+/* The map's spatial hash grid (cells of max(r_max, d_overlap) / 3; searches visit rings
+ * of cells until their result is proven). Required after the caller changes the map;
+ * sgad_gicp_insert rebuilds it itself. */
 sgad_status sgad_gicp_index(const sgad_gicp_params *p, const sgad_gaussian_set *map, void *workspace,
                             size_t ws_bytes, void *stream);
 

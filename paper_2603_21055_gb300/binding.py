@@ -65,7 +65,8 @@ class sgad_image_grads(C.Structure):
 
 class sgad_gicp_params(C.Structure):
     _fields_ = [("stride", C.c_int32), ("k_cov", C.c_int32), ("k_match", C.c_int32), ("max_iters", C.c_int32),
-                ("r_max", C.c_float), ("d_overlap", C.c_float), ("tol", C.c_float), ("eps", C.c_float)]
+                ("r_max", C.c_float), ("d_overlap", C.c_float), ("tol", C.c_float), ("eps", C.c_float),
+                ("src_capacity", C.c_int32), ("map_capacity", C.c_int32)]
 
 
 class sgad_gaussian_set(C.Structure):
@@ -185,7 +186,7 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         "sgad_ssim_workspace_size": (st, [I32, P, P]),
         "sgad_ssim_loss_grad": (st, [I32, P, P, P, C.c_float, P, P, P, C.c_size_t, P]),
         "sgad_gicp_default_params": (st, [P]),
-        "sgad_gicp_workspace_size": (st, [P, I32, I32, P]),
+        "sgad_gicp_workspace_size": (st, [P, P]),
         "sgad_gicp_frame": (st, [P, P, P, P, P, P, P, C.c_size_t, P]),
         "sgad_gicp_index": (st, [P, P, P, C.c_size_t, P]),
         "sgad_gicp_correspond": (st, [P, P, P, P, P, P, C.c_size_t, P]),
@@ -317,9 +318,9 @@ def sgad_gicp_default_params() -> sgad_gicp_params:
     return p
 
 
-def sgad_gicp_workspace_size(p: sgad_gicp_params, src_capacity: int, map_capacity: int) -> int:
+def sgad_gicp_workspace_size(p: sgad_gicp_params) -> int:
     n = C.c_size_t(0)
-    _call("sgad_gicp_workspace_size", C.byref(p), int(src_capacity), int(map_capacity), C.byref(n))
+    _call("sgad_gicp_workspace_size", C.byref(p), C.byref(n))
     return n.value
 
 

@@ -6,6 +6,7 @@
 // Where floating point decides an integer (neighbour ranks, correspondences, overlaps)
 // the kernels use explicitly rounded FP32 operations (__fmul_rn, __fadd_rn, ...) in a
 // fixed order, so the decision does not depend on the compiler's contraction choices.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cmath>
@@ -39,39 +40,51 @@ struct GicpState {
 };
 
 struct GLayout {
-    size_t state, partial, sel_counts, ins_flags, ins_counts, hash_cnt, hash_off, hash_ent, total;
-    int32_t table, max_blocks;
+    size_t state, sel_counts, tile_sums, hash_cnt, hash_off, hash_pts, knn_cnt, knn_off, knn_pts, partial, ins_flags,
+        ins_counts, total;
+    int32_t table, knn_table, max_blocks, step_blocks;
 };
+
+constexpr int kScanTile = 4096;          // buckets per tile of the parallel scan
+constexpr int kMaxTiles = 4096;          // tables of up to 2^24 buckets
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Sections: the fixed ones first, then the map's hash grid (sized by the map's
-// capacity), then the source's scratch (sized by the source's capacity), so a call that
-// only touches a prefix does not depend on the capacities of sets it is not given.
-GLayout glayout(int32_t src_cap, int32_t map_cap)
+int32_t table_for(int32_t cap)
+{
+    int32_t t = 1024;
+    while (t < 2 * cap && t < (1 << 24)) t <<= 1;
+    return t;
+}
+
+// Every call computes the same layout from the parameters (capacities included).
+GLayout glayout(const sgad_gicp_params &p)
 {
     GLayout L;
-    int32_t t = 1024;
-    while (t < 2 * map_cap && t < (1 << 24)) t <<= 1;
-    L.table = t;
-    L.max_blocks = (src_cap + kStepThreads - 1) / kStepThreads;
+    L.table = table_for(p.map_capacity);
+    L.knn_table = table_for(p.src_capacity);
+    L.max_blocks = (p.src_capacity + kStepThreads - 1) / kStepThreads;
+    // the correspondence step: one team of 8 lanes per source point, 32 per block,
+    // grid-stride over at most 4 blocks per SM of a 152-SM part
+    L.step_blocks = std::min((p.src_capacity + 31) / 32, 4 * 152);
     size_t o = 0;
-    L.state = o;
-    o = a256(o + sizeof(GicpState));
-    L.sel_counts = o;
-    o = a256(o + (size_t)kMaxSelBlocks * sizeof(int32_t));
-    L.hash_cnt = o;
-    o = a256(o + (size_t)t * sizeof(int32_t));
-    L.hash_off = o;
-    o = a256(o + (size_t)(t + 1) * sizeof(int32_t));
-    L.hash_ent = o;
-    o = a256(o + (size_t)map_cap * sizeof(int32_t));
-    L.partial = o;
-    o = a256(o + (size_t)L.max_blocks * 32 * sizeof(float));
-    L.ins_flags = o;
-    o = a256(o + (size_t)src_cap * sizeof(int32_t));
-    L.ins_counts = o;
-    o = a256(o + (size_t)(L.max_blocks + 1) * sizeof(int32_t));
+    const auto take = [&o](size_t bytes) {
+        const size_t at = o;
+        o = a256(o + bytes);
+        return at;
+    };
+    L.state = take(sizeof(GicpState));
+    L.sel_counts = take((size_t)kMaxSelBlocks * sizeof(int32_t));
+    L.tile_sums = take((size_t)kMaxTiles * sizeof(int32_t));
+    L.hash_cnt = take((size_t)L.table * sizeof(int32_t));
+    L.hash_off = take((size_t)(L.table + 1) * sizeof(int32_t));
+    L.hash_pts = take((size_t)p.map_capacity * sizeof(float4));
+    L.knn_cnt = take((size_t)L.knn_table * sizeof(int32_t));
+    L.knn_off = take((size_t)(L.knn_table + 1) * sizeof(int32_t));
+    L.knn_pts = take((size_t)p.src_capacity * sizeof(float4));
+    L.partial = take((size_t)std::max(L.max_blocks, L.step_blocks) * 32 * sizeof(float));
+    L.ins_flags = take((size_t)p.src_capacity * sizeof(int32_t));
+    L.ins_counts = take((size_t)(L.max_blocks + 1) * sizeof(int32_t));
     L.total = o;
     return L;
 }
@@ -301,91 +314,227 @@ __global__ void __launch_bounds__(256) k_select_write(const __grid_constant__ Se
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *a.count = min(prefix + total, a.capacity);
 }
 
-// ------------------------------------------------------------------ shapes
-template <int KMAX>
-__global__ void __launch_bounds__(64) k_shape(const float4 *__restrict__ pos, const int32_t *count, int K, float eps,
-                                              float4 *cov, float4 *normal, int32_t *knn_out)
+// ------------------------------------------------------------------ team search
+// Neighbour searches run one query per team of kTeam lanes of a warp: the lanes share the
+// cells of each ring, keep their own sorted candidate lists, and rank their candidates
+// among the team's through shared memory, which gives the exact team-wide k-th candidate
+// after every ring (for the stopping proof) and the final sorted list.
+constexpr int kTeam = 8;
+constexpr int kRings = 4;                // rings searched before the exhaustive fallback
+
+struct Grid {
+    const int32_t *off;       // [table + 1] bucket offsets
+    const float4 *pts;        // [indexed count] points sorted by bucket: x, y, z, index bits
+    float inv_cell, cell;
+    uint32_t mask;
+};
+
+__device__ __forceinline__ bool lex_less(float d1, int j1, float d2, int j2)
 {
-    const int kcov = K;
-    __shared__ float4 tile[128];
-    const int n = *count;
-    const int i = blockIdx.x * 64 + threadIdx.x;
-    if ((int)(blockIdx.x * 64) >= n) return;                  // whole block idle (uniform)
-    K = min(K, n);                                            // fewer points than K_c: all of them
-    const bool act = i < n;
-    const float4 me = act ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    return d1 < d2 || (d1 == d2 && j1 < j2);
+}
+
+__device__ __forceinline__ unsigned team_mask() { return 0xFFu << (threadIdx.x & 24); }
+
+// Sorted insert into a lane's list (entries are unique: every point is seen once);
+// (wd, wj) tracks the list's K-th entry for the early rejection.
+template <int KMAX>
+__device__ __forceinline__ void lane_insert(float d, int j, int K, float (&bd)[KMAX], int (&bj)[KMAX], float &wd,
+                                            int &wj)
+{
+    if (!lex_less(d, j, wd, wj)) return;
+    float cd = d;
+    int cj = j;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < K && lex_less(cd, cj, bd[k], bj[k])) {
+            const float td = bd[k];
+            const int tj = bj[k];
+            bd[k] = cd;
+            bj[k] = cj;
+            cd = td;
+            cj = tj;
+        }
+        if (k == K - 1) {
+            wd = bd[k];
+            wj = bj[k];
+        }
+    }
+}
+
+// Calls f(q) for every point of the cells of ring r around (ix, iy, iz) that this lane
+// owns (cube cells c = tl, tl + kTeam, ... with Chebyshev distance r). Points stored in
+// a visited bucket but belonging to another cell (hash collisions) are skipped, so each
+// point is seen once, in its own cell.
+template <typename F>
+__device__ __forceinline__ void team_ring(const Grid &g, int ix, int iy, int iz, int r, int tl, F &&f)
+{
+    const int side = 2 * r + 1, ncube = side * side * side;
+#pragma unroll 1
+    for (int c = tl; c < ncube; c += kTeam) {
+        const int dx = c % side - r, dy = (c / side) % side - r, dz = c / (side * side) - r;
+        if (max(abs(dx), max(abs(dy), abs(dz))) != r) continue;
+        const int cx = ix + dx, cy = iy + dy, cz = iz + dz;
+        const uint32_t h = cell_hash(cx, cy, cz, g.mask);
+        const int e1 = g.off[h + 1];
+#pragma unroll 1
+        for (int e = g.off[h]; e < e1; ++e) {
+            const float4 q = g.pts[e];
+            if (cell_of(q.x, g.inv_cell) == cx && cell_of(q.y, g.inv_cell) == cy && cell_of(q.z, g.inv_cell) == cz)
+                f(q);
+        }
+    }
+}
+
+// The team's K smallest (d, j) entries in order, merged from the lanes' sorted lists
+// (copied to the team's shared-memory slots sd/sj [kTeam][KMAX]): K rounds of a team
+// argmin over the lanes' heads. Writes out/outd [0, found) and returns found.
+template <int KMAX>
+__device__ __forceinline__ int team_select(const float (&bd)[KMAX], const int (&bj)[KMAX], int K, float *sd, int *sj,
+                                           int tl, int *out, float *outd)
+{
+    const unsigned m = team_mask();
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+        if (k < K) {
+            sd[tl * KMAX + k] = bd[k];
+            sj[tl * KMAX + k] = bj[k];
+        }
+    __syncwarp(m);
+    int head = 0;
+    float hd = sd[tl * KMAX];
+    int hj = sj[tl * KMAX];
+    int found = 0;
+#pragma unroll 1
+    for (; found < K; ++found) {
+        float md = hd;
+        int mj = hj, ml = tl;
+#pragma unroll
+        for (int o = kTeam / 2; o > 0; o >>= 1) {
+            const float od = __shfl_xor_sync(m, md, o, kTeam);
+            const int oj = __shfl_xor_sync(m, mj, o, kTeam), ol = __shfl_xor_sync(m, ml, o, kTeam);
+            if (lex_less(od, oj, md, mj) || (od == md && oj == mj && ol < ml)) {
+                md = od;
+                mj = oj;
+                ml = ol;
+            }
+        }
+        if (mj == INT_MAX) break;                             // the lanes hold no more entries
+        if (tl == 0) {
+            out[found] = mj;
+            outd[found] = md;
+        }
+        if (tl == ml) {
+            ++head;
+            hd = head < K ? sd[tl * KMAX + head] : FLT_MAX;
+            hj = head < K ? sj[tl * KMAX + head] : INT_MAX;
+        }
+    }
+    __syncwarp(m);
+    return found;
+}
+
+// K nearest points of `me` among the indexed ones (optionally within r_max): on return
+// out[0 .. K) (team shared memory) holds their indices nearest first, -1 past the last
+// found; returns the number found. `pos`/`n` serve the exhaustive fallback.
+template <int KMAX>
+__device__ int team_nearest(const Grid &g, float3 me, int K, float r_max, int max_rings, const float4 *pos, int n,
+                            float *sd, int *sj, int *out, float *outd)
+{
+    const int tl = threadIdx.x & (kTeam - 1);
     float bd[KMAX];
     int bj[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
         bd[k] = FLT_MAX;
-        bj[k] = 0;
+        bj[k] = INT_MAX;
     }
-    float worst = FLT_MAX;
-    for (int base = 0; base < n; base += 128) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < 128; t += 64) tile[t] = base + t < n ? pos[base + t] : make_float4(0, 0, 0, 0);
-        __syncthreads();
-        if (!act) continue;
-        const int lim = min(128, n - base);
-#pragma unroll 4
-        for (int t = 0; t < lim; ++t) {
-            const float4 q = tile[t];
+    float wd = FLT_MAX;
+    int wj = INT_MAX;
+    const float r2 = r_max * r_max;
+    const int ix = cell_of(me.x, g.inv_cell), iy = cell_of(me.y, g.inv_cell), iz = cell_of(me.z, g.inv_cell);
+    int found = 0;
+    bool proven = false;
+#pragma unroll 1
+    for (int r = 0; r <= max_rings && !proven; ++r) {
+        team_ring(g, ix, iy, iz, r, tl, [&](float4 q) {
             const float d = sqdist(q.x, q.y, q.z, me.x, me.y, me.z);
-            if (d < worst) {
-                // the list is kept sorted by (distance, index); a new candidate (the
-                // largest index so far) settles after equal distances, and an entry it
-                // displaces moves on in (distance, index) order
-                float cd = d;
-                int cj = base + t;
+            if (d <= r2) lane_insert<KMAX>(d, __float_as_int(q.w), K, bd, bj, wd, wj);
+        });
+        found = team_select<KMAX>(bd, bj, K, sd, sj, tl, out, outd);
+        const float reach = (float)r * g.cell * (1.f - 1e-4f);
+        // every point outside the searched rings lies at least `reach` away
+        proven = reach >= r_max || (found == K && outd[K - 1] < reach * reach);
+    }
+    if (!proven) {                                          // exhaustive over the set, from scratch
 #pragma unroll
-                for (int k = 0; k < KMAX; ++k) {
-                    if (k < K && (cd < bd[k] || (cd == bd[k] && cj < bj[k]))) {
-                        const float td = bd[k];
-                        const int tj = bj[k];
-                        bd[k] = cd;
-                        bj[k] = cj;
-                        cd = td;
-                        cj = tj;
-                    }
-                    if (k == K - 1) worst = bd[k];
-                }
-            }
+        for (int k = 0; k < KMAX; ++k) {
+            bd[k] = FLT_MAX;
+            bj[k] = INT_MAX;
         }
+        wd = FLT_MAX;
+        wj = INT_MAX;
+#pragma unroll 1
+        for (int j = tl; j < n; j += kTeam) {
+            const float4 q = pos[j];
+            const float d = sqdist(q.x, q.y, q.z, me.x, me.y, me.z);
+            if (d <= r2) lane_insert<KMAX>(d, j, K, bd, bj, wd, wj);
+        }
+        found = team_select<KMAX>(bd, bj, K, sd, sj, tl, out, outd);
     }
-    if (!act) return;
-    if (knn_out) {
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < kcov) knn_out[(size_t)i * kcov + k] = k < K ? bj[k] : -1;
-    }
+    return found;
+}
+
+// ------------------------------------------------------------------ shapes
+// One team per selected point: its K_c nearest selected points (FP32 squared distance,
+// ties by index) from a ring search of the points' own hash grid, then (lane 0) the
+// covariance, its eigen-decomposition and the normalised shape.
+template <int KMAX>
+__global__ void __launch_bounds__(128) k_shape(const float4 *__restrict__ pos, const int32_t *count, int K, float eps,
+                                               Grid g, float4 *cov, float4 *normal, int32_t *knn_out)
+{
+    __shared__ float s_d[128 / kTeam][kTeam * KMAX];
+    __shared__ int s_j[128 / kTeam][kTeam * KMAX];
+    __shared__ int s_out[128 / kTeam][KMAX];
+    __shared__ float s_outd[128 / kTeam][KMAX];
+    const int kcov = K;
+    const int n = *count;
+    const int team = threadIdx.x / kTeam, tl = threadIdx.x & (kTeam - 1);
+    const int i = blockIdx.x * (128 / kTeam) + team;
+    if (i >= n) return;                                       // whole team
+    K = min(K, n);                                            // fewer points than K_c: all of them
+    const float4 me4 = pos[i];
+    const float3 me = make_float3(me4.x, me4.y, me4.z);
+    team_nearest<KMAX>(g, me, K, FLT_MAX, kRings, pos, n, s_d[team], s_j[team], s_out[team], s_outd[team]);
+    const int *nb = s_out[team];
+    if (knn_out)
+        for (int k = tl; k < kcov; k += kTeam) knn_out[(size_t)i * kcov + k] = k < K ? nb[k] : -1;
+    if (tl != 0) return;
     // covariance of the K neighbours (FP32): mean, then centred second moments
     float mx = 0.f, my = 0.f, mz = 0.f;
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k)
-        if (k < K) {
-            const float4 q = pos[bj[k]];
-            mx += q.x;
-            my += q.y;
-            mz += q.z;
-        }
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+        const float4 q = pos[nb[k]];
+        mx += q.x;
+        my += q.y;
+        mz += q.z;
+    }
     const float invk = 1.f / (float)K;
     mx *= invk;
     my *= invk;
     mz *= invk;
     float A[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k)
-        if (k < K) {
-            const float4 q = pos[bj[k]];
-            const float dx = q.x - mx, dy = q.y - my, dz = q.z - mz;
-            A[0][0] += dx * dx;
-            A[0][1] += dx * dy;
-            A[0][2] += dx * dz;
-            A[1][1] += dy * dy;
-            A[1][2] += dy * dz;
-            A[2][2] += dz * dz;
-        }
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+        const float4 q = pos[nb[k]];
+        const float dx = q.x - mx, dy = q.y - my, dz = q.z - mz;
+        A[0][0] += dx * dx;
+        A[0][1] += dx * dy;
+        A[0][2] += dx * dz;
+        A[1][1] += dy * dy;
+        A[1][2] += dy * dz;
+        A[2][2] += dz * dz;
+    }
     A[0][0] *= invk;
     A[0][1] *= invk;
     A[0][2] *= invk;
@@ -397,20 +546,20 @@ __global__ void __launch_bounds__(64) k_shape(const float4 *__restrict__ pos, co
     A[2][1] = A[1][2];
     float w[3], V[3][3];
     eig3(A, w, V);
-    float s[3];
+    float sc[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) s[k] = sqrtf(fmaxf(w[k], 0.f));
-    const float smax = s[2];
+    for (int k = 0; k < 3; ++k) sc[k] = sqrtf(fmaxf(w[k], 0.f));
+    const float smax = sc[2];
     const float floor_s = sqrtf(eps);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) s[k] = fmaxf(smax > 0.f ? s[k] / smax : 1.f, floor_s);
+    for (int k = 0; k < 3; ++k) sc[k] = fmaxf(smax > 0.f ? sc[k] / smax : 1.f, floor_s);
     float C[6];
     const int rr[6] = {0, 0, 0, 1, 1, 2}, cc[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
         float acc = 0.f;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) acc += V[rr[e]][k] * (s[k] * s[k]) * V[cc[e]][k];
+        for (int k = 0; k < 3; ++k) acc += V[rr[e]][k] * (sc[k] * sc[k]) * V[cc[e]][k];
         C[e] = acc;
     }
     cov[2 * i] = make_float4(C[0], C[1], C[2], C[3]);
@@ -419,12 +568,7 @@ __global__ void __launch_bounds__(64) k_shape(const float4 *__restrict__ pos, co
 }
 
 // ------------------------------------------------------------------ hash grid
-struct Grid {
-    const int32_t *off;       // [table + 1]
-    const int32_t *ent;       // [map capacity]
-    float inv_cell;
-    uint32_t mask;
-};
+
 
 __global__ void k_hash_count(const float4 *pos, const int32_t *count, float inv_cell, uint32_t mask, int32_t *cnt)
 {
@@ -434,108 +578,72 @@ __global__ void k_hash_count(const float4 *pos, const int32_t *count, float inv_
     atomicAdd(&cnt[cell_hash(cell_of(p.x, inv_cell), cell_of(p.y, inv_cell), cell_of(p.z, inv_cell), mask)], 1);
 }
 
-// Single block of 1024 threads: exclusive offsets of the bucket counts; the counts are
-// reset to 0 for use as fill cursors.
-__global__ void __launch_bounds__(1024) k_hash_scan(int32_t *cnt, int32_t *off, int table)
+// Exclusive offsets of the bucket counts in three parallel passes (tile sums, a scan of
+// the tile sums, offsets within each tile); the counts are reset to 0 for use as fill
+// cursors.
+__global__ void __launch_bounds__(256) k_scan_tiles(const int32_t *cnt, int table, int32_t *tile_sums)
+{
+    __shared__ int red[8];
+    const int b0 = blockIdx.x * kScanTile;
+    int s = 0;
+    for (int t = threadIdx.x; t < kScanTile; t += 256)
+        if (b0 + t < table) s += cnt[b0 + t];
+    int total;
+    block_exclusive_scan(s, red, &total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int32_t *tile_sums, int ntiles)
 {
     __shared__ int red[32];
-    const int chunk = table / 1024;
-    const int b0 = threadIdx.x * chunk;
-    int s = 0;
-    for (int k = 0; k < chunk; ++k) s += cnt[b0 + k];
+    int v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = threadIdx.x * 4 + k;
+        v[k] = i < ntiles ? tile_sums[i] : 0;
+        s += v[k];
+    }
     int total;
     int o = block_exclusive_scan(s, red, &total);
-    for (int k = 0; k < chunk; ++k) {
-        off[b0 + k] = o;
-        o += cnt[b0 + k];
-        cnt[b0 + k] = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = threadIdx.x * 4 + k;
+        if (i < ntiles) tile_sums[i] = o;
+        o += v[k];
     }
-    if (threadIdx.x == 1023) off[table] = total;
+}
+
+__global__ void __launch_bounds__(256) k_scan_write(int32_t *cnt, int32_t *off, int table, const int32_t *tile_sums)
+{
+    __shared__ int red[8];
+    const int b0 = blockIdx.x * kScanTile + threadIdx.x * 16;
+    int v[16], s = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        v[k] = b0 + k < table ? cnt[b0 + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int o = tile_sums[blockIdx.x] + block_exclusive_scan(s, red, &total);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (b0 + k < table) {
+            off[b0 + k] = o;
+            cnt[b0 + k] = 0;
+        }
+        o += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 255) off[table] = o;
 }
 
 __global__ void k_hash_fill(const float4 *pos, const int32_t *count, float inv_cell, uint32_t mask,
-                            const int32_t *off, int32_t *cnt, int32_t *ent)
+                            const int32_t *off, int32_t *cnt, float4 *pts)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= *count) return;
     const float4 p = pos[i];
     const uint32_t h = cell_hash(cell_of(p.x, inv_cell), cell_of(p.y, inv_cell), cell_of(p.z, inv_cell), mask);
-    ent[off[h] + atomicAdd(&cnt[h], 1)] = i;
-}
-
-// ------------------------------------------------------------------ correspondence
-struct Match {
-    int j;
-    float m, d2;
-};
-
-// The k_match nearest map Gaussians of x within r (by (d2, index)), then the smallest
-// point-to-surface distance among them (ties by d2, then index).
-__device__ __forceinline__ Match find_match(float3 x, const float4 *__restrict__ mpos, const float4 *__restrict__ mnorm,
-                            const Grid &g, float r2, int kmatch)
-{
-    float cd[kKMatchMax];
-    int cj[kKMatchMax];
-#pragma unroll
-    for (int k = 0; k < kKMatchMax; ++k) {
-        cd[k] = FLT_MAX;
-        cj[k] = INT_MAX;
-    }
-    float wd = FLT_MAX;
-    int wj = INT_MAX;
-    const int ix = cell_of(x.x, g.inv_cell), iy = cell_of(x.y, g.inv_cell), iz = cell_of(x.z, g.inv_cell);
-#pragma unroll 1
-    for (int c = 0; c < 27; ++c) {
-        const uint32_t h = cell_hash(ix + c % 3 - 1, iy + (c / 3) % 3 - 1, iz + c / 9 - 1, g.mask);
-        const int e1 = g.off[h + 1];
-#pragma unroll 1
-        for (int e = g.off[h]; e < e1; ++e) {
-            const int j = g.ent[e];
-            const float4 b = mpos[j];
-            const float d2 = sqdist(b.x, b.y, b.z, x.x, x.y, x.z);
-            if (d2 > r2 || d2 > wd || (d2 == wd && j >= wj)) continue;
-            bool dup = false;
-#pragma unroll
-            for (int k = 0; k < kKMatchMax; ++k) dup |= cj[k] == j;
-            if (dup) continue;                            // two cells hashed to one bucket
-            float td = d2;
-            int tj = j;
-#pragma unroll
-            for (int k = 0; k < kKMatchMax; ++k) {
-                if (k < kmatch && (td < cd[k] || (td == cd[k] && tj < cj[k]))) {
-                    const float sd = cd[k];
-                    const int sj = cj[k];
-                    cd[k] = td;
-                    cj[k] = tj;
-                    td = sd;
-                    tj = sj;
-                }
-                if (k == kmatch - 1) {
-                    wd = cd[k];
-                    wj = cj[k];
-                }
-            }
-        }
-    }
-    Match best;
-    best.j = -1;
-    best.m = FLT_MAX;
-    best.d2 = FLT_MAX;
-#pragma unroll
-    for (int k = 0; k < kKMatchMax; ++k) {
-        if (k >= kmatch || cj[k] == INT_MAX) continue;
-        const int j = cj[k];
-        const float4 b = mpos[j], n = mnorm[j];
-        const float dx = __fsub_rn(b.x, x.x), dy = __fsub_rn(b.y, x.y), dz = __fsub_rn(b.z, x.z);
-        const float m = fabsf(__fadd_rn(__fadd_rn(__fmul_rn(n.x, dx), __fmul_rn(n.y, dy)), __fmul_rn(n.z, dz)));
-        const float d2 = cd[k];
-        if (m < best.m || (m == best.m && (d2 < best.d2 || (d2 == best.d2 && j < best.j)))) {
-            best.j = j;
-            best.m = m;
-            best.d2 = d2;
-        }
-    }
-    return best;
+    pts[off[h] + atomicAdd(&cnt[h], 1)] = make_float4(p.x, p.y, p.z, __int_as_float(i));
 }
 
 // ------------------------------------------------------------------ Gauss-Newton step
@@ -543,74 +651,119 @@ struct StepArgs {
     const float4 *spos, *scov;
     const int32_t *scount;
     const float4 *mpos, *mcov, *mnorm;
+    const int32_t *mcount;
     Grid grid;
-    float r2;
+    float r_max;
     int32_t kmatch;
     int32_t system;          // accumulate the Gauss-Newton system
     int32_t use_state;       // pose from the state (tracking) instead of `pose`
     GicpState *state;
     Pose12 pose;
     int32_t *idx_out;
-    float *partial;          // [blocks][32]
+    float *partial;          // [gridDim.x][32]
 };
 
+constexpr int kStepTeams = kStepThreads / kTeam;         // source points per block and round
+
+// The contribution of one correspondence to the Gauss-Newton system (H upper triangle,
+// g = J^T M e, cost, count) in FP32.
+__device__ __forceinline__ void gn_terms(const float *P, float3 x, float4 b, float4 cb0, float4 cb1, float4 ca0,
+                                         float4 ca1, float (&acc)[kSys])
+{
+    const float Ca[3][3] = {{ca0.x, ca0.y, ca0.z}, {ca0.y, ca0.w, ca1.x}, {ca0.z, ca1.x, ca1.y}};
+    const float R[3][3] = {{P[0], P[1], P[2]}, {P[4], P[5], P[6]}, {P[8], P[9], P[10]}};
+    float RC[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) RC[r][c] = R[r][0] * Ca[0][c] + R[r][1] * Ca[1][c] + R[r][2] * Ca[2][c];
+    float S[6];
+    const int rr[6] = {0, 0, 0, 1, 1, 2}, cc[6] = {0, 1, 2, 1, 2, 2};
+    const float cb[6] = {cb0.x, cb0.y, cb0.z, cb0.w, cb1.x, cb1.y};
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+        S[e] = cb[e] + RC[rr[e]][0] * R[cc[e]][0] + RC[rr[e]][1] * R[cc[e]][1] + RC[rr[e]][2] * R[cc[e]][2];
+    float Mi[6];
+    inv_sym3(S, Mi);
+    const float M[3][3] = {{Mi[0], Mi[1], Mi[2]}, {Mi[1], Mi[3], Mi[4]}, {Mi[2], Mi[4], Mi[5]}};
+    const float e3[3] = {b.x - x.x, b.y - x.y, b.z - x.z};
+    // J = [[x]_x, -I]
+    const float J[3][6] = {{0.f, -x.z, x.y, -1.f, 0.f, 0.f}, {x.z, 0.f, -x.x, 0.f, -1.f, 0.f},
+                           {-x.y, x.x, 0.f, 0.f, 0.f, -1.f}};
+    float MJ[3][6];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) MJ[r][c] = M[r][0] * J[0][c] + M[r][1] * J[1][c] + M[r][2] * J[2][c];
+    int t = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c) acc[t++] += J[0][r] * MJ[0][c] + J[1][r] * MJ[1][c] + J[2][r] * MJ[2][c];
+    float Me[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) Me[r] = M[r][0] * e3[0] + M[r][1] * e3[1] + M[r][2] * e3[2];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[21 + c] += J[0][c] * Me[0] + J[1][c] * Me[1] + J[2][c] * Me[2];
+    acc[27] += e3[0] * Me[0] + e3[1] * Me[1] + e3[2] * Me[2];
+    acc[28] += 1.f;
+}
+
+// One team per source point (grid-stride over the points): the k_match nearest map
+// Gaussians within r_max by a ring search of the map's grid (cells of r_max / 3, at most
+// 3 rings), the smallest point-to-surface distance among them (ties by squared
+// distance, then index), and that correspondence's Gauss-Newton terms, reduced per block.
 __global__ void __launch_bounds__(kStepThreads) k_gicp_step(const __grid_constant__ StepArgs a)
 {
     __shared__ float red[kStepThreads / 32][kSys + 3];
+    __shared__ float s_d[kStepTeams][kTeam * kKMatchMax];
+    __shared__ int s_j[kStepTeams][kTeam * kKMatchMax];
+    __shared__ int s_out[kStepTeams][kKMatchMax];
+    __shared__ float s_outd[kStepTeams][kKMatchMax];
     if (a.use_state && a.state->done) return;                  // uniform across the grid
     float P[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) P[k] = a.use_state ? a.state->posef[k] : a.pose.p[k];
-    const int i = blockIdx.x * kStepThreads + threadIdx.x;
+    const int team = threadIdx.x / kTeam, tl = threadIdx.x & (kTeam - 1);
+    const int n = *a.scount, nm = *a.mcount;
+    const unsigned m = team_mask();
     float acc[kSys];
 #pragma unroll
     for (int k = 0; k < kSys; ++k) acc[k] = 0.f;
-    if (i < *a.scount) {
+#pragma unroll 1
+    for (int base = blockIdx.x * kStepTeams; base < n; base += gridDim.x * kStepTeams) {
+        const int i = base + team;
+        if (i >= n) continue;                                  // whole team
         const float3 x = transform(P, a.spos[i]);
-        const Match mt = find_match(x, a.mpos, a.mnorm, a.grid, a.r2, a.kmatch);
-        if (a.idx_out) a.idx_out[i] = mt.j;
-        if (a.system && mt.j >= 0) {
-            const float4 b = a.mpos[mt.j];
-            const float4 cb0 = a.mcov[2 * mt.j], cb1 = a.mcov[2 * mt.j + 1];
-            const float4 ca0 = a.scov[2 * i], ca1 = a.scov[2 * i + 1];
-            const float Ca[3][3] = {{ca0.x, ca0.y, ca0.z}, {ca0.y, ca0.w, ca1.x}, {ca0.z, ca1.x, ca1.y}};
-            const float R[3][3] = {{P[0], P[1], P[2]}, {P[4], P[5], P[6]}, {P[8], P[9], P[10]}};
-            float RC[3][3];
+        const int found = team_nearest<kKMatchMax>(a.grid, x, a.kmatch, a.r_max, 3, a.mpos, nm, s_d[team], s_j[team],
+                                                  s_out[team], s_outd[team]);
+        // point-to-surface choice among the found candidates (lane k takes candidate k)
+        float bm = FLT_MAX, bd2 = FLT_MAX;
+        int bj = INT_MAX;
+        if (tl < found) {
+            const int j = s_out[team][tl];
+            const float4 b = a.mpos[j], nr = a.mnorm[j];
+            const float dx = __fsub_rn(b.x, x.x), dy = __fsub_rn(b.y, x.y), dz = __fsub_rn(b.z, x.z);
+            bm = fabsf(__fadd_rn(__fadd_rn(__fmul_rn(nr.x, dx), __fmul_rn(nr.y, dy)), __fmul_rn(nr.z, dz)));
+            bd2 = s_outd[team][tl];
+            bj = j;
+        }
 #pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) RC[r][c] = R[r][0] * Ca[0][c] + R[r][1] * Ca[1][c] + R[r][2] * Ca[2][c];
-            float S[6];
-            const int rr[6] = {0, 0, 0, 1, 1, 2}, cc[6] = {0, 1, 2, 1, 2, 2};
-            const float cb[6] = {cb0.x, cb0.y, cb0.z, cb0.w, cb1.x, cb1.y};
-#pragma unroll
-            for (int e = 0; e < 6; ++e)
-                S[e] = cb[e] + RC[rr[e]][0] * R[cc[e]][0] + RC[rr[e]][1] * R[cc[e]][1] + RC[rr[e]][2] * R[cc[e]][2];
-            float Mi[6];
-            inv_sym3(S, Mi);
-            const float M[3][3] = {{Mi[0], Mi[1], Mi[2]}, {Mi[1], Mi[3], Mi[4]}, {Mi[2], Mi[4], Mi[5]}};
-            const float e3[3] = {b.x - x.x, b.y - x.y, b.z - x.z};
-            // J = [[x]_x, -I]
-            const float J[3][6] = {{0.f, -x.z, x.y, -1.f, 0.f, 0.f},
-                                   {x.z, 0.f, -x.x, 0.f, -1.f, 0.f},
-                                   {-x.y, x.x, 0.f, 0.f, 0.f, -1.f}};
-            float MJ[3][6];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 6; ++c) MJ[r][c] = M[r][0] * J[0][c] + M[r][1] * J[1][c] + M[r][2] * J[2][c];
-            int t = 0;
-#pragma unroll
-            for (int r = 0; r < 6; ++r)
-#pragma unroll
-                for (int c = r; c < 6; ++c) acc[t++] = J[0][r] * MJ[0][c] + J[1][r] * MJ[1][c] + J[2][r] * MJ[2][c];
-            float Me[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) Me[r] = M[r][0] * e3[0] + M[r][1] * e3[1] + M[r][2] * e3[2];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) acc[21 + c] = J[0][c] * Me[0] + J[1][c] * Me[1] + J[2][c] * Me[2];
-            acc[27] = e3[0] * Me[0] + e3[1] * Me[1] + e3[2] * Me[2];
-            acc[28] = 1.f;
+        for (int o = kTeam / 2; o > 0; o >>= 1) {
+            const float om = __shfl_xor_sync(m, bm, o, kTeam), od = __shfl_xor_sync(m, bd2, o, kTeam);
+            const int oj = __shfl_xor_sync(m, bj, o, kTeam);
+            if (om < bm || (om == bm && (od < bd2 || (od == bd2 && oj < bj)))) {
+                bm = om;
+                bd2 = od;
+                bj = oj;
+            }
+        }
+        const int jbest = found > 0 ? bj : -1;
+        if (tl == 0) {
+            if (a.idx_out) a.idx_out[i] = jbest;
+            if (a.system && jbest >= 0)
+                gn_terms(P, x, a.mpos[jbest], a.mcov[2 * jbest], a.mcov[2 * jbest + 1], a.scov[2 * i],
+                         a.scov[2 * i + 1], acc);
         }
     }
     if (!a.system) return;
@@ -770,24 +923,33 @@ struct InsArgs {
     int32_t *mcount;
     int32_t mcap;
     Grid grid;
-    float d2ov;
+    float d_ov;
     GicpState *state;
     int32_t *flags;
     int32_t *blk;
 };
 
-__device__ __forceinline__ bool overlaps(float3 x, const float4 *mpos, const Grid &g, float d2ov)
+__device__ __forceinline__ bool overlaps(float3 x, const Grid &g, float d_ov)
 {
+    const float d2ov = d_ov * d_ov;
     const int ix = cell_of(x.x, g.inv_cell), iy = cell_of(x.y, g.inv_cell), iz = cell_of(x.z, g.inv_cell);
+    // cells of a third of max(r_max, d_ov) >= d_ov / 3: the three rings reach d_ov
 #pragma unroll 1
-    for (int c = 0; c < 27; ++c) {
-        const uint32_t h = cell_hash(ix + c % 3 - 1, iy + (c / 3) % 3 - 1, iz + c / 9 - 1, g.mask);
-        const int e1 = g.off[h + 1];
+    for (int r = 0; r <= 3; ++r) {
+        const int side = 2 * r + 1, ncube = side * side * side;
 #pragma unroll 1
-        for (int e = g.off[h]; e < e1; ++e) {
-            const float4 b = mpos[g.ent[e]];
-            if (sqdist(b.x, b.y, b.z, x.x, x.y, x.z) <= d2ov) return true;
+        for (int c = 0; c < ncube; ++c) {
+            const int dx = c % side - r, dy = (c / side) % side - r, dz = c / (side * side) - r;
+            if (max(abs(dx), max(abs(dy), abs(dz))) != r) continue;
+            const uint32_t h = cell_hash(ix + dx, iy + dy, iz + dz, g.mask);
+            const int e1 = g.off[h + 1];
+#pragma unroll 1
+            for (int e = g.off[h]; e < e1; ++e) {
+                const float4 b = g.pts[e];
+                if (sqdist(b.x, b.y, b.z, x.x, x.y, x.z) <= d2ov) return true;
+            }
         }
+        if ((float)r * g.cell * (1.f - 1e-4f) >= d_ov) break;
     }
     return false;
 }
@@ -798,7 +960,7 @@ __global__ void __launch_bounds__(256) k_insert_flag(const __grid_constant__ Ins
     bool keep = false;
     if (i < *a.scount) {
         const float3 x = transform(a.state->posef, a.spos[i]);
-        keep = *a.mcount == 0 || !overlaps(x, a.mpos, a.grid, a.d2ov);
+        keep = *a.mcount == 0 || !overlaps(x, a.grid, a.d_ov);
         a.flags[i] = keep ? 1 : 0;
     }
     const int n = __syncthreads_count(keep);
@@ -867,14 +1029,15 @@ sgad_status check_params(const sgad_gicp_params *p)
     if (!p) return fail("sgad_gicp: NULL params");
     if (p->stride < 1 || p->k_cov < 3 || p->k_cov > 32 || p->k_match < 1 || p->k_match > kKMatchMax ||
         p->max_iters < 1 || p->max_iters > 100 || !(p->r_max > 0.f) || !(p->d_overlap >= 0.f) || !(p->tol >= 0.f) ||
-        !(p->eps > 0.f && p->eps <= 1.f) || !std::isfinite(p->r_max) || !std::isfinite(p->d_overlap))
+        !(p->eps > 0.f && p->eps <= 1.f) || !std::isfinite(p->r_max) || !std::isfinite(p->d_overlap) ||
+        p->src_capacity < 1 || p->map_capacity < 1 || p->src_capacity > (1 << 24) || p->map_capacity > (1 << 24))
         return fail("sgad_gicp: parameter out of range");
     return SGAD_OK;
 }
 
-sgad_status check_set(const sgad_gaussian_set *s, const char *what)
+sgad_status check_set(const sgad_gaussian_set *s, int32_t max_capacity, const char *what)
 {
-    if (!s || !s->pos || !s->cov || !s->normal || !s->count || s->capacity < 1 || s->capacity > (1 << 26))
+    if (!s || !s->pos || !s->cov || !s->normal || !s->count || s->capacity < 1 || s->capacity > max_capacity)
         return fail(what);
     if (!aligned(s->pos, 16) || !aligned(s->cov, 16) || !aligned(s->normal, 16) || !aligned(s->count, 4))
         return fail(what);
@@ -891,14 +1054,17 @@ sgad_status check_ws(void *ws, size_t bytes, size_t need)
 template <typename T>
 T *at(void *ws, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(ws) + off); }
 
-float cell_size(const sgad_gicp_params *p) { return fmaxf(p->r_max, p->d_overlap) * 1.001f; }
+// Map grid cells of a third of the larger search radius: correspondence and overlap
+// searches visit rings of cells until their result is proven (at most 3 rings).
+float cell_size(const sgad_gicp_params *p) { return fmaxf(p->r_max, p->d_overlap) * (1.001f / 3.f); }
 
 Grid grid_of(const sgad_gicp_params *p, void *ws, const GLayout &L)
 {
     Grid g;
     g.off = at<int32_t>(ws, L.hash_off);
-    g.ent = at<int32_t>(ws, L.hash_ent);
-    g.inv_cell = 1.f / cell_size(p);
+    g.pts = at<float4>(ws, L.hash_pts);
+    g.cell = cell_size(p);
+    g.inv_cell = 1.f / g.cell;
     g.mask = (uint32_t)L.table - 1u;
     return g;
 }
@@ -909,19 +1075,30 @@ sgad_status launched(const char *what)
     return e == cudaSuccess ? SGAD_OK : report_error(SGAD_ERR_CUDA, what);
 }
 
+// Counting sort of a set's indices by the hash of their cells: counts, parallel scan,
+// fill (entries within a bucket in arbitrary order; queries do not depend on it).
+sgad_status hash_build(const float4 *pos, const int32_t *count, int32_t capacity, float inv_cell, int32_t table,
+                       int32_t *cnt, int32_t *off, float4 *pts, int32_t *tile_sums, cudaStream_t st)
+{
+    if (cudaMemsetAsync(cnt, 0, (size_t)table * sizeof(int32_t), st) != cudaSuccess)
+        return report_error(SGAD_ERR_CUDA, "sgad_gicp: memset failed");
+    const uint32_t mask = (uint32_t)table - 1u;
+    const int blocks = (capacity + 255) / 256;
+    const int tiles = (table + kScanTile - 1) / kScanTile;
+    k_hash_count<<<blocks, 256, 0, st>>>(pos, count, inv_cell, mask, cnt);
+    k_scan_tiles<<<tiles, 256, 0, st>>>(cnt, table, tile_sums);
+    k_scan_top<<<1, 1024, 0, st>>>(tile_sums, tiles);
+    k_scan_write<<<tiles, 256, 0, st>>>(cnt, off, table, tile_sums);
+    k_hash_fill<<<blocks, 256, 0, st>>>(pos, count, inv_cell, mask, off, cnt, pts);
+    return launched("sgad_gicp: index launch failed");
+}
+
 sgad_status build_index(const sgad_gicp_params *p, const sgad_gaussian_set *map, void *ws, const GLayout &L,
                         cudaStream_t st)
 {
-    int32_t *cnt = at<int32_t>(ws, L.hash_cnt);
-    if (cudaMemsetAsync(cnt, 0, (size_t)L.table * sizeof(int32_t), st) != cudaSuccess)
-        return report_error(SGAD_ERR_CUDA, "sgad_gicp_index: memset failed");
-    const Grid g = grid_of(p, ws, L);
-    const int blocks = (map->capacity + 255) / 256;
-    const float4 *pos = reinterpret_cast<const float4 *>(map->pos);
-    k_hash_count<<<blocks, 256, 0, st>>>(pos, map->count, g.inv_cell, g.mask, cnt);
-    k_hash_scan<<<1, 1024, 0, st>>>(cnt, at<int32_t>(ws, L.hash_off), L.table);
-    k_hash_fill<<<blocks, 256, 0, st>>>(pos, map->count, g.inv_cell, g.mask, g.off, cnt, at<int32_t>(ws, L.hash_ent));
-    return launched("sgad_gicp_index: launch failed");
+    return hash_build(reinterpret_cast<const float4 *>(map->pos), map->count, map->capacity, 1.f / cell_size(p),
+                      L.table, at<int32_t>(ws, L.hash_cnt), at<int32_t>(ws, L.hash_off), at<float4>(ws, L.hash_pts),
+                      at<int32_t>(ws, L.tile_sums), st);
 }
 
 StepArgs step_args(const sgad_gicp_params *p, const sgad_gaussian_set *src, const sgad_gaussian_set *map, void *ws,
@@ -935,8 +1112,9 @@ StepArgs step_args(const sgad_gicp_params *p, const sgad_gaussian_set *src, cons
     a.mpos = reinterpret_cast<const float4 *>(map->pos);
     a.mcov = reinterpret_cast<const float4 *>(map->cov);
     a.mnorm = reinterpret_cast<const float4 *>(map->normal);
+    a.mcount = map->count;
     a.grid = grid_of(p, ws, L);
-    a.r2 = p->r_max * p->r_max;
+    a.r_max = p->r_max;
     a.kmatch = p->k_match;
     a.state = at<GicpState>(ws, L.state);
     a.partial = at<float>(ws, L.partial);
@@ -956,17 +1134,17 @@ extern "C" sgad_status sgad_gicp_default_params(sgad_gicp_params *out)
     out->d_overlap = 0.02f;
     out->tol = 1e-6f;
     out->eps = 1e-3f;
+    out->src_capacity = 1 << 16;
+    out->map_capacity = 1 << 20;
     return SGAD_OK;
 }
 
-extern "C" sgad_status sgad_gicp_workspace_size(const sgad_gicp_params *p, int32_t src_capacity,
-                                                int32_t map_capacity, size_t *bytes)
+extern "C" sgad_status sgad_gicp_workspace_size(const sgad_gicp_params *p, size_t *bytes)
 {
     sgad_status s = check_params(p);
     if (s) return s;
-    if (!bytes || src_capacity < 1 || map_capacity < 1 || src_capacity > (1 << 26) || map_capacity > (1 << 26))
-        return fail("sgad_gicp_workspace_size: bad capacity");
-    *bytes = glayout(src_capacity, map_capacity).total;
+    if (!bytes) return fail("sgad_gicp_workspace_size: NULL");
+    *bytes = glayout(*p).total;
     return SGAD_OK;
 }
 
@@ -976,11 +1154,11 @@ extern "C" sgad_status sgad_gicp_frame(const sgad_gicp_params *p, const sgad_cam
 {
     sgad_status s = check_params(p);
     if (s) return s;
-    if ((s = check_set(out, "sgad_gicp_frame: bad output set"))) return s;
+    if ((s = check_set(out, p->src_capacity, "sgad_gicp_frame: bad output set"))) return s;
     if (!cam || !depth || cam->width < 1 || cam->height < 1 || !(cam->fx > 0.f) || !(cam->fy > 0.f))
         return fail("sgad_gicp_frame: bad camera or depth");
-    const GLayout L = glayout(out->capacity, 1);
-    if ((s = check_ws(workspace, ws_bytes, L.sel_counts + (size_t)kMaxSelBlocks * sizeof(int32_t)))) return s;
+    const GLayout L = glayout(*p);
+    if ((s = check_ws(workspace, ws_bytes, L.total))) return s;
     SelArgs a;
     a.depth = depth;
     a.W = cam->width;
@@ -1004,17 +1182,30 @@ extern "C" sgad_status sgad_gicp_frame(const sgad_gicp_params *p, const sgad_cam
     const int nb = (int)((ncells + kSelBlock - 1) / kSelBlock);
     k_select_count<<<nb, 256, 0, st>>>(a);
     k_select_write<<<nb, 256, 0, st>>>(a);
-    const int sb = (out->capacity + 63) / 64;
     const float4 *pos = reinterpret_cast<const float4 *>(out->pos);
+    // the points' own hash grid for the neighbour search; its cells are about twice the
+    // selection spacing at 2 m (a performance choice only: the search proves its result)
+    const float cell = fmaxf(5e-3f, 2.f * (float)p->stride * 2.f / cam->fx);
+    Grid g;
+    g.off = at<int32_t>(workspace, L.knn_off);
+    g.pts = at<float4>(workspace, L.knn_pts);
+    g.cell = cell;
+    g.inv_cell = 1.f / cell;
+    g.mask = (uint32_t)L.knn_table - 1u;
+    if ((s = hash_build(pos, out->count, out->capacity, g.inv_cell, L.knn_table, at<int32_t>(workspace, L.knn_cnt),
+                        at<int32_t>(workspace, L.knn_off), at<float4>(workspace, L.knn_pts),
+                        at<int32_t>(workspace, L.tile_sums), st)))
+        return s;
+    const int sb = (out->capacity + (128 / kTeam) - 1) / (128 / kTeam);
     float4 *cov = reinterpret_cast<float4 *>(out->cov), *nrm = reinterpret_cast<float4 *>(out->normal);
     if (p->k_cov <= 8)
-        k_shape<8><<<sb, 64, 0, st>>>(pos, out->count, p->k_cov, p->eps, cov, nrm, knn_out);
+        k_shape<8><<<sb, 128, 0, st>>>(pos, out->count, p->k_cov, p->eps, g, cov, nrm, knn_out);
     else if (p->k_cov <= 16)
-        k_shape<16><<<sb, 64, 0, st>>>(pos, out->count, p->k_cov, p->eps, cov, nrm, knn_out);
+        k_shape<16><<<sb, 128, 0, st>>>(pos, out->count, p->k_cov, p->eps, g, cov, nrm, knn_out);
     else if (p->k_cov <= 24)
-        k_shape<24><<<sb, 64, 0, st>>>(pos, out->count, p->k_cov, p->eps, cov, nrm, knn_out);
+        k_shape<24><<<sb, 128, 0, st>>>(pos, out->count, p->k_cov, p->eps, g, cov, nrm, knn_out);
     else
-        k_shape<32><<<sb, 64, 0, st>>>(pos, out->count, p->k_cov, p->eps, cov, nrm, knn_out);
+        k_shape<32><<<sb, 128, 0, st>>>(pos, out->count, p->k_cov, p->eps, g, cov, nrm, knn_out);
     return launched("sgad_gicp_frame: launch failed");
 }
 
@@ -1023,9 +1214,9 @@ extern "C" sgad_status sgad_gicp_index(const sgad_gicp_params *p, const sgad_gau
 {
     sgad_status s = check_params(p);
     if (s) return s;
-    if ((s = check_set(map, "sgad_gicp_index: bad map set"))) return s;
-    const GLayout L = glayout(1, map->capacity);
-    if ((s = check_ws(workspace, ws_bytes, L.partial))) return s;
+    if ((s = check_set(map, p->map_capacity, "sgad_gicp_index: bad map set"))) return s;
+    const GLayout L = glayout(*p);
+    if ((s = check_ws(workspace, ws_bytes, L.total))) return s;
     return build_index(p, map, workspace, L, static_cast<cudaStream_t>(stream));
 }
 
@@ -1035,9 +1226,9 @@ sgad_status pair_checks(const sgad_gicp_params *p, const sgad_gaussian_set *src,
 {
     sgad_status s = check_params(p);
     if (s) return s;
-    if ((s = check_set(src, "sgad_gicp: bad source set"))) return s;
-    if ((s = check_set(map, "sgad_gicp: bad map set"))) return s;
-    *L = glayout(src->capacity, map->capacity);
+    if ((s = check_set(src, p->src_capacity, "sgad_gicp: bad source set"))) return s;
+    if ((s = check_set(map, p->map_capacity, "sgad_gicp: bad map set"))) return s;
+    *L = glayout(*p);
     return check_ws(ws, bytes, L->total);
 }
 
@@ -1060,7 +1251,7 @@ extern "C" sgad_status sgad_gicp_correspond(const sgad_gicp_params *p, const sga
     StepArgs a = step_args(p, src, map, workspace, L);
     std::memcpy(a.pose.p, pose, sizeof(a.pose.p));
     a.idx_out = idx_out;
-    k_gicp_step<<<L.max_blocks, kStepThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    k_gicp_step<<<L.step_blocks, kStepThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
     return launched("sgad_gicp_correspond: launch failed");
 }
 
@@ -1076,8 +1267,8 @@ extern "C" sgad_status sgad_gicp_linearize(const sgad_gicp_params *p, const sgad
     std::memcpy(a.pose.p, pose, sizeof(a.pose.p));
     a.system = 1;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    k_gicp_step<<<L.max_blocks, kStepThreads, 0, st>>>(a);
-    k_gicp_sum<<<1, 32, 0, st>>>(a.partial, L.max_blocks, system_out);
+    k_gicp_step<<<L.step_blocks, kStepThreads, 0, st>>>(a);
+    k_gicp_sum<<<1, 32, 0, st>>>(a.partial, L.step_blocks, system_out);
     return launched("sgad_gicp_linearize: launch failed");
 }
 
@@ -1112,8 +1303,8 @@ extern "C" sgad_status sgad_gicp_track(const sgad_gicp_params *p, const sgad_gau
     a.use_state = 1;
     k_gicp_init<<<1, 1, 0, st>>>(a.state, p0, p->max_iters, p->tol, 0);
     for (int it = 0; it < p->max_iters; ++it) {
-        k_gicp_step<<<L.max_blocks, kStepThreads, 0, st>>>(a);
-        k_gicp_solve<<<1, 32, 0, st>>>(a.state, a.partial, L.max_blocks);
+        k_gicp_step<<<L.step_blocks, kStepThreads, 0, st>>>(a);
+        k_gicp_solve<<<1, 32, 0, st>>>(a.state, a.partial, L.step_blocks);
     }
     return launched("sgad_gicp_track: launch failed");
 }
@@ -1136,7 +1327,7 @@ extern "C" sgad_status sgad_gicp_insert(const sgad_gicp_params *p, const sgad_ga
     a.mcount = map->count;
     a.mcap = map->capacity;
     a.grid = grid_of(p, workspace, L);
-    a.d2ov = p->d_overlap * p->d_overlap;
+    a.d_ov = p->d_overlap;
     a.state = at<GicpState>(workspace, L.state);
     a.flags = at<int32_t>(workspace, L.ins_flags);
     a.blk = at<int32_t>(workspace, L.ins_counts);

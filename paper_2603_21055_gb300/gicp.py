@@ -72,9 +72,10 @@ class GicpTracker:
         self.p = params or B.sgad_gicp_default_params()
         for k, v in overrides.items():
             setattr(self.p, k, v)
+        self.p.src_capacity, self.p.map_capacity = int(src_capacity), int(map_capacity)
         self.src = GaussianSet(src_capacity)
         self.map = GaussianSet(map_capacity)
-        self.ws_bytes = B.sgad_gicp_workspace_size(self.p, src_capacity, map_capacity)
+        self.ws_bytes = B.sgad_gicp_workspace_size(self.p)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
         self.pix = torch.empty(src_capacity, dtype=torch.int32, device="cuda")
 

@@ -181,18 +181,20 @@ def test_gicp_params_workspace_and_validation_on_the_host():
     p = B.sgad_gicp_default_params()
     assert (p.stride, p.k_cov, p.k_match, p.max_iters) == (10, 10, 5, 30)
     assert abs(p.r_max - 0.1) < 1e-7 and abs(p.d_overlap - 0.02) < 1e-7
-    n1 = B.sgad_gicp_workspace_size(p, 1000, 5000)
-    n2 = B.sgad_gicp_workspace_size(p, 2000, 5000)
-    n3 = B.sgad_gicp_workspace_size(p, 1000, 10000)
-    assert n2 > n1 and n3 > n1
+    assert (p.src_capacity, p.map_capacity) == (1 << 16, 1 << 20)
+    sizes = []
+    for src, mp in ((1000, 5000), (2000, 5000), (1000, 10000)):
+        p.src_capacity, p.map_capacity = src, mp
+        sizes.append(B.sgad_gicp_workspace_size(p))
+    assert sizes[1] > sizes[0] and sizes[2] > sizes[0]
     lib = B.load()
     n = C.c_size_t()
-    assert lib.sgad_gicp_workspace_size(C.byref(p), 0, 10, C.byref(n)) == B.SGAD_ERR_INVALID_ARG
     for field, bad in (("stride", 0), ("k_cov", 2), ("k_cov", 33), ("k_match", 9), ("max_iters", 0),
-                       ("r_max", 0.0), ("eps", 0.0), ("eps", 2.0)):
+                       ("r_max", 0.0), ("eps", 0.0), ("eps", 2.0), ("src_capacity", 0), ("map_capacity", 1 << 25)):
         q = B.sgad_gicp_default_params()
         setattr(q, field, bad)
-        assert lib.sgad_gicp_workspace_size(C.byref(q), 10, 10, C.byref(n)) == B.SGAD_ERR_INVALID_ARG, field
+        assert lib.sgad_gicp_workspace_size(C.byref(q), C.byref(n)) == B.SGAD_ERR_INVALID_ARG, field
+    p = B.sgad_gicp_default_params()
     s = B.sgad_gaussian_set(4096, 4096, 4096, 4096, 0)               # capacity 0
     assert lib.sgad_gicp_index(C.byref(p), C.byref(s), None, 0, None) == B.SGAD_ERR_INVALID_ARG
     s.capacity = 10
@@ -201,6 +203,8 @@ def test_gicp_params_workspace_and_validation_on_the_host():
     assert lib.sgad_gicp_index(C.byref(p), C.byref(s), 4096, 1 << 20, None) == B.SGAD_ERR_INVALID_ARG
     s.pos = 4096
     assert lib.sgad_gicp_index(C.byref(p), C.byref(s), 4096, 16, None) == B.SGAD_ERR_WORKSPACE_TOO_SMALL
+    s.capacity = p.map_capacity + 1                                  # above the workspace's capacity
+    assert lib.sgad_gicp_index(C.byref(p), C.byref(s), 4096, 1 << 30, None) == B.SGAD_ERR_INVALID_ARG
     cam = B.sgad_camera(0, 10, 100.0, 100.0, 0.0, 0.0)
     assert lib.sgad_gicp_frame(C.byref(p), C.byref(cam), 4096, C.byref(s), None, None, 4096, 1 << 20,
                                None) == B.SGAD_ERR_INVALID_ARG
