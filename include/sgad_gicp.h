@@ -115,7 +115,8 @@ sgad_status sgad_gicp_set_pose(const double pose[12], void *workspace, size_t ws
 
 /* GICP of the source set against the map (whose index must be current) from the host
  * initial pose; the estimate stays in the workspace (read by sgad_gicp_result, used by
- * sgad_gicp_insert). 1 + 2 max_iters kernel launches; iterations after convergence exit
+ * sgad_gicp_insert). 1 + max_iters kernel launches (the last block of each iteration
+ * solves and updates the pose); iterations after convergence exit
  * at once. Capturable in a CUDA graph. */
 sgad_status sgad_gicp_track(const sgad_gicp_params *p, const sgad_gaussian_set *src,
                             const sgad_gaussian_set *map, const double pose0[12], void *workspace,

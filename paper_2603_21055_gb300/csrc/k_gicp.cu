@@ -37,6 +37,7 @@ struct GicpState {
     int32_t iters, done, converged, n, status, max_iters;
     float tol;
     int32_t map_old, ins_total;
+    int32_t blocks_done;     // step blocks finished in the current iteration
 };
 
 struct GLayout {
@@ -665,6 +666,9 @@ struct StepArgs {
 
 constexpr int kStepTeams = kStepThreads / kTeam;         // source points per block and round
 
+__device__ void sum_partials(const float *partial, int nblocks, double *sys);
+__device__ void solve_state(GicpState *st, const double *sys);
+
 // The contribution of one correspondence to the Gauss-Newton system (H upper triangle,
 // g = J^T M e, cost, count) in FP32.
 __device__ __forceinline__ void gn_terms(const float *P, float3 x, float4 b, float4 cb0, float4 cb1, float4 ca0,
@@ -782,14 +786,39 @@ __global__ void __launch_bounds__(kStepThreads) k_gicp_step(const __grid_constan
         for (int w = 0; w < kStepThreads / 32; ++w) s += red[w][threadIdx.x];
         a.partial[blockIdx.x * 32 + threadIdx.x] = s;
     }
+    if (!a.use_state) return;
+    // tracking: the last block to finish sums the partials and takes the step
+    __shared__ int s_last;
+    __shared__ double sys[kSys];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.state->blocks_done, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    sum_partials(a.partial, gridDim.x, sys);
+    if (threadIdx.x == 0) {
+        solve_state(a.state, sys);
+        a.state->blocks_done = 0;
+    }
 }
 
-// Sum of the per-block partials in FP64, fixed order: lane k sums value k.
+// Sum of the per-block partials in FP64 in a fixed order (warp w takes rows w, w + nw,
+// ...; the warps' sums are added in warp order), so the result does not depend on
+// scheduling. Partials are read through L2 (written by other blocks of the same grid).
 __device__ void sum_partials(const float *partial, int nblocks, double *sys)
 {
+    __shared__ double part[32][kSys];
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, k = threadIdx.x & 31;
+    if (k < kSys) {
+        double s = 0.0;
+        for (int b = w; b < nblocks; b += nw) s += (double)__ldcg(partial + b * 32 + k);
+        part[w][k] = s;
+    }
+    __syncthreads();
     if (threadIdx.x < kSys) {
         double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += (double)partial[b * 32 + threadIdx.x];
+        for (int q = 0; q < nw; ++q) s += part[q][threadIdx.x];
         sys[threadIdx.x] = s;
     }
     __syncthreads();
@@ -822,14 +851,10 @@ __device__ void exp_so3(const double w[3], double E[3][3])
         }
 }
 
-// One block of 32 threads: the summed system, a Cholesky solve of H xi = -g in FP64 and
-// the pose update (R, t) <- (Exp(omega) R, Exp(omega) t + v).
-__global__ void k_gicp_solve(GicpState *st, const float *partial, int nblocks)
+// One thread: from the summed system, a Cholesky solve of H xi = -g in FP64 and the
+// pose update (R, t) <- (Exp(omega) R, Exp(omega) t + v).
+__device__ void solve_state(GicpState *st, const double *sys)
 {
-    __shared__ double sys[kSys];
-    if (st->done) return;
-    sum_partials(partial, nblocks, sys);
-    if (threadIdx.x != 0) return;
     st->n = (int)sys[28];
     st->cost = sys[27];
     if (sys[28] < 6.0) {
@@ -913,6 +938,7 @@ __global__ void k_gicp_init(GicpState *st, PoseD p0, int max_iters, float tol, i
     st->max_iters = max_iters;
     st->tol = tol;
     st->status &= ~2;
+    st->blocks_done = 0;
 }
 
 // ------------------------------------------------------------------ map update
@@ -1302,9 +1328,9 @@ extern "C" sgad_status sgad_gicp_track(const sgad_gicp_params *p, const sgad_gau
     a.system = 1;
     a.use_state = 1;
     k_gicp_init<<<1, 1, 0, st>>>(a.state, p0, p->max_iters, p->tol, 0);
+    // one launch per iteration: each step's last block solves and updates the pose
     for (int it = 0; it < p->max_iters; ++it) {
         k_gicp_step<<<L.step_blocks, kStepThreads, 0, st>>>(a);
-        k_gicp_solve<<<1, 32, 0, st>>>(a.state, a.partial, L.step_blocks);
     }
     return launched("sgad_gicp_track: launch failed");
 }
