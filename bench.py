@@ -255,8 +255,10 @@ def run_ours(args):
     ssim = ssim_term(mp.sp, mp.views, mp.images, mp.trgb, flush, peaks, peak_src)
     from paper_2603_21055_gb300 import binding as B
     pairs = mp.sp.options.bwd_algorithm == B.SGAD_BWD_PAIRS
+    fp32 = measured_fp32_tflops()
     roof = roofline(stages, stats, scene, peaks, peak_src,
-                    bwd_kernel="k_composite_bwdp" if pairs else "k_composite_bwd")
+                    bwd_kernel="k_composite_bwdp" if pairs else "k_composite_bwd", fp32=fp32)
+    path = path_roofline(stages, stats, scene, peaks, fp32)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -270,6 +272,8 @@ def run_ours(args):
                    "parallelism": "independent keyframe window per GPU" if world > 1 else "1 GPU"},
         "stage_ms": {k: round(v, 4) for k, v in stages.items()},
         "roofline": roof,
+        "path_roofline": path,
+        "fp32_peak": fp32,
         "ssim_term": ssim,
         "e2e": e2e,
         "gpu_launches": mp.launches_per_step() * args.steps,
@@ -353,9 +357,54 @@ def run_e2e(mp, steps, stream, flush):
             "eager_wall_ms_per_step": round(eager_ms, 3)}
 
 
-def roofline(stages, stats, scene, peaks, src, bwd_kernel="k_composite_bwdp"):
+def measured_fp32_tflops(reps: int = 5):
+    """The device's FP32 FMA throughput by the library's own probe (sgad_fma_burn): 8
+    blocks of 256 threads per SM, ~20 ms per launch, 2 warm-up launches, the median of
+    `reps` timed with CUDA events; with the derived peak (152 SMs x 128 lanes x 2 flops x
+    2,070 MHz) beside it."""
+    import torch
+    from paper_2603_21055_gb300 import binding as B
+    blocks, iters = 152 * 8, 20000
+    sink = torch.empty(blocks * 256, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        B.sgad_fma_burn(blocks, iters, sink.data_ptr(), stream.cuda_stream)
+    vals = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        flops = B.sgad_fma_burn(blocks, iters, sink.data_ptr(), stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        vals.append(flops / (a.elapsed_time(b) / 1e3) / 1e12)
+    vals.sort()
+    return {"measured_tflops": round(vals[len(vals) // 2], 2), "derived_tflops": round(152 * 128 * 2 * 2070e6 / 1e12, 2),
+            "probe": "sgad_fma_burn: 1216 blocks x 256 threads x 8 FMA chains, median of %d" % reps}
+
+
+def path_roofline(stages, stats, scene, peaks, fp32):
+    """Roofline of the whole forward + backward path (projection to finalisation, loss and
+    Adam excluded): T_roof = max(B_alg / HBM, F_alg / FP32) against the measured stage
+    time. B_alg per Gaussian: 28 B read forward, 28 B read backward, 24 B of gradients;
+    per key: 12 B written and 12 B read; per view pixel: 20 B of images, 8 B of state
+    written and read, 20 B of image gradients. F_alg: 105 flops per contributing pair."""
+    if not stages:
+        return None
+    t_ms = sum(stages.get(k, 0.0) for k in ("binning", "emit", "sort", "composite_fwd", "composite_bwd", "finalize"))
+    b_alg = 80.0 * scene.n_gaussians + 24.0 * stats["n_keys"] + 56.0 * scene.n_pixels
+    f_alg = (FLOPS_FWD_PAIR + FLOPS_BWD_PAIR) * stats["n_pairs"]
+    t_hbm = b_alg / (float(peaks["hbm_gbs"]) * 1e9) * 1e3
+    t_fp32 = f_alg / (fp32["measured_tflops"] * 1e12) * 1e3
+    t_roof = max(t_hbm, t_fp32)
+    return {"bytes_alg": int(b_alg), "flops_alg": int(f_alg), "t_hbm_ms": round(t_hbm, 4), "t_fp32_ms": round(t_fp32, 4),
+            "bound": "hbm" if t_hbm >= t_fp32 else "alu", "t_roof_ms": round(t_roof, 4), "t_measured_ms": round(t_ms, 4),
+            "frac": round(t_roof / t_ms, 4), "fwd_bwd_mpix_s": round(scene.n_pixels / (t_ms / 1e3) / 1e6, 2)}
+
+
+def roofline(stages, stats, scene, peaks, src, bwd_kernel="k_composite_bwdp", fp32=None):
     """Roofline of the dominant kernel. The compositing kernels are bound by FP32
-    arithmetic (peak = SMs x 128 FP32 lanes x 2 flop x max SM clock); the rest by HBM."""
+    arithmetic (peak = the device's FP32 FMA throughput measured by the library's own
+    probe, else SMs x 128 FP32 lanes x 2 flop x max SM clock); the rest by HBM."""
     if not stages:
         return None
     name = max(stages, key=stages.get)
@@ -371,6 +420,9 @@ def roofline(stages, stats, scene, peaks, src, bwd_kernel="k_composite_bwdp"):
         achieved = work / (ms / 1e3) / 1e12
         bound, unit, peak = "alu", "TFLOP/s", fp32_tflops
         peak_note = "FP32 CUDA-core peak derived: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz
+        if fp32:
+            peak = fp32["measured_tflops"]
+            peak_note = "FP32 FMA throughput of measured (sgad_fma_burn on this GPU)"
     else:
         # algorithmic bytes of the HBM-bound stages
         byts = {"sort": nk * 16, "emit": ng * 40 + nk * 8, "binning": ng * 60,

@@ -338,6 +338,14 @@ sgad_status sgad_ssim_loss_grad(int32_t n_views, const sgad_camera *views,
                                 float weight, float *const *d_rgb, float *loss_accum,
                                 void *workspace, size_t ws_bytes, void *stream);
 
+/* FP32 FMA throughput probe: launches `blocks` blocks of 256 threads, each thread running
+ * 8 independent chains of 16 * iters dependent FMAs, on `stream`, and sets *flops (host)
+ * to the floating-point operations the launch performs (2 per FMA). Timing it with events
+ * on the stream gives the device's measured FP32 peak, the denominator of the
+ * compositing kernels' roofline. sink: device float [blocks * 256], written only in a
+ * case that does not occur (it keeps the arithmetic from being removed). */
+sgad_status sgad_fma_burn(int32_t blocks, int32_t iters, float *sink, double *flops, void *stream);
+
 /* One bias-corrected Adam step (PyTorch convention) on `n` FP32 parameters in place:
  *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
  *   p <- p - lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).

@@ -26,7 +26,7 @@ EXPORTS = ["sgad_default_options", "sgad_create", "sgad_destroy", "sgad_last_err
            "sgad_count_keys", "sgad_forward", "sgad_backward", "sgad_check", "sgad_state", "sgad_read_stats",
            "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_adam_step",
            "sgad_adam_step_multi", "sgad_forward_noalloc", "sgad_autotune", "sgad_get_options",
-           "sgad_ssim_workspace_size", "sgad_ssim_loss_grad",
+           "sgad_ssim_workspace_size", "sgad_ssim_loss_grad", "sgad_fma_burn",
            # include/sgad_gicp.h
            "sgad_gicp_default_params", "sgad_gicp_workspace_size", "sgad_gicp_frame", "sgad_gicp_index",
            "sgad_gicp_correspond", "sgad_gicp_linearize", "sgad_gicp_set_pose", "sgad_gicp_track",
@@ -185,6 +185,7 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         "sgad_get_options": (st, [P, P]),
         "sgad_ssim_workspace_size": (st, [I32, P, P]),
         "sgad_ssim_loss_grad": (st, [I32, P, P, P, C.c_float, P, P, P, C.c_size_t, P]),
+        "sgad_fma_burn": (st, [I32, I32, P, P, P]),
         "sgad_gicp_default_params": (st, [P]),
         "sgad_gicp_workspace_size": (st, [P, P]),
         "sgad_gicp_frame": (st, [P, P, P, P, P, P, P, C.c_size_t, P]),
@@ -310,6 +311,12 @@ def sgad_ssim_loss_grad(views, rendered, target_rgb, weight, d_rgb, loss_accum: 
                         ws_bytes: int, stream: int) -> None:
     _call("sgad_ssim_loss_grad", len(views), views, rendered, target_rgb, float(weight), d_rgb, loss_accum,
           workspace, C.c_size_t(ws_bytes), stream)
+
+
+def sgad_fma_burn(blocks: int, iters: int, sink: int, stream: int) -> float:
+    flops = C.c_double(0.0)
+    _call("sgad_fma_burn", int(blocks), int(iters), sink, C.byref(flops), stream)
+    return flops.value
 
 
 def sgad_gicp_default_params() -> sgad_gicp_params:

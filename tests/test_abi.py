@@ -210,3 +210,11 @@ def test_gicp_params_workspace_and_validation_on_the_host():
                                None) == B.SGAD_ERR_INVALID_ARG
     nanpose = (C.c_double * 12)(*([float("nan")] * 12))
     assert lib.sgad_gicp_set_pose(nanpose, 4096, 1 << 20, None) == B.SGAD_ERR_INVALID_ARG
+
+
+def test_fma_probe_validation_on_the_host():
+    lib = B.load()
+    d = C.c_double()
+    assert lib.sgad_fma_burn(0, 10, 4096, C.byref(d), None) == B.SGAD_ERR_INVALID_ARG
+    assert lib.sgad_fma_burn(10, 0, 4096, C.byref(d), None) == B.SGAD_ERR_INVALID_ARG
+    assert lib.sgad_fma_burn(10, 10, None, C.byref(d), None) == B.SGAD_ERR_INVALID_ARG
