@@ -66,8 +66,10 @@ typedef struct {
     int32_t iterations;   /* GICP iterations taken by the last sgad_gicp_track */
     int32_t converged;    /* 1 if |xi| < tol ended it */
     int32_t n_matches;    /* correspondences of the last iteration */
-    int32_t status;       /* bit 0: a set overflowed its capacity; bit 1: fewer than 6
-                             correspondences or a singular system ended the loop */
+    int32_t status;       /* bit 0: a set overflowed its capacity (cleared by
+                             sgad_gicp_frame, set by it or by sgad_gicp_insert);
+                             bit 1: fewer than 6 correspondences or a singular system
+                             ended the last sgad_gicp_track */
     double cost;          /* Eq. 2 at the start of the last iteration */
     double step;          /* |xi| of the last iteration */
 } sgad_gicp_stats;

@@ -269,6 +269,7 @@ __device__ __forceinline__ bool cell_valid(const SelArgs &a, int c, int *u, int 
 __global__ void __launch_bounds__(256) k_select_count(const __grid_constant__ SelArgs a)
 {
     __shared__ int red[8];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.state->status = 0;   // a new frame: fresh flags
     int n = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -937,7 +938,7 @@ __global__ void k_gicp_init(GicpState *st, PoseD p0, int max_iters, float tol, i
     st->step = 0.0;
     st->max_iters = max_iters;
     st->tol = tol;
-    st->status &= ~2;
+    st->status &= 1;                 // keep the source's overflow flag, clear the rest
     st->blocks_done = 0;
 }
 

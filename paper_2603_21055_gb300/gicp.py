@@ -76,7 +76,7 @@ class GicpTracker:
         self.src = GaussianSet(src_capacity)
         self.map = GaussianSet(map_capacity)
         self.ws_bytes = B.sgad_gicp_workspace_size(self.p)
-        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device="cuda")
         self.pix = torch.empty(src_capacity, dtype=torch.int32, device="cuda")
 
     def stream(self) -> int:
