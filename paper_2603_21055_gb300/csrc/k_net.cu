@@ -17,9 +17,10 @@
 // pixels as K: its A rows are (tap, input channel) pairs, 4 or 8 taps per 128-row MMA,
 // plus one row of ones whose product gives the bias gradient. A 64-pixel K block of the
 // three input rows is staged pixel-major and transposed into the K-major layout with
-// ldmatrix.trans / stmatrix (one copy per dx shift); the accumulators stay in tensor
-// memory across all K blocks of the persistent block and are added to the output with
-// one atomic per (row, column) at the end.
+// ldmatrix.trans / stmatrix (one copy per dx shift); the next K block's rows are fetched
+// by cp.async into a second buffer meanwhile; the accumulators stay in tensor memory
+// across all K blocks of the persistent block and are added to the output with one
+// atomic per (row, column) at the end.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -423,7 +424,9 @@ struct WgradSmem {
     static constexpr int kNatY = kKBlock * kYStride;
     static constexpr int kA = (kKBlock / 8) * kRowsP;
     static constexpr int kB = (kKBlock / 8) * CO;
-    static constexpr size_t bytes = (size_t)(kNatX + kNatY + kA + kB) * 16;
+    // two natural-layout buffers: the next K block's rows arrive (cp.async) while the
+    // current one is transposed and multiplied
+    static constexpr size_t bytes = (size_t)(2 * (kNatX + kNatY) + kA + kB) * 16;
     static constexpr int kCols = kGroups * CO <= 32 ? 32 : (kGroups * CO <= 64 ? 64 : 128);
 };
 
@@ -432,9 +435,8 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const WgradArgs a)
 {
     using S = WgradSmem<CI, CO>;
     extern __shared__ uint4 smem[];
-    uint4 *natx = smem;
-    uint4 *naty = natx + S::kNatX;
-    uint4 *sA = naty + S::kNatY;
+    uint4 *nat = smem;                                   // [2][kNatX + kNatY]
+    uint4 *sA = nat + 2 * (S::kNatX + S::kNatY);
     uint4 *sB = sA + S::kA;
     __shared__ uint64_t bar;
     __shared__ uint32_t taddr_s;
@@ -456,31 +458,46 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const WgradArgs a)
     const uint32_t tmem = taddr_s;
     constexpr uint32_t idesc = tc::idesc_bf16(128, CO);
     const uint32_t a_base = tc::smem_u32(sA), b_base = tc::smem_u32(sB);
-    const uint32_t natx_base = tc::smem_u32(natx), naty_base = tc::smem_u32(naty);
     uint32_t phase = 0;
     bool any = false, failed = false;
     constexpr int kcx = CI / 8, kcy = CO / 8;
 
-    for (long long kb = blockIdx.x; kb < n_blocks; kb += gridDim.x) {
+    // natural-layout staging of K block kb into buffer `buf` by 16-byte cp.async (zero
+    // fill outside the image): x rows y-1..y+1, pixels x0-1 .. x0+64; dy row y, x0 .. x0+63
+    const auto stage = [&](long long kb, int buf) {
         const int xs = (int)(kb % segs);
         const long long ry = kb / segs;
         const int y = (int)(ry % a.H), n = (int)(ry / a.H);
         const int x0 = xs * kKBlock;
-        // natural-layout staging: x rows y-1..y+1, pixels x0-1 .. x0+64; dy row y, x0 .. x0+63
+        uint4 *natx = nat + buf * (S::kNatX + S::kNatY), *naty = natx + S::kNatX;
         for (int i = threadIdx.x; i < 3 * (kKBlock + 2) * kcx; i += blockDim.x) {
             const int kc = i % kcx, px = (i / kcx) % (kKBlock + 2), dy = i / (kcx * (kKBlock + 2));
             const int yy = y + dy - 1, xx = x0 + px - 1;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) v = __ldg(&a.x[(((size_t)n * a.H + yy) * a.W + xx) * kcx + kc]);
-            natx[(dy * (kKBlock + 2) + px) * S::kXStride + kc] = v;
+            const bool in = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const uint4 *src = in ? &a.x[(((size_t)n * a.H + yy) * a.W + xx) * kcx + kc] : a.x;
+            tc::cp_async16(tc::smem_u32(&natx[(dy * (kKBlock + 2) + px) * S::kXStride + kc]), src, in ? 16u : 0u);
         }
         for (int i = threadIdx.x; i < kKBlock * kcy; i += blockDim.x) {
             const int kc = i % kcy, px = i / kcy, xx = x0 + px;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (xx < a.W) v = __ldg(&a.dy[(((size_t)n * a.H + y) * a.W + xx) * kcy + kc]);
-            naty[px * S::kYStride + kc] = v;
+            const bool in = xx < a.W;
+            const uint4 *src = in ? &a.dy[(((size_t)n * a.H + y) * a.W + xx) * kcy + kc] : a.dy;
+            tc::cp_async16(tc::smem_u32(&naty[px * S::kYStride + kc]), src, in ? 16u : 0u);
         }
+        tc::cp_async_commit();
+    };
+
+    int buf = 0;
+    if (blockIdx.x < n_blocks) stage(blockIdx.x, 0);
+    for (long long kb = blockIdx.x; kb < n_blocks; kb += gridDim.x, buf ^= 1) {
+        const bool more = kb + gridDim.x < n_blocks;
+        if (more) stage(kb + gridDim.x, buf ^ 1);       // the next block's loads in flight
+        if (more)
+            tc::cp_async_wait<1>();
+        else
+            tc::cp_async_wait<0>();
         __syncthreads();
+        const uint32_t natx_base = tc::smem_u32(nat + buf * (S::kNatX + S::kNatY));
+        const uint32_t naty_base = natx_base + (uint32_t)S::kNatX * 16u;
         // transposed copies: A[kp][(3 dy + dx) CI + 8 kcc + r] = x[y+dy-1][x0 + 8 kp + j + dx - 1][8 kcc + r], j = 0..7
         constexpr int kABlocks = 9 * kcx * (kKBlock / 8);
         constexpr int kBBlocks = kcy * (kKBlock / 8);
@@ -524,6 +541,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const WgradArgs a)
             break;
         }
     }
+    tc::cp_async_wait<0>();                               // no copy outlives the loop
     tc::fence_after_sync();
     if (any && !failed) {
         for (int g = 0; g < S::kGroups; ++g) {
