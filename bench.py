@@ -49,7 +49,7 @@ FLOPS_BWD_PAIR = 75.0
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--seed", type=int, default=2)
@@ -74,6 +74,17 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over the ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -95,21 +106,31 @@ class ClockSampler:
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.file = None
+        self.window = None
 
-    def start(self):
+    def start(self, settle: float = 0.0):
+        """Starts sampling every 50 ms; `settle` seconds are waited so that nvidia-smi is
+        running before the caller's timed region begins."""
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.file, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        if settle > 0:
+            time.sleep(settle)
+
+    def mark(self, t0: float, t1: float):
+        """The wall-clock bounds (time.time()) of the timed region: samples outside it are
+        dropped (unless none falls inside)."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -123,6 +144,18 @@ class ClockSampler:
         self.file.seek(0)
         rows = [r.strip().split(",") for r in self.file.read().splitlines() if r.strip()]
         os.unlink(self.file.name)
+        if self.window is not None:
+            import datetime
+            inside = []
+            for r in rows:
+                try:
+                    ts = datetime.datetime.strptime(r[9].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except (ValueError, IndexError):
+                    continue
+                if self.window[0] - 0.05 <= ts <= self.window[1] + 0.05:
+                    inside.append(r)
+            if inside:
+                rows = inside
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -205,33 +238,28 @@ def run_ours(args):
             mp.capture()
             torch.cuda.synchronize()
         clocks = ClockSampler(local)
+        clocks.start(settle=0.5)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        clocks.start()
+        w0 = time.time()
         for i in range(args.steps):
             flush.zero_()
             starts[i].record(stream)
             mp.step()
             ends[i].record(stream)
         torch.cuda.synchronize()
+        clocks.mark(w0, time.time())
         if world > 1:
             dist.barrier()
         clk = clocks.stop()
         # every timed forward must have had room for all its keys (sticky device status)
         ok = mp.ensure_capacity()
-        if world > 1:
-            flag = torch.tensor([0 if ok else 1], device="cuda")
-            dist.all_reduce(flag, op=dist.ReduceOp.MAX)
-            ok = flag.item() == 0
+        ok = max_over_ranks(0.0 if ok else 1.0, world, "cuda") == 0.0
         if ok:
             break
     assert ok, "key capacity overflowed in every timing attempt"
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, "cuda")
     ms_per_step = total_ms / args.steps
     value = n_pix * world * args.steps / (total_ms / 1e3) / 1e6
 
@@ -979,10 +1007,7 @@ def run_sequence(args):
         wall = time.perf_counter() - w0
         c = clocks.stop()
         clk = clk or c
-        if world > 1:
-            t = torch.tensor([wall], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            wall = float(t.item())
+        wall = max_over_ranks(wall, world, "cuda")
         mine = sorted(fm.psnr)
         out["%s/%s" % (mode, views)] = {"s_per_frame": round(wall / seq.n_frames, 4), "wall_s": round(wall, 3),
                      "psnr_db_own_view_mean": round(float(np.mean([fm.psnr[i] for i in mine])), 3),
