@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(256) k_select_write(const __grid_constant__ Se
 // among the team's through shared memory, which gives the exact team-wide k-th candidate
 // after every ring (for the stopping proof) and the final sorted list.
 constexpr int kTeam = 8;
-constexpr int kRings = 4;                // rings searched before the exhaustive fallback
+constexpr int kRings = 6;                // rings searched before the exhaustive fallback
 
 struct Grid {
     const int32_t *off;       // [table + 1] bucket offsets

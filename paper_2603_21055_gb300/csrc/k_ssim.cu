@@ -402,11 +402,16 @@ extern "C" sgad_status sgad_ssim_loss_grad(int32_t n_views, const sgad_camera *v
         o = round256(o + (size_t)9 * v.W * v.H * sizeof(float));
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    static bool carveout = false;
-    if (!carveout) {           // the whole unified L1 as shared memory: 4 blocks per SM
-        cudaFuncSetAttribute(k_ssim_maps, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_ssim_grad, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        carveout = true;
+    // the whole unified L1 as shared memory (4 blocks per SM); a preference only, set
+    // once per device (outside any stream capture, which replays launches only)
+    static int configured[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(SGAD_ERR_CUDA, "sgad_ssim_loss_grad: no device");
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        if (cudaFuncSetAttribute(k_ssim_maps, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess ||
+            cudaFuncSetAttribute(k_ssim_grad, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+            return fail(SGAD_ERR_CUDA, "sgad_ssim_loss_grad: cannot set the shared-memory carveout");
+        if (dev >= 0 && dev < 64) configured[dev] = 1;
     }
     k_ssim_maps<<<blocks, kThreads, 0, st>>>(b);
     k_ssim_grad<<<blocks, kThreads, 0, st>>>(b);
