@@ -116,8 +116,10 @@ sgad_status sgad_gicp_linearize(const sgad_gicp_params *p, const sgad_gaussian_s
 sgad_status sgad_gicp_set_pose(const double pose[12], void *workspace, size_t ws_bytes, void *stream);
 
 /* GICP of the source set against the map (whose index must be current) from the host
- * initial pose; the estimate stays in the workspace (read by sgad_gicp_result, used by
- * sgad_gicp_insert). 1 + max_iters kernel launches (the last block of each iteration
+ * initial pose, or from the workspace's pose (sgad_gicp_set_pose, or the last estimate)
+ * when pose0 is NULL, so that a frame's calls can be captured once in a CUDA graph and
+ * replayed with a new starting pose; the estimate stays in the workspace (read by
+ * sgad_gicp_result, used by sgad_gicp_insert). 1 + max_iters kernel launches (the last block of each iteration
  * solves and updates the pose); iterations after convergence exit
  * at once. Capturable in a CUDA graph. */
 sgad_status sgad_gicp_track(const sgad_gicp_params *p, const sgad_gaussian_set *src,

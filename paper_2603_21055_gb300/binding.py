@@ -370,7 +370,9 @@ def sgad_gicp_set_pose(pose, ws: int, ws_bytes: int, stream: int) -> None:
 
 
 def sgad_gicp_track(p, src, map_, pose0, ws: int, ws_bytes: int, stream: int) -> None:
-    _call("sgad_gicp_track", C.byref(p), C.byref(src), C.byref(map_), _d12(pose0), ws, C.c_size_t(ws_bytes), stream)
+    """pose0 None: start from the workspace's pose."""
+    _call("sgad_gicp_track", C.byref(p), C.byref(src), C.byref(map_), _d12(pose0) if pose0 is not None else None, ws,
+          C.c_size_t(ws_bytes), stream)
 
 
 def sgad_gicp_insert(p, src, map_, ws: int, ws_bytes: int, stream: int) -> None:

@@ -924,12 +924,11 @@ __device__ void solve_state(GicpState *st, const double *sys)
     }
 }
 
-__global__ void k_gicp_init(GicpState *st, PoseD p0, int max_iters, float tol, int done)
+__global__ void k_gicp_init(GicpState *st, PoseD p0, int keep_pose, int max_iters, float tol, int done)
 {
-    for (int k = 0; k < 12; ++k) {
-        st->pose[k] = p0.p[k];
-        st->posef[k] = (float)p0.p[k];
-    }
+    if (!keep_pose)
+        for (int k = 0; k < 12; ++k) st->pose[k] = p0.p[k];
+    for (int k = 0; k < 12; ++k) st->posef[k] = (float)st->pose[k];
     st->iters = 0;
     st->done = done;
     st->converged = 0;
@@ -1308,7 +1307,7 @@ extern "C" sgad_status sgad_gicp_set_pose(const double pose[12], void *workspace
     if (s) return s;
     PoseD p0;
     std::memcpy(p0.p, pose, sizeof(p0.p));
-    k_gicp_init<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(at<GicpState>(workspace, 0), p0, 0, 0.f, 1);
+    k_gicp_init<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(at<GicpState>(workspace, 0), p0, 0, 0, 0.f, 1);
     return launched("sgad_gicp_set_pose: launch failed");
 }
 
@@ -1319,16 +1318,18 @@ extern "C" sgad_status sgad_gicp_track(const sgad_gicp_params *p, const sgad_gau
     GLayout L;
     sgad_status s = pair_checks(p, src, map, workspace, ws_bytes, &L);
     if (s) return s;
-    if (!pose0) return fail("sgad_gicp_track: NULL pose");
-    for (int k = 0; k < 12; ++k)
-        if (!std::isfinite(pose0[k])) return fail("sgad_gicp_track: non-finite pose");
     PoseD p0;
-    std::memcpy(p0.p, pose0, sizeof(p0.p));
+    std::memset(&p0, 0, sizeof(p0));
+    if (pose0) {                              // else: start from the workspace's pose
+        for (int k = 0; k < 12; ++k)
+            if (!std::isfinite(pose0[k])) return fail("sgad_gicp_track: non-finite pose");
+        std::memcpy(p0.p, pose0, sizeof(p0.p));
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     StepArgs a = step_args(p, src, map, workspace, L);
     a.system = 1;
     a.use_state = 1;
-    k_gicp_init<<<1, 1, 0, st>>>(a.state, p0, p->max_iters, p->tol, 0);
+    k_gicp_init<<<1, 1, 0, st>>>(a.state, p0, pose0 ? 0 : 1, p->max_iters, p->tol, 0);
     // one launch per iteration: each step's last block solves and updates the pose
     for (int it = 0; it < p->max_iters; ++it) {
         k_gicp_step<<<L.step_blocks, kStepThreads, 0, st>>>(a);

@@ -106,9 +106,34 @@ class GicpTracker:
     def set_pose(self, pose) -> None:
         B.sgad_gicp_set_pose(np.asarray(pose, np.float64).ravel(), self.ws.data_ptr(), self.ws_bytes, self.stream())
 
-    def track(self, pose0) -> None:
-        B.sgad_gicp_track(self.p, self.src.c, self.map.c, np.asarray(pose0, np.float64).ravel(), self.ws.data_ptr(),
-                          self.ws_bytes, self.stream())
+    def track(self, pose0=None) -> None:
+        """GICP from pose0 (cam -> world 3x4), or from the workspace's pose when None."""
+        p0 = np.asarray(pose0, np.float64).ravel() if pose0 is not None else None
+        B.sgad_gicp_track(self.p, self.src.c, self.map.c, p0, self.ws.data_ptr(), self.ws_bytes, self.stream())
+
+    def capture(self, cam, height: int, width: int) -> None:
+        """Records one frame's library calls (geometry Gaussians of self.depth_in, GICP from
+        the workspace's pose, map update) as a CUDA graph; `step` replays it."""
+        self.cam = cam
+        self.depth_in = torch.zeros(height, width, device="cuda")
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):                 # warm-up outside the capture
+            self.frame(cam, self.depth_in)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.frame(cam, self.depth_in)
+            self.track(None)
+            self.insert()
+
+    def step(self, depth: torch.Tensor, guess) -> None:
+        """One frame through the captured graph: copy the depth in, set the starting pose,
+        replay (frame -> GICP -> map update)."""
+        self.depth_in.copy_(depth)
+        self.set_pose(guess)
+        self.graph.replay()
 
     def insert(self) -> None:
         B.sgad_gicp_insert(self.p, self.src.c, self.map.c, self.ws.data_ptr(), self.ws_bytes, self.stream())
