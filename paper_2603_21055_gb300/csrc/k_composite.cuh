@@ -261,24 +261,58 @@ __global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks<B>())
 
 // ------------------------------------------------------------------ backward
 
-// Reduce-scatter of 16 per-lane values over the warp in 16 shuffles (instead of 80 for
-// 16 butterfly all-reductions): at each level a lane sends the half of its slots its
-// partner keeps and adds the partner's copy of the half it keeps. Afterwards every lane
-// returns the warp total of slot (lane >> 1).
-__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[16], int lane)
+// Reduce-scatter of ten per-lane values over the warp by recursive halving with padding:
+// at lane distance 16, 8, 4 and 2 a lane sends the part of its slots its partner keeps
+// (5, 3, 2 and 1 values) and adds the partner's copy of the part it keeps; a last
+// exchange at distance 1 sums the pair. 12 shuffles (a 16-slot scatter takes 16, ten
+// all-reductions 50). Both lanes of a pair then hold the warp total of the slot
+// scatter10_slot(lane) names (-1: padding).
+__device__ __forceinline__ float warp_reduce_scatter10(float (&v)[10], int lane)
 {
+    {
+        const bool up = (lane & 16) != 0;
 #pragma unroll
-    for (int lvl = 0; lvl < 4; ++lvl) {
-        const int half = 8 >> lvl, mask = 16 >> lvl;
-        const bool upper = (lane & mask) != 0;
-#pragma unroll
-        for (int i = 0; i < half; ++i) {
-            const float send = upper ? v[i] : v[i + half];
-            const float keep = upper ? v[i + half] : v[i];
-            v[i] = keep + __shfl_xor_sync(kFull, send, mask);
+        for (int i = 0; i < 5; ++i) {
+            const float send = up ? v[i] : v[i + 5];
+            const float keep = up ? v[i + 5] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, 16);
         }
     }
+    {
+        const bool up = (lane & 8) != 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float hi = i + 3 < 5 ? v[i + 3] : 0.f;
+            const float send = up ? v[i] : hi;
+            const float keep = up ? hi : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, 8);
+        }
+    }
+    {
+        const bool up = (lane & 4) != 0;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float hi = i + 2 < 3 ? v[i + 2] : 0.f;
+            const float send = up ? v[i] : hi;
+            const float keep = up ? hi : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, 4);
+        }
+    }
+    {
+        const bool up = (lane & 2) != 0;
+        const float send = up ? v[0] : v[1];
+        const float keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(kFull, send, 2);
+    }
     return v[0] + __shfl_xor_sync(kFull, v[0], 1);
+}
+
+// Slot held by a lane after warp_reduce_scatter10, -1 for padding.
+__device__ __forceinline__ int scatter10_slot(int lane)
+{
+    const int g = lane >> 4, q = (lane >> 3) & 1, r = (lane >> 1) & 3;
+    if (q ? r >= 2 : r >= 3) return -1;
+    return 5 * g + (q ? 3 + r : r);
 }
 
 // Chain rule of one staged Gaussian from its ten accumulated pair moments (colour (3),
@@ -426,9 +460,9 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
                     const int bit = 31 - __clz(mask);
                     mask &= ~(1u << bit);
                     const int jj = c0 + bit;
-                    float val[16];
+                    float val[10];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) val[q] = 0.f;
+                    for (int q = 0; q < 10; ++q) val[q] = 0.f;
                     bool contrib = false;
                     const Staged st = sm[jj];
 #pragma unroll
@@ -466,9 +500,9 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
                         T[p] = Ti;
                     }
                     if (__any_sync(kFull, contrib)) {
-                        const float total = warp_reduce_scatter16(val, lane);
-                        const int slot = lane >> 1;
-                        if ((lane & 1) == 0 && slot < 10) atomicAdd(&acc[jj][slot], total);
+                        const float total = warp_reduce_scatter10(val, lane);
+                        const int slot = scatter10_slot(lane);
+                        if ((lane & 1) == 0 && slot >= 0) atomicAdd(&acc[jj][slot], total);
                     }
                 }
             }
