@@ -511,8 +511,17 @@ def cpu_baseline(scene):
     _, g = oracle.l1_loss(scene, ref)
     oracle.backward(scene, g)
     dt = time.perf_counter() - t0
+    # and the tiny plane case (one 64x48 keyframe into one view), timed in full
+    from paper_2603_21055_gb300 import synth
+    tiny = synth.config1_plane()
+    t1 = time.perf_counter()
+    ref1 = oracle.render(tiny)
+    _, g1 = oracle.l1_loss(tiny, ref1)
+    oracle.backward(tiny, g1)
+    dt1 = time.perf_counter() - t1
     return {"value": round(scene.n_pixels / dt / 1e6, 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "all 8 views (640x480, all 8 keyframes): FP64 forward + L1 grad + adjoint, %.1f s" % dt}
+            "sample": "all 8 views (640x480, all 8 keyframes): FP64 forward + L1 grad + adjoint, %.1f s" % dt,
+            "plane64x48": {"value": round(tiny.n_pixels / dt1 / 1e6, 6), "unit": UNIT, "seconds": round(dt1, 4)}}
 
 
 # ----------------------------------------------------------------- reference arm
