@@ -180,3 +180,47 @@ def test_view_pose_gradient(scene1, crop, algo):
         e = compare_pose(res, dp, ab)
         print("%s %s pose grad ratio %.3f" % (sc.name, algo, e))
         assert e <= 1.0
+
+
+def test_view_that_sees_nothing(scene1):
+    """A view turned away from every Gaussian: no keys, background images, and every
+    gradient written as zero (the outputs start as NaN)."""
+    from paper_2603_21055_gb300.synth import Camera, Scene, _f32pose
+    v = scene1.views[0]
+    P = np.asarray(v.pose, np.float64)
+    flip = np.diag([-1.0, 1.0, -1.0])                      # 180 degrees about the camera's y axis
+    away = Camera(v.width, v.height, v.fx, v.fy, v.cx, v.cy, _f32pose(np.hstack([flip @ P[:, :3], (flip @ P[:, 3])[:, None]])))
+    sc = Scene(scene1.keyframes, [away], scene1.target_rgb, scene1.target_depth, 0.0)
+    ref, g = _grads_for(sc)
+    res = gpu_run(sc, grads_in=g)
+    assert res["n_keys"] == 0
+    im = res["images"][0]
+    assert not im["rgb"].any() and not im["depth"].any() and not im["alpha"].any()
+    assert not np.abs(ref[0]["rgb"]).any()
+    for gk in res["grads"]:
+        for name, arr in gk.items():
+            assert np.isfinite(arr).all() and not arr.any(), name
+
+
+def test_most_keyframes_and_views(scene1):
+    """The most keyframes (32) and views (64) a call takes: disjoint 8 x 6 crops of the
+    plane's keyframe and view, so most views see a handful of Gaussians and some none."""
+    from paper_2603_21055_gb300.synth import Scene, crop_scene
+    kfs, views, tr, td = [], [], [], []
+    for i in range(32):
+        c = crop_scene(scene1, (8 * (i % 8), 6 * (i // 8), 8, 6), (0, 0, 8, 6))
+        kfs += c.keyframes
+    for j in range(64):
+        c = crop_scene(scene1, (0, 0, 8, 6), (8 * (j % 8), 6 * (j // 8), 8, 6))
+        views += c.views
+        tr += c.target_rgb
+        td += c.target_depth
+    sc = Scene(kfs, views, tr, td, 0.0)
+    ref, g = _grads_for(sc)
+    res = gpu_run(sc, grads_in=g)
+    n_aside = compare_keys(res, sc)
+    worst, n_near = compare_images(res, ref)
+    og = oracle.backward(sc, [{k: v.astype(np.float64) for k, v in x.items()} for x in g])
+    e = compare_grads(res, og)
+    print("32 kf x 64 views: keys %d aside %d img %.2e grad ratio %.3f" % (res["n_keys"], n_aside, worst, e))
+    assert res["n_keys"] > 0 and e <= 1.0
