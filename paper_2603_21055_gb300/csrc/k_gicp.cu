@@ -27,7 +27,8 @@ using sgad::report_error;
 constexpr int kSys = 29;                 // H upper triangle (21), g (6), cost, count
 constexpr int kSelBlock = 1024;          // cells per selection block (4 per thread)
 constexpr int kMaxSelBlocks = 16384;     // selection grids of up to 16.7 M cells
-constexpr int kStepThreads = 256;
+constexpr int kStepThreads = 128;        // correspondence step: 16 teams of 8 lanes per block
+constexpr int kInsThreads = 256;         // map-update kernels
 constexpr int kKMatchMax = 8;
 
 struct GicpState {
@@ -64,10 +65,11 @@ GLayout glayout(const sgad_gicp_params &p)
     GLayout L;
     L.table = table_for(p.map_capacity);
     L.knn_table = table_for(p.src_capacity);
-    L.max_blocks = (p.src_capacity + kStepThreads - 1) / kStepThreads;
-    // the correspondence step: one team of 8 lanes per source point, 32 per block,
-    // grid-stride over at most 4 blocks per SM of a 152-SM part
-    L.step_blocks = std::min((p.src_capacity + 31) / 32, 4 * 152);
+    L.max_blocks = (p.src_capacity + kInsThreads - 1) / kInsThreads;
+    // the correspondence step: one team of 8 lanes per source point, 16 per block (blocks
+    // small enough to spread a few thousand points evenly over the SMs), grid-stride over
+    // at most 4 blocks per SM of a 152-SM part (the solve sums one partial row per block)
+    L.step_blocks = std::min((p.src_capacity + 15) / 16, 4 * 152);
     size_t o = 0;
     const auto take = [&o](size_t bytes) {
         const size_t at = o;
@@ -463,6 +465,7 @@ __device__ int team_nearest(const Grid &g, float3 me, int K, float r_max, int ma
             const float d = sqdist(q.x, q.y, q.z, me.x, me.y, me.z);
             if (d <= r2) lane_insert<KMAX>(d, __float_as_int(q.w), K, bd, bj, wd, wj);
         });
+        if (r == 0) continue;                               // nothing is proven at radius 0
         found = team_select<KMAX>(bd, bj, K, sd, sj, tl, out, outd);
         const float reach = (float)r * g.cell * (1.f - 1e-4f);
         // every point outside the searched rings lies at least `reach` away
@@ -809,12 +812,18 @@ __global__ void __launch_bounds__(kStepThreads) k_gicp_step(const __grid_constan
 // scheduling. Partials are read through L2 (written by other blocks of the same grid).
 __device__ void sum_partials(const float *partial, int nblocks, double *sys)
 {
-    __shared__ double part[32][kSys];
+    __shared__ double part[8][kSys];                    // blocks of up to 256 threads
     const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, k = threadIdx.x & 31;
     if (k < kSys) {
-        double s = 0.0;
-        for (int b = w; b < nblocks; b += nw) s += (double)__ldcg(partial + b * 32 + k);
-        part[w][k] = s;
+        // eight independent sums keep eight row loads in flight; added in a fixed order
+        double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int b = w;
+        for (; b + 7 * nw < nblocks; b += 8 * nw) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s[u] += (double)__ldcg(partial + (b + u * nw) * 32 + k);
+        }
+        for (int u = 0; b < nblocks; b += nw, ++u) s[u & 7] += (double)__ldcg(partial + b * 32 + k);
+        part[w][k] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
     }
     __syncthreads();
     if (threadIdx.x < kSys) {
