@@ -6,45 +6,30 @@
 // 64-bit integers gives exactly the front-to-back order by (depth, index) with ties
 // broken by the lower index; positive floats order like their bit patterns.
 //
-// One CTA per tile. Buckets up to `cap` entries are sorted in shared memory by a
-// merge sort (per-thread insertion sort of a short run, then log2(threads) rounds of
-// merge-path merging); larger buckets are sorted in cap-sized chunks the same way and
-// then merged through global memory, ping-ponging with a scratch key array.
+// One CTA per tile. A bucket of up to `cap` entries is sorted in shared memory by a
+// least-significant-digit radix sort on the depth field only: the bits that vary within
+// the tile (depth bits minus the tile's smallest, 8 bits per pass, so a tile whose
+// depths share their exponent needs three passes) are ranked stably, warp by warp, with
+// one match per 32 entries. Equal depths then sit in runs in input order; each run is
+// put in index order by one thread. A run longer than kRunMax (a tile of equal depths,
+// e.g. a fronto-parallel plane seen from its own camera) sends the tile through the
+// exact 64-bit LSD order instead: passes on the index field, then on the depth field.
+// Larger buckets are sorted in cap-sized chunks the same way and then merged through
+// global memory, ping-ponging with a scratch key array.
 #include "sgad_device.cuh"
 
 namespace sgad {
 
-#ifndef SGAD_SORT_THREADS
-#define SGAD_SORT_THREADS 512
-#endif
-constexpr int kSortThreads = SGAD_SORT_THREADS;
-
-// Shared-memory index with one padding slot per 16 entries: each thread works on its own
-// run of consecutive entries, and without padding the 64-bit accesses of lanes whose runs
-// start 128 bytes apart would all hit the same two banks.
-template <bool kPad>
-__device__ __forceinline__ int pidx(int i)
-{
-    return kPad ? i + (i >> 4) : i;
-}
-
-template <bool kPad>
-__device__ __forceinline__ void insertion_sort(uint64_t *a, int lo, int n)
-{
-    for (int i = 1; i < n; ++i) {
-        const uint64_t x = a[pidx<kPad>(lo + i)];
-        int j = i - 1;
-        while (j >= 0 && a[pidx<kPad>(lo + j)] > x) {
-            a[pidx<kPad>(lo + j + 1)] = a[pidx<kPad>(lo + j)];
-            --j;
-        }
-        a[pidx<kPad>(lo + j + 1)] = x;
-    }
-}
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kRadixBins = 256;
+constexpr int kCntStride = kSortWarps + 1;          // one padding word per digit row
+constexpr int kCntWords = kRadixBins * kCntStride;
+constexpr int kRunMax = 32;
+static_assert(kRadixBins * kSortWarps == kSortThreads * 8, "the scan gives each thread 8 counters");
 
 // Merged positions [k0, k1) of the sorted runs src[a0 .. a0+la) and src[b0 .. b0+lb),
-// written to dst[d0 + k0 .. d0 + k1) (indices before padding).
-template <bool kPad>
+// written to dst[d0 + k0 .. d0 + k1).
 __device__ __forceinline__ void merge_segment(const uint64_t *src, int a0, int la, int b0, int lb, int k0, int k1,
                                               uint64_t *dst, int d0)
 {
@@ -52,91 +37,256 @@ __device__ __forceinline__ void merge_segment(const uint64_t *src, int a0, int l
     int hi = k0 < la ? k0 : la;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (src[pidx<kPad>(a0 + mid)] <= src[pidx<kPad>(b0 + k0 - 1 - mid)])
+        if (src[a0 + mid] <= src[b0 + k0 - 1 - mid])
             lo = mid + 1;
         else
             hi = mid;
     }
     int i = lo, j = k0 - lo;
-    uint64_t va = i < la ? src[pidx<kPad>(a0 + i)] : ~0ull;
-    uint64_t vb = j < lb ? src[pidx<kPad>(b0 + j)] : ~0ull;
+    uint64_t va = i < la ? src[a0 + i] : ~0ull;
+    uint64_t vb = j < lb ? src[b0 + j] : ~0ull;
     for (int k = k0; k < k1; ++k) {
         const bool take_a = j >= lb || (i < la && va <= vb);
         if (take_a) {
-            dst[pidx<kPad>(d0 + k)] = va;
+            dst[d0 + k] = va;
             ++i;
-            va = i < la ? src[pidx<kPad>(a0 + i)] : ~0ull;
+            va = i < la ? src[a0 + i] : ~0ull;
         } else {
-            dst[pidx<kPad>(d0 + k)] = vb;
+            dst[d0 + k] = vb;
             ++j;
-            vb = j < lb ? src[pidx<kPad>(b0 + j)] : ~0ull;
+            vb = j < lb ? src[b0 + j] : ~0ull;
         }
     }
 }
 
-// Sorts a[0..n) using b as scratch (both padded shared-memory buffers when kPad); returns
-// the buffer holding the result.
-template <bool kPad>
-__device__ uint64_t *block_merge_sort(uint64_t *a, uint64_t *b, int n)
+struct SortSmem {
+    uint32_t cnt[kCntWords];       // per (digit, warp) counts, then their exclusive offsets
+    uint32_t wsum[kSortWarps];
+    uint32_t red[2][kSortWarps];   // block min / max scratch
+    int flag;
+};
+
+__device__ __forceinline__ uint32_t field_of(uint64_t key, int field) { return (uint32_t)(key >> field); }
+
+// Block-wide (min, max) of one 32-bit field over the valid registers; every thread
+// returns the same pair. Ends with a barrier after the scratch is read.
+template <int kPer>
+__device__ __forceinline__ void field_range(const uint64_t (&k)[kPer], int C, int p0, int n, int field, SortSmem &s,
+                                            uint32_t &mn, uint32_t &mx)
 {
-    const int T = blockDim.x;
-    const int C = n > T ? (n + T - 1) / T : 1;
-    const int lo = threadIdx.x * C;
-    if (lo < n) insertion_sort<kPad>(a, lo, n - lo < C ? n - lo : C);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    mn = 0xffffffffu;
+    mx = 0u;
+#pragma unroll
+    for (int r = 0; r < kPer; ++r)
+        if (r < C && p0 + r * 32 < n) {
+            const uint32_t f = field_of(k[r], field);
+            mn = min(mn, f);
+            mx = max(mx, f);
+        }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+        s.red[0][w] = mn;
+        s.red[1][w] = mx;
+    }
     __syncthreads();
-    for (int w = C; w < n; w <<= 1) {
-        const int k0 = threadIdx.x * C;
-        if (k0 < n) {
-            const int base = (k0 / (2 * w)) * (2 * w);
-            const int la = n - base < w ? n - base : w;
-            const int rest = n - base - la;
-            const int lb = rest < w ? rest : w;
-            int k1 = k0 + C;
-            if (k1 > base + la + lb) k1 = base + la + lb;
-            merge_segment<kPad>(a, base, la, base + la, lb, k0 - base, k1 - base, b, base);
-        }
-        __syncthreads();
-        uint64_t *t = a;
-        a = b;
-        b = t;
+#pragma unroll
+    for (int i = 0; i < kSortWarps; ++i) {
+        mn = min(mn, s.red[0][i]);
+        mx = max(mx, s.red[1][i]);
     }
-    return a;
+    __syncthreads();
 }
 
-__host__ __device__ constexpr int padded(int n) { return n + (n >> 4) + 16; }
-
-__global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *__restrict__ off,
-                                                             uint64_t *__restrict__ entries,
-                                                             uint64_t *__restrict__ alt, int cap,
-                                                             const WsHeader *hdr)
+// One stable pass: entries move to ks in the order of digit ((field - base) >> shift) & 255,
+// equal digits keeping the order of positions p = w * 32 C + r * 32 + lane. The caller's
+// registers hold the entries at those positions; on return ks holds the pass's output.
+template <int kPer>
+__device__ __forceinline__ void radix_pass(uint64_t *ks, SortSmem &s, const uint64_t (&k)[kPer], int C, int p0, int n,
+                                           int field, uint32_t base, int shift)
 {
-    extern __shared__ uint64_t smem[];
-    if (hdr->overflow) return;
-    const int t = blockIdx.x;
-    const uint32_t s = off[t];
-    const int n = (int)(off[t + 1] - s);
-    if (n <= 1) return;
-    uint64_t *a = smem, *b = smem + padded(cap);
-    uint64_t *gk = entries + s;
-    if (n <= cap) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) a[pidx<true>(i)] = gk[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kCntWords; i += kSortThreads) s.cnt[i] = 0u;
+    __syncthreads();
+    // rank within the warp: earlier rounds' count of the digit + earlier lanes of this
+    // round; kept with the digit as rank << 8 | digit
+    uint32_t rd[kPer];
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        if (r >= C) continue;
+        const bool valid = p0 + r * 32 < n;
+        const uint32_t d = valid ? ((field_of(k[r], field) - base) >> shift) & (kRadixBins - 1) : kRadixBins;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (valid && lane == leader) {
+            uint32_t *c = &s.cnt[d * kCntStride + w];
+            old = *c;
+            *c = old + __popc(peers);
+        }
+        rd[r] = ((__shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt)) << 8) | (d & (kRadixBins - 1));
+    }
+    __syncthreads();
+    // exclusive scan of the counts in (digit, warp) order: thread t owns digit t / 2,
+    // warps (t & 1) * 8 .. + 7
+    {
+        const int t = threadIdx.x;
+        uint32_t *row = &s.cnt[(t >> 1) * kCntStride + (t & 1) * 8];
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            v[j] = row[j];
+            sum += v[j];
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s.wsum[w] = inc;
         __syncthreads();
-        const uint64_t *r = block_merge_sort<true>(a, b, n);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) gk[i] = r[pidx<true>(i)];
+        uint32_t run = inc - sum;
+        for (int i = 0; i < w; ++i) run += s.wsum[i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            row[j] = run;
+            run += v[j];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        if (r < C && p0 + r * 32 < n) ks[s.cnt[(rd[r] & (kRadixBins - 1)) * kCntStride + w] + (rd[r] >> 8)] = k[r];
+    }
+    __syncthreads();
+}
+
+template <int kPer>
+__device__ __forceinline__ void load_regs(const uint64_t *src, uint64_t (&k)[kPer], int C, int p0, int n)
+{
+#pragma unroll
+    for (int r = 0; r < kPer; ++r)
+        if (r < C && p0 + r * 32 < n) k[r] = src[p0 + r * 32];
+}
+
+// LSD passes over the bits of (field - min) that vary within the tile. On entry the
+// registers hold the entries at positions p; on return ks holds them in the pass order
+// (the registers are stale if any pass ran: `in_smem` tells the caller).
+template <int kPer>
+__device__ __forceinline__ void sort_field(uint64_t *ks, SortSmem &s, uint64_t (&k)[kPer], int C, int p0, int n, int field,
+                           bool &in_smem)
+{
+    uint32_t mn, mx;
+    field_range<kPer>(k, C, p0, n, field, s, mn, mx);
+    const int bits = mx == mn ? 0 : 32 - __clz(mx - mn);
+    for (int shift = 0; shift < bits; shift += 8) {
+        if (in_smem) load_regs<kPer>(ks, k, C, p0, n);
+        radix_pass<kPer>(ks, s, k, C, p0, n, field, mn, shift);
+        in_smem = true;
+    }
+}
+
+// Sorts the n <= kSortThreads * kPer entries of src into ks (shared memory), exactly by
+// their 64-bit value. Phase 0 sorts by depth and orders runs of equal depth by index;
+// a run longer than kRunMax sends the tile through phases 1 (index field) and 2 (depth
+// field), the exact LSD order. One instance of the pass code serves every phase.
+template <int kPer>
+__device__ __forceinline__ void block_sort(const uint64_t *src, uint64_t *ks, SortSmem &s, int n)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int C = (n + kSortThreads - 1) / kSortThreads;
+    const int p0 = w * 32 * C + lane;
+    uint64_t k[kPer];
+    load_regs<kPer>(src, k, C, p0, n);
+    bool in_smem = false;
+    for (int phase = 0;; ++phase) {
+        if (phase > 0) load_regs<kPer>(ks, k, C, p0, n);
+        sort_field<kPer>(ks, s, k, C, p0, n, phase == 1 ? 0 : 32, in_smem);
+        if (phase == 1) continue;
+        if (phase == 2) return;
+        if (!in_smem) {
+#pragma unroll
+            for (int r = 0; r < kPer; ++r)
+                if (r < C && p0 + r * 32 < n) ks[p0 + r * 32] = k[r];
+            in_smem = true;
+        }
+        if (threadIdx.x == 0) s.flag = 0;
+        __syncthreads();
+        // runs of equal depth: find them (read only), then order each by index. Position
+        // m of this thread (i = thread + m * threads) records (run length - 1) in 5 bits,
+        // 0 if no run of 2 .. kRunMax entries starts there.
+        constexpr int kCodes = (kPer + 5) / 6;
+        uint32_t code[kCodes];
+#pragma unroll
+        for (int q = 0; q < kCodes; ++q) code[q] = 0u;
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) {
+            const int i = threadIdx.x + m * kSortThreads;
+            if (m < C && i + 1 < n) {
+                const uint32_t h = field_of(ks[i], 32);
+                if ((i == 0 || field_of(ks[i - 1], 32) != h) && field_of(ks[i + 1], 32) == h) {
+                    int j = i + 2;
+                    while (j < n && j - i <= kRunMax && field_of(ks[j], 32) == h) ++j;
+                    if (j - i > kRunMax)
+                        s.flag = 1;
+                    else
+                        code[m / 6] |= (uint32_t)(j - i - 1) << (5 * (m % 6));
+                }
+            }
+        }
+        __syncthreads();
+        if (s.flag) continue;        // uniform: read after the barrier
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) {
+            const int len = (int)((code[m / 6] >> (5 * (m % 6))) & 31u) + 1;
+            if (len < 2) continue;
+            uint64_t *a = ks + threadIdx.x + m * kSortThreads;
+            for (int i = 1; i < len; ++i) {
+                const uint64_t x = a[i];
+                int j = i - 1;
+                while (j >= 0 && a[j] > x) {
+                    a[j + 1] = a[j];
+                    --j;
+                }
+                a[j + 1] = x;
+            }
+        }
+        __syncthreads();
         return;
     }
-    // large bucket: sort cap-sized chunks in shared memory ...
+}
+
+template <int kPer>
+__global__ void __launch_bounds__(kSortThreads, kPer <= 12 ? 2 : 1)
+    k_sort_tiles(const uint32_t *__restrict__ off, uint64_t *__restrict__ entries, uint64_t *__restrict__ alt, int cap,
+                 const WsHeader *hdr)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem &s = *reinterpret_cast<SortSmem *>(smem_raw);
+    uint64_t *ks = reinterpret_cast<uint64_t *>(smem_raw + ((sizeof(SortSmem) + 15) & ~size_t(15)));
+    if (hdr->overflow) return;
+    const int t = blockIdx.x;
+    const uint32_t s0 = off[t];
+    const int n = (int)(off[t + 1] - s0);
+    if (n <= 1) return;
+    uint64_t *gk = entries + s0;
+    // sort cap-sized chunks in shared memory ...
     for (int c0 = 0; c0 < n; c0 += cap) {
         const int m = n - c0 < cap ? n - c0 : cap;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) a[pidx<true>(i)] = gk[c0 + i];
-        __syncthreads();
-        const uint64_t *r = block_merge_sort<true>(a, b, m);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) gk[c0 + i] = r[pidx<true>(i)];
+        block_sort<kPer>(gk + c0, ks, s, m);
+        for (int i = threadIdx.x; i < m; i += kSortThreads) gk[c0 + i] = ks[i];
         __syncthreads();
     }
+    if (n <= cap) return;
     // ... then merge the sorted chunks through global memory
-    uint64_t *src = gk, *dst = alt + s;
-    const int per = (n + blockDim.x - 1) / blockDim.x;
+    uint64_t *src = gk, *dst = alt + s0;
+    const int per = (n + kSortThreads - 1) / kSortThreads;
     for (int w = cap; w < n; w <<= 1) {
         const int k0 = threadIdx.x * per;
         const int kend = k0 + per < n ? k0 + per : n;
@@ -146,7 +296,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *__r
             const int rest = n - base - la;
             const int lb = rest < w ? rest : w;
             const int seg_end = kend < base + la + lb ? kend : base + la + lb;
-            merge_segment<false>(src, base, la, base + la, lb, k - base, seg_end - base, dst, base);
+            merge_segment(src, base, la, base + la, lb, k - base, seg_end - base, dst, base);
             k = seg_end;
         }
         __syncthreads();
@@ -155,11 +305,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tiles(const uint32_t *__r
         dst = tmp;
     }
     if (src != gk)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) gk[i] = src[i];
+        for (int i = threadIdx.x; i < n; i += kSortThreads) gk[i] = src[i];
 }
 
-cudaError_t launch_sort_tiles(const uint32_t *off, uint64_t *entries, uint64_t *alt, int n_tiles, int cap,
-                              const WsHeader *hdr, cudaStream_t st)
+template <int kPer>
+static cudaError_t launch_sort(const uint32_t *off, uint64_t *entries, uint64_t *alt, int n_tiles, int cap,
+                               const WsHeader *hdr, cudaStream_t st)
 {
     // Raise the kernel's dynamic shared-memory limit once per device and size (outside
     // any stream capture, which only replays launches).
@@ -167,14 +318,22 @@ cudaError_t launch_sort_tiles(const uint32_t *off, uint64_t *entries, uint64_t *
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)padded(cap) * 2 * sizeof(uint64_t);
+    const size_t smem = ((sizeof(SortSmem) + 15) & ~size_t(15)) + (size_t)cap * sizeof(uint64_t);
     if (dev < 0 || dev >= 64 || configured[dev] < (int)smem) {
-        e = cudaFuncSetAttribute(k_sort_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_sort_tiles<kPer>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = (int)smem;
     }
-    if (n_tiles > 0) k_sort_tiles<<<n_tiles, kSortThreads, smem, st>>>(off, entries, alt, cap, hdr);
+    if (n_tiles > 0) k_sort_tiles<kPer><<<n_tiles, kSortThreads, smem, st>>>(off, entries, alt, cap, hdr);
     return cudaSuccess;
+}
+
+// cap in [64, 12288] (checked by the caller).
+cudaError_t launch_sort_tiles(const uint32_t *off, uint64_t *entries, uint64_t *alt, int n_tiles, int cap,
+                              const WsHeader *hdr, cudaStream_t st)
+{
+    if (cap <= kSortThreads * 12) return launch_sort<12>(off, entries, alt, n_tiles, cap, hdr, st);
+    return launch_sort<24>(off, entries, alt, n_tiles, cap, hdr, st);
 }
 
 }  // namespace sgad

@@ -224,3 +224,31 @@ def test_most_keyframes_and_views(scene1):
     e = compare_grads(res, og)
     print("32 kf x 64 views: keys %d aside %d img %.2e grad ratio %.3f" % (res["n_keys"], n_aside, worst, e))
     assert res["n_keys"] > 0 and e <= 1.0
+
+
+@pytest.mark.parametrize("quantum", [0.0, 0.001, 0.05])
+def test_equal_depth_runs(scene1, quantum):
+    """Entries of equal depth in one tile are listed by index. The plane's keyframe is
+    seen from its own camera with zero offsets, so an entry's depth is its depth-map
+    value: a constant map (every entry of a tile at one depth, long runs) and the tilted
+    plane's depths rounded to 1 mm (short runs of equal depth) and to 5 cm (long runs)."""
+    from paper_2603_21055_gb300.synth import Camera, Keyframe, Scene
+    k = scene1.keyframes[0]
+    if quantum == 0.0:
+        depth = np.full_like(k.depth, 1.5)
+    else:
+        depth = (np.round(k.depth / quantum) * quantum).astype(np.float32)
+    kf = Keyframe(k.cam, depth, np.zeros_like(k.offset), k.rgb, k.logit, (depth / np.float32(k.cam.fx)).astype(np.float32))
+    c = k.cam
+    view = Camera(c.width, c.height, c.fx, c.fy, c.cx, c.cy, np.eye(4, dtype=np.float32)[:3].copy())
+    sc = Scene([kf], [view], scene1.target_rgb, scene1.target_depth, 0.0)
+    ref = oracle.render(sc)
+    res = gpu_run(sc)
+    offs, ent = res["offsets"], res["entries"]
+    runs = 0
+    for t in range(len(offs) - 1):
+        z = ent[offs[t]:offs[t + 1]] >> np.uint64(32)
+        runs = max(runs, int(np.unique(z, return_counts=True)[1].max()) if len(z) else 0)
+    assert runs > (32 if quantum != 0.001 else 1)                      # the case it is meant to exercise
+    compare_keys(res, sc)
+    compare_images(res, ref)
