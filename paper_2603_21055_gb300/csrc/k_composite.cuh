@@ -4,18 +4,24 @@
 // entries staged per block-wide barrier (B).
 //
 // Forward: 256 threads per tile, one pixel per thread; each warp owns an 8x4 block of
-// pixels. The tile's sorted list is consumed in batches of B entries: the threads stage
-// them (gathering each Gaussian's 32-byte world record and projecting it into the view)
-// into shared memory, then every warp tests 32 staged Gaussians at a time against its
-// pixel block (one lane per Gaussian, a ballot) and walks only the ones whose
-// alpha >= 1/255 box reaches it. A warp stops when all its pixels are done; the block
-// stops when all warps are.
+// pixels, split into four 4x2 groups of eight lanes. The tile's sorted list is consumed
+// in batches of B entries: the threads stage them (gathering each Gaussian's 32-byte
+// world record and projecting it into the view) into shared memory, then every warp
+// tests 32 staged Gaussians at a time against each group's pixel block (one lane per
+// Gaussian, a ballot per group) and each group walks only the ones whose alpha >= 1/255
+// box reaches its block, the four groups side by side in the same instructions. Small
+// groups cut the (pixel, entry) pairs a walk evaluates for nothing: an entry whose box
+// touches the warp's block usually misses most of its pixels. A group stops when its
+// pixels are done, a warp when its groups are, the block when all warps are.
 //
 // Backward: 128 threads per tile, each warp an 8x8 pixel block and each lane the pixels
 // (x, y) and (x, y + 4). The same lists are walked from the tile's largest contributor
-// count down to 0. Each pixel starts from its saved final transmittance and recovers the
-// transmittance in front of entry i by division, T_i = T_{i+1} / (1 - alpha_i), which is
-// stable because alpha <= 0.99. Per (pixel, entry) it forms the gradient of the colour,
+// count down to 0. (Splitting the warp into groups as in the forward walks fewer
+// entries here too, but each step then carries more state and a group-wise reduction,
+// and it measured slower.) Each pixel starts from its saved final transmittance and
+// recovers the transmittance in front of entry i by division,
+// T_i = T_{i+1} / (1 - alpha_i), which is stable because alpha <= 0.99. Per
+// (pixel, entry) it forms the gradient of the colour,
 // depth and alpha terms; the moments of the lane's two pixels are summed in registers,
 // reduced over the warp with a reduce-scatter and accumulated per staged Gaussian in
 // shared memory. At the end of the batch each staging thread turns them into d mu, d s,
@@ -140,17 +146,45 @@ struct FwdPixel {
     bool done;
 };
 
-// The warp walks nb staged entries (list positions b0 - s ...) against its pixel block:
-// 32 entries at a time, a ballot of those whose alpha box reaches the block, then each
-// of them in order for every pixel not yet done.
+// Box of a staged entry against the pixel rectangle [x0, x0 + w - 1] x [y0, y0 + h - 1]
+// (pixel centres); a negative half extent never overlaps.
+__device__ __forceinline__ bool box_overlaps(const float4 box, float x0, float y0, float w1, float h1)
+{
+    return box.z >= 0.0f && box.x + box.z >= x0 && box.x - box.z <= x0 + w1 && box.y + box.w >= y0 &&
+           box.y - box.w <= y0 + h1;
+}
+
+// Forward pixel of thread (warp, lane) in a TW-wide tile at pixel (ox, oy): the warp's
+// 8x4 block, group q = lane / 8 its 4x2 sub-block (4 (q & 1), 2 (q >> 1)).
+template <int TW>
+__device__ __forceinline__ int2 fwd_pixel(int ox, int oy, int warp, int lane)
+{
+    const int q = lane >> 3;
+    return make_int2(ox + (warp % (TW / 8)) * 8 + 4 * (q & 1) + (lane & 3),
+                     oy + (warp / (TW / 8)) * 4 + 2 * (q >> 1) + ((lane >> 2) & 1));
+}
+
+// The warp walks nb staged entries (list positions b0 - s ...) against its pixel block
+// (origin bx, by): 32 entries at a time, one ballot per 4x2 group of the entries whose
+// alpha box reaches the group's block (groups whose pixels are all done take none), then
+// each group walks its entries in order for every pixel not yet done.
 __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0, uint32_t s, int tile,
-                                           const CompositeArgs &a, const WarpRect &wr, float qx, float qy, int lane,
+                                           const CompositeArgs &a, float bx, float by, float qx, float qy, int lane,
                                            FwdPixel &px, bool &warp_done, uint32_t &n_pairs, uint32_t &n_evals)
 {
+    const int q = lane >> 3;
     for (int c0 = 0; c0 < nb; c0 += 32) {
         const int j = c0 + lane;
-        const uint32_t hits = __ballot_sync(kFull, j < nb && overlaps(sm[j], wr));
-        uint32_t mask = hits, bits = 0;
+        const float4 box = j < nb ? sm[j].a : make_float4(0.f, 0.f, -1.f, -1.f);
+        const uint32_t done = __ballot_sync(kFull, px.done);
+        uint32_t m[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const bool live = ((done >> (8 * r)) & 0xffu) != 0xffu;
+            m[r] = __ballot_sync(kFull, live && box_overlaps(box, bx + 4 * (r & 1), by + 2 * (r >> 1), 3.0f, 1.0f));
+        }
+        uint32_t mask = q == 0 ? m[0] : (q == 1 ? m[1] : (q == 2 ? m[2] : m[3]));
+        uint32_t bits = 0;
         while (mask) {
             const int jj = c0 + __ffs(mask) - 1;
             mask &= mask - 1;
@@ -192,10 +226,10 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
     const int local = tile - v.tile_base;
     const int tx = local % v.tiles_x, ty = local / v.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * 4;
-    const int px = bx + (lane & 7), py = by + (lane >> 3);
+    const float bx = (float)(tx * TW + (warp % (TW / 8)) * 8), by = (float)(ty * TH + (warp / (TW / 8)) * 4);
+    const int2 pix = fwd_pixel<TW>(tx * TW, ty * TH, warp, lane);
+    const int px = pix.x, py = pix.y;
     const bool inside = px < v.W && py < v.H;
-    const WarpRect wr = {(float)bx, (float)by, (float)(bx + 7), (float)(by + 3)};
     const float qx = (float)px, qy = (float)py;
 
     FwdPixel st = {1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, !inside};
@@ -212,7 +246,7 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
         for (uint32_t b0 = s; b0 < e; b0 += B, parity ^= 1) {
             if (b0 + B < e) stage_batch<B>(sc, a, v, b0 + B, e, sm + (parity ^ 1) * B);
             const int nb = (int)min((uint32_t)B, e - b0);
-            if (!warp_done) walk_batch(sm + parity * B, nb, b0, s, tile, a, wr, qx, qy, lane, st, warp_done, n_pairs, n_evals);
+            if (!warp_done) walk_batch(sm + parity * B, nb, b0, s, tile, a, bx, by, qx, qy, lane, st, warp_done, n_pairs, n_evals);
             if (__syncthreads_and(st.done)) break;
         }
     }
@@ -222,7 +256,7 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
         stage_batch<B>(sc, a, v, b0, e, sm);
         __syncthreads();
         const int nb = (int)min((uint32_t)B, e - b0);
-        if (!warp_done) walk_batch(sm, nb, b0, s, tile, a, wr, qx, qy, lane, st, warp_done, n_pairs, n_evals);
+        if (!warp_done) walk_batch(sm, nb, b0, s, tile, a, bx, by, qx, qy, lane, st, warp_done, n_pairs, n_evals);
     }
 #endif
     if (inside) {
@@ -553,8 +587,8 @@ __global__ void __launch_bounds__(kBwdThreads, SGAD_BWD_MINBLOCKS)
 
 // ------------------------------------------------------------------ pair-parallel backward
 //
-// 256 threads per tile with the forward's pixel map (one pixel per thread, 8x4 pixels per
-// warp). The list is staged in batches of 256 entries (one per thread, batch starts at
+// 256 threads per tile with the forward's pixel map (one pixel per thread, fwd_pixel).
+// The list is staged in batches of 256 entries (one per thread, batch starts at
 // multiples of 256), walked from the tile's largest contributor count down. Each thread
 // walks only its own pixel's contributing entries, read from the forward's contribution
 // words (bit j of a chunk word), in reverse order: it recovers the transmittance by
@@ -574,8 +608,8 @@ __device__ __forceinline__ void bwdp_tile(const Scene &sc, const CompositeArgs &
     const int local = tile - v.tile_base;
     const int tx = local % v.tiles_x, ty = local / v.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = tx * TW + (warp % (TW / 8)) * 8 + (lane & 7);
-    const int py = ty * TH + (warp / (TW / 8)) * 4 + (lane >> 3);
+    const int2 pix = fwd_pixel<TW>(tx * TW, ty * TH, warp, lane);
+    const int px = pix.x, py = pix.y;
     const float qx = (float)px, qy = (float)py;
     const uint32_t s = a.off[tile];
     const int len = (int)(a.off[tile + 1] - s);
