@@ -40,10 +40,11 @@ if ROOT not in sys.path:
 METRIC = "fwd+bwd splat Mpix/s at 640x480x8 views; mapping secs to PSNR 30 dB vs plain"
 UNIT = "Mpix/s"
 WORKLOAD = "room8x640x480: 8 keyframes x 640x480 (2,457,600 Gaussians) -> 8 views 640x480, fx=600"
-# Algorithmic work per contributing (pixel, entry) pair, counted from the formulas:
-# forward 29 FP32 flops + 1 exp; backward 73 flops + 1 exp + 1 reciprocal.
-FLOPS_FWD_PAIR = 30.0
-FLOPS_BWD_PAIR = 75.0
+# Algorithmic work per contributing (pixel, entry) pair, counted operation by operation
+# from the compositing formulas (add, multiply, min and each prescribed threshold test 1,
+# FMA 2): forward 28 FP32 operations + 1 exp; backward 75 + 1 exp + 1 reciprocal.
+FLOPS_FWD_PAIR = 29.0
+FLOPS_BWD_PAIR = 77.0
 
 
 def parse():
@@ -415,7 +416,7 @@ def path_roofline(stages, stats, scene, peaks, fp32):
     Adam excluded): T_roof = max(B_alg / HBM, F_alg / FP32) against the measured stage
     time. B_alg per Gaussian: 28 B read forward, 28 B read backward, 24 B of gradients;
     per key: 12 B written and 12 B read; per view pixel: 20 B of images, 8 B of state
-    written and read, 20 B of image gradients. F_alg: 105 flops per contributing pair."""
+    written and read, 20 B of image gradients. F_alg: 106 flops per contributing pair."""
     if not stages:
         return None
     t_ms = sum(stages.get(k, 0.0) for k in ("binning", "emit", "sort", "composite_fwd", "composite_bwd", "finalize"))
