@@ -331,31 +331,32 @@ def split_of(sp):
 
 
 def run_e2e(mp, steps, stream, flush):
-    """Same metric through the public API with host buffers: each step copies the keyframe
-    parameter planes and the targets from pinned host memory, runs the iteration, and
-    reads the updated parameters and the loss back; copies and iteration are one CUDA
-    graph replay."""
+    """Same metric through the public API with host buffers: the window's keyframe planes,
+    targets and loss slot live in one pinned host buffer laid out like the device copy of
+    splat.upload_window; each step copies it in (one copy), runs the iteration on a
+    Mapper over those device views (the tuned options of `mp`), and reads the updated
+    parameters and the loss back (one copy); copies and iteration are one CUDA graph
+    replay."""
     import torch
-    host_in, dev_in = [], []
-    for k in mp.kfs:
-        for n in ("depth", "offset", "rgb", "logit", "scale"):
-            t = getattr(k, n)
-            host_in.append(t.detach().cpu().pin_memory())
-            dev_in.append(t)
-    for t in mp.trgb + mp.tdep:
-        host_in.append(t.detach().cpu().pin_memory())
-        dev_in.append(t)
-    dev_out = [getattr(k, n) for k in mp.kfs for n in ("offset", "rgb", "logit", "scale")] + [mp.loss]
-    host_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in dev_out]
-    bi = sum(t.numel() * t.element_size() for t in host_in)
-    bo = sum(t.numel() * t.element_size() for t in host_out)
+    from paper_2603_21055_gb300 import splat
+    from paper_2603_21055_gb300.mapping import Mapper
+    buf, n_state, kfs, trgb, tdep, loss = splat.upload_window(mp.scene)
+    m2 = Mapper(mp.scene, kfs=kfs, targets=(trgb, tdep), loss=loss, options=mp.sp.options)
+    for _ in range(3):
+        m2.step_eager()
+        torch.cuda.synchronize()
+        if m2.ensure_capacity():
+            break
+    assert m2.ensure_capacity(), "key capacity could not be met"
+    host_in = buf.cpu().pin_memory()
+    host_out = torch.empty(n_state, dtype=torch.float32, pin_memory=True)
+    bi = host_in.numel() * host_in.element_size()
+    bo = host_out.numel() * host_out.element_size()
 
     def body():
-        for h, d in zip(host_in, dev_in):
-            d.copy_(h, non_blocking=True)
-        mp.step_eager()
-        for d, h in zip(dev_out, host_out):
-            h.copy_(d, non_blocking=True)
+        buf.copy_(host_in, non_blocking=True)
+        m2.step_eager()
+        host_out.copy_(buf[:n_state], non_blocking=True)
 
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())

@@ -28,18 +28,26 @@ class Mapper:
     targets and the library workspace."""
 
     def __init__(self, scene, tile=(16, 16), slack: float = 1.3, lr: Optional[dict] = None,
-                 freeze_offset: bool = False, kfs=None, work_split: Optional[dict] = None):
+                 freeze_offset: bool = False, kfs=None, work_split: Optional[dict] = None, targets=None,
+                 loss: Optional[torch.Tensor] = None, options=None):
+        """kfs, targets ((rgb list, depth list)) and loss (one float) may be given as device
+        tensors (e.g. the views of splat.upload_window); options: a complete sgad_options
+        used instead of tile, freeze_offset and work_split."""
         self.scene = scene
         self.views = scene.views
         self.lr = dict(LR, **(lr or {}))
-        self.sp = splat.Splatter(tile=tile, freeze_offset=freeze_offset, **(work_split or {}))
+        if options is not None:
+            self.sp = splat.Splatter(options=options)
+            freeze_offset = bool(options.freeze_offset)
+        else:
+            self.sp = splat.Splatter(tile=tile, freeze_offset=freeze_offset, **(work_split or {}))
         self.kfs = kfs if kfs is not None else splat.upload_keyframes(scene)
-        self.trgb, self.tdep = splat.upload_targets(scene)
+        self.trgb, self.tdep = targets if targets is not None else splat.upload_targets(scene)
         self.images = splat.alloc_images(self.views)
         self.d_rgb = [torch.empty_like(im["rgb"]) for im in self.images]
         self.d_dep = [torch.empty_like(im["depth"]) for im in self.images]
         self.gin = [dict(rgb=r, depth=d) for r, d in zip(self.d_rgb, self.d_dep)]
-        self.loss = torch.zeros(1, device="cuda")
+        self.loss = loss if loss is not None else torch.zeros(1, device="cuda")
         self.valid = torch.zeros(len(self.views), dtype=torch.int32, device="cuda")
         self.grads = [dict(d_offset=torch.empty_like(k.offset), d_rgb=torch.empty_like(k.rgb),
                            d_logit=torch.empty_like(k.logit), d_scale=torch.empty_like(k.scale))

@@ -60,6 +60,41 @@ def upload_targets(scene, device="cuda"):
     return [f(r) for r in scene.target_rgb], [f(d) for d in scene.target_depth]
 
 
+def upload_window(scene, device="cuda"):
+    """The keyframes, the targets and a loss slot of one mapping window as views of one
+    flat FP32 device buffer, each array starting on a 256-byte boundary, laid out as
+    [per keyframe: offset, rgb, logit, scale] [loss] [per keyframe: depth] [per view:
+    target rgb, target depth]. What a mapping step updates is the prefix of `n_state`
+    floats, so moving a window between host and device takes one copy each way.
+    Returns (buffer, n_state, keyframes, target_rgb, target_depth, loss)."""
+    state = [(k, n) for k in scene.keyframes for n in ("offset", "rgb", "logit", "scale")]
+    rest = [(k, "depth") for k in scene.keyframes]
+    arrays = [np.ascontiguousarray(getattr(k, n), np.float32) for k, n in state]
+    arrays.append(np.zeros(1, np.float32))                               # loss
+    arrays += [np.ascontiguousarray(k.depth, np.float32) for k, _ in rest]
+    arrays += [np.ascontiguousarray(a, np.float32) for a in scene.target_rgb]
+    arrays += [np.ascontiguousarray(a, np.float32) for a in scene.target_depth]
+    offs, n = [], 0
+    for a in arrays:
+        offs.append(n)
+        n += (a.size + 63) // 64 * 64
+    host = np.zeros(n, np.float32)
+    for a, o in zip(arrays, offs):
+        host[o:o + a.size] = a.ravel()
+    buf = torch.as_tensor(host).to(device)
+    views = [buf[o:o + a.size].view(a.shape) for a, o in zip(arrays, offs)]
+    n_state = offs[len(state)] + 64
+    ns = len(state)
+    kfs = []
+    for i, k in enumerate(scene.keyframes):
+        off, rgb, logit, scale = views[4 * i:4 * i + 4]
+        kfs.append(DeviceKeyframe(k.cam, views[ns + 1 + i], off, rgb, logit, scale, bool(k.learnable)))
+    nk, nv = len(scene.keyframes), len(scene.views)
+    trgb = views[ns + 1 + nk:ns + 1 + nk + nv]
+    tdep = views[ns + 1 + nk + nv:ns + 1 + nk + 2 * nv]
+    return buf, n_state, kfs, trgb, tdep, views[ns]
+
+
 def _schedule(x) -> int:
     if isinstance(x, str):
         names = {v: k for k, v in B.SCHEDULE_NAMES.items()}
@@ -80,7 +115,17 @@ class Splatter:
 
     def __init__(self, tile=(16, 16), bg=(0.0, 0.0, 0.0), sort_smem_cap: int = 0, freeze_offset: bool = False,
                  fwd_batch: int = 0, bwd_batch: int = 0, fwd_schedule="tiles", bwd_schedule="tiles",
-                 bwd_algorithm: str = "warp_reduce"):
+                 bwd_algorithm: str = "warp_reduce", options=None):
+        """options: a complete sgad_options (e.g. another Splatter's tuned options), used
+        instead of the other arguments."""
+        if options is not None:
+            self.options = B.sgad_options.from_buffer_copy(options)
+            self.ctx = B.sgad_create(self.options)
+            self.workspace: Optional[torch.Tensor] = None
+            self.key_capacity = 0
+            self._cache = {}
+            self._ssim_ws: Optional[torch.Tensor] = None
+            return
         o = B.sgad_default_options()
         o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
         for i in range(3):

@@ -145,3 +145,27 @@ def test_mapping_reduces_loss_and_raises_psnr(room2):
     l1, p1 = mp.loss.item(), mp.psnr()
     print("loss %.5f -> %.5f, PSNR %.2f -> %.2f dB" % (l0, l1, p0, p1))
     assert l1 < 0.8 * l0 and p1 > p0 + 1.0
+
+
+def test_packed_window_matches_separate_tensors(scene1):
+    """A Mapper over the views of one flat window buffer (splat.upload_window, the layout
+    the end-to-end measurement copies in one piece) takes the same iterations as one over
+    separately allocated tensors: same loss, same updated parameters."""
+    import torch
+    from paper_2603_21055_gb300 import splat
+    from paper_2603_21055_gb300.mapping import Mapper
+    m1 = Mapper(scene1)
+    buf, n_state, kfs, trgb, tdep, loss = splat.upload_window(scene1)
+    m2 = Mapper(scene1, kfs=kfs, targets=(trgb, tdep), loss=loss, options=m1.sp.options)
+    for _ in range(3):
+        m1.step_eager()
+        m2.step_eager()
+        torch.cuda.synchronize()
+        assert abs(float(m1.loss) - float(m2.loss)) <= 1e-6 * abs(float(m1.loss))
+    for a, b in zip(m1.kfs, m2.kfs):
+        for n in ("offset", "rgb", "logit", "scale"):
+            x, y = getattr(a, n), getattr(b, n)
+            assert torch.allclose(x, y, rtol=1e-5, atol=1e-7), n
+    host = buf[:n_state].cpu()                                   # the prefix is the updated state
+    off = (m2.kfs[0].rgb.data_ptr() - buf.data_ptr()) // 4
+    assert torch.equal(host[off:off + m2.kfs[0].rgb.numel()], m2.kfs[0].rgb.flatten().cpu())
