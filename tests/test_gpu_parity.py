@@ -88,6 +88,15 @@ def test_global_memory_sort_path(crop):
     compare_images(res, ref)
 
 
+@pytest.mark.parametrize("cap", [100, 6145, 12288])
+def test_sort_capacities(crop, cap):
+    """Shared-memory sort capacities other than the default 6144: a small one (chunks of
+    100 merged through global memory) and the larger ones served by 24 entries per
+    thread."""
+    res = gpu_run(crop, sort_smem_cap=cap)
+    compare_keys(res, crop)
+
+
 def test_background_and_zero_opacity(scene1):
     """All opacities at zero: the image is exactly the background, nothing contributes,
     every gradient but colour-free terms is zero."""
