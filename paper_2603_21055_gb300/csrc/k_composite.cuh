@@ -44,14 +44,23 @@
 namespace sgad {
 
 constexpr int kFwdThreads = 256;
-constexpr int kBwdThreads = 128;
+// Backward pixels per lane: 2 (each warp an 8x8 block, 128 threads per tile) or 1 (each
+// warp an 8x4 block, 256 threads per tile). One pixel walks 1.3x the (warp, entry) hits
+// with half the arithmetic per hit and no spills; on the room workload both take the
+// same time, and 2 stays the default.
+#ifndef SGAD_BWD_PX
+#define SGAD_BWD_PX 2
+#endif
+constexpr int kBwdPx = SGAD_BWD_PX;
+static_assert(kBwdPx == 1 || kBwdPx == 2, "one or two backward pixels per lane");
+constexpr int kBwdThreads = 256 / kBwdPx;
 constexpr unsigned kFull = 0xffffffffu;
 // Resident-block targets (they bound the registers per thread).
 #ifndef SGAD_FWD_MINBLOCKS
 #define SGAD_FWD_MINBLOCKS 6
 #endif
 #ifndef SGAD_BWD_MINBLOCKS
-#define SGAD_BWD_MINBLOCKS 8
+#define SGAD_BWD_MINBLOCKS (kBwdPx == 2 ? 8 : 4)
 #endif
 
 // Launch arguments common to both directions.
@@ -419,25 +428,31 @@ template <int TW, int TH, int B, bool POSE>
 __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a, int tile, Staged *sm, uint32_t *sg,
                                          float (*acc)[11], int *s_nmax, float *s_pose)
 {
-    static_assert(TW * TH == 2 * kBwdThreads, "tile must hold 256 pixels");
+    static_assert(TW * TH == kBwdPx * kBwdThreads, "tile must hold 256 pixels");
     const ViewDev &v = sc.view[find_view_of_tile(sc, tile)];
     const int local = tile - v.tile_base;
     const int tx = local % v.tiles_x, ty = local / v.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * 8;
+    const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * (4 * kBwdPx);
     const int px = bx + (lane & 7);
-    const int py[2] = {by + (lane >> 3), by + (lane >> 3) + 4};
-    const WarpRect wr = {(float)bx, (float)by, (float)(bx + 7), (float)(by + 7)};
+    int py[kBwdPx];
+    float qy[kBwdPx];
+#pragma unroll
+    for (int p = 0; p < kBwdPx; ++p) {
+        py[p] = by + (lane >> 3) + 4 * p;
+        qy[p] = (float)py[p];
+    }
+    const WarpRect wr = {(float)bx, (float)by, (float)(bx + 7), (float)(by + 4 * kBwdPx - 1)};
     const float qx = (float)px;
-    const float qy[2] = {(float)py[0], (float)py[1]};
     const uint32_t s = a.off[tile];
     const int len = (int)(a.off[tile + 1] - s);
     const size_t hw = (size_t)v.W * v.H;
 
-    float Tf[2], gr[2], gg[2], gb[2], gD[2], gA[2], T[2], SCr[2], SCg[2], SCb[2], SD[2], SA[2];
-    int nc[2];
+    float Tf[kBwdPx], gr[kBwdPx], gg[kBwdPx], gb[kBwdPx], gD[kBwdPx], gA[kBwdPx], T[kBwdPx], SCr[kBwdPx],
+        SCg[kBwdPx], SCb[kBwdPx], SD[kBwdPx], SA[kBwdPx];
+    int nc[kBwdPx];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < kBwdPx; ++p) {
         Tf[p] = 1.0f;
         gr[p] = gg[p] = gb[p] = gD[p] = gA[p] = 0.f;
         nc[p] = 0;
@@ -456,7 +471,7 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
         T[p] = Tf[p];
         SCr[p] = SCg[p] = SCb[p] = SD[p] = SA[p] = 0.f;
     }
-    const int warp_nc = __reduce_max_sync(kFull, (unsigned)max(nc[0], nc[1]));
+    const int warp_nc = __reduce_max_sync(kFull, (unsigned)(kBwdPx == 2 ? max(nc[0], nc[kBwdPx - 1]) : nc[0]));
     __syncthreads();     // the previous tile's readers of *s_nmax are done
     if (POSE && threadIdx.x < 12) s_pose[threadIdx.x] = 0.f;
     if (threadIdx.x == 0) *s_nmax = 0;
@@ -464,9 +479,9 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
     if (lane == 0) atomicMax(s_nmax, warp_nc);
     __syncthreads();
     const int nmax = *s_nmax;
-    float bgdot[2];
+    float bgdot[kBwdPx];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) bgdot[p] = sc.bg[0] * gr[p] + sc.bg[1] * gg[p] + sc.bg[2] * gb[p];
+    for (int p = 0; p < kBwdPx; ++p) bgdot[p] = sc.bg[0] * gr[p] + sc.bg[1] * gg[p] + sc.bg[2] * gb[p];
 
     for (int b1 = nmax; b1 > 0; b1 -= B) {
         const int b0 = b1 > B ? b1 - B : 0;
@@ -500,7 +515,7 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
                     bool contrib = false;
                     const Staged st = sm[jj];
 #pragma unroll
-                    for (int p = 0; p < 2; ++p) {
+                    for (int p = 0; p < kBwdPx; ++p) {
                         if (b0 + jj >= nc[p]) continue;
                         float dx, dy, ep, alpha;
                         if (!gauss_alpha(st, qx, qy[p], dx, dy, ep, alpha)) continue;
