@@ -119,26 +119,21 @@ class Splatter:
         """options: a complete sgad_options (e.g. another Splatter's tuned options), used
         instead of the other arguments."""
         if options is not None:
-            self.options = B.sgad_options.from_buffer_copy(options)
-            self.ctx = B.sgad_create(self.options)
-            self.workspace: Optional[torch.Tensor] = None
-            self.key_capacity = 0
-            self._cache = {}
-            self._ssim_ws: Optional[torch.Tensor] = None
-            return
-        o = B.sgad_default_options()
-        o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
-        for i in range(3):
-            o.bg[i] = float(bg[i])
-        o.sort_smem_cap = int(sort_smem_cap)
-        o.freeze_offset = int(bool(freeze_offset))
-        if fwd_batch:
-            o.fwd_batch = int(fwd_batch)
-        if bwd_batch:
-            o.bwd_batch = int(bwd_batch)
-        o.fwd_schedule = _schedule(fwd_schedule)
-        o.bwd_schedule = _schedule(bwd_schedule)
-        o.bwd_algorithm = {"pairs": B.SGAD_BWD_PAIRS, "warp_reduce": B.SGAD_BWD_WARP_REDUCE}[bwd_algorithm]
+            o = B.sgad_options.from_buffer_copy(options)
+        else:
+            o = B.sgad_default_options()
+            o.tile_w, o.tile_h = int(tile[0]), int(tile[1])
+            for i in range(3):
+                o.bg[i] = float(bg[i])
+            o.sort_smem_cap = int(sort_smem_cap)
+            o.freeze_offset = int(bool(freeze_offset))
+            if fwd_batch:
+                o.fwd_batch = int(fwd_batch)
+            if bwd_batch:
+                o.bwd_batch = int(bwd_batch)
+            o.fwd_schedule = _schedule(fwd_schedule)
+            o.bwd_schedule = _schedule(bwd_schedule)
+            o.bwd_algorithm = {"pairs": B.SGAD_BWD_PAIRS, "warp_reduce": B.SGAD_BWD_WARP_REDUCE}[bwd_algorithm]
         self.options = o
         self.ctx = B.sgad_create(o)
         self.workspace: Optional[torch.Tensor] = None
