@@ -454,7 +454,9 @@ def roofline(stages, stats, scene, peaks, src, bwd_kernel="k_composite_bwdp", fp
             peak = fp32["measured_tflops"]
             peak_note = "FP32 FMA throughput of measured (sgad_fma_burn on this GPU)"
     else:
-        # algorithmic bytes of the HBM-bound stages
+        # algorithmic bytes of the HBM-bound stages: sort 16 B per key (read and write 8 B);
+        # emission 40 B per Gaussian + 8 B per key; projection and count 60 B per Gaussian;
+        # finalisation 68 B per Gaussian
         byts = {"sort": nk * 16, "emit": ng * 40 + nk * 8, "binning": ng * 60,
                 "finalize": ng * (32 + 12 + 24)}[name]
         work = byts
