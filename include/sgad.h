@@ -173,8 +173,10 @@ const char *sgad_last_error(void);
  * (tile, Gaussian) keys. Host arithmetic only. The workspace holds the per-Gaussian
  * world records and gradient accumulators (64 B per Gaussian), per-tile offsets,
  * counters and heavy-first order (12 B per tile), the per-pixel state kept for the
- * backward pass (8 B per view pixel), two key arrays (16 B per key) and the per-pixel
- * contribution words of the pair-parallel backward (32 B per key + 1 KB per tile). */
+ * backward pass (8 B per view pixel), two key arrays (16 B per key), the per-pixel
+ * contribution words of the pair-parallel backward (32 B per key + 1 KB per tile) and
+ * the per-warp contribution masks the forward leaves for the warp-reduced backward
+ * (1 B per key + 64 B per tile). */
 sgad_status sgad_workspace_size(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                                 const sgad_camera *views, int32_t n_views, int64_t key_capacity,
                                 size_t *bytes);
@@ -388,7 +390,8 @@ sgad_status sgad_adam_step_multi(int32_t n_tensors, const sgad_adam_tensor *tens
  * Same arguments and results as sgad_forward(), without the workspace: the scratch is a
  * static device array of SGAD_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
  * that loads the library holds until the process exits. Problems whose workspace does
- * not fit (64 B per Gaussian, 8 B per view pixel, 16 B per key, plus per-tile offsets)
+ * not fit (the workspace of sgad_workspace_size: 64 B per Gaussian, 8 B per view
+ * pixel, 49 B per key and ~1.1 KB per tile)
  * are rejected with SGAD_ERR_WORKSPACE_TOO_SMALL before anything is launched; a forward
  * whose keys exceed the room left returns SGAD_ERR_KEY_OVERFLOW. The call synchronises
  * `stream` to report that status. The first call on a device looks up the array's device

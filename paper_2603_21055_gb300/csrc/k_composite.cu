@@ -50,11 +50,13 @@ cudaError_t persistent_blocks(bool fwd, int batch, const Scene &sc, int *blocks)
 
 cudaError_t launch_composite(bool fwd, int batch, int schedule, const Scene &sc, const World *world,
                              const uint32_t *off, const uint64_t *entries, float *pix_t, uint32_t *pix_n, float4 *gacc,
-                             WsHeader *hdr, const uint32_t *order, uint32_t *contrib, cudaStream_t st)
+                             WsHeader *hdr, const uint32_t *order, uint32_t *contrib, uint32_t *wmask,
+                             cudaStream_t st)
 {
     if (sc.n_tiles <= 0) return cudaSuccess;
     CompositeArgs a = {};
     a.contrib = contrib;
+    a.wmask = wmask;
     for (int i = 0; i < sc.n_views && !fwd; ++i)
         if (sc.view[i].d_pose) a.pose = 1;
     a.world = world;

@@ -80,8 +80,15 @@ struct CompositeArgs {
     // pixel), word contrib[8 off[t] + 256 t + 256 c + i] has bit j set iff entry 32c + j
     // contributed to that pixel. Written for every chunk the pixel's warp walked.
     uint32_t *contrib;
+    // Per-warp contribution masks (forward writes, warp-reduced backward reads): for tile
+    // t, list chunk c and forward warp w (its 8x4 pixel block), word
+    // wmask[(off[t] >> 2) + 16 t + 8 c + w] has bit j set iff entry 32c + j contributed to
+    // a pixel of that block. Written for every chunk the warp walked.
+    uint32_t *wmask;
     int32_t pose;                 // some view wants its pose gradient (selects the kernel variant)
 };
+
+__device__ __forceinline__ size_t wmask_base(int tile, uint32_t s) { return (size_t)(s >> 2) + 16 * (size_t)tile; }
 
 __device__ __forceinline__ size_t contrib_base(const CompositeArgs &a, int tile, uint32_t s)
 {
@@ -179,7 +186,8 @@ __device__ __forceinline__ int2 fwd_pixel(int ox, int oy, int warp, int lane)
 // each group walks its entries in order for every pixel not yet done.
 __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0, uint32_t s, int tile,
                                            const CompositeArgs &a, float bx, float by, float qx, float qy, int lane,
-                                           FwdPixel &px, bool &warp_done, uint32_t &n_pairs, uint32_t &n_evals)
+                                           FwdPixel &px, bool &warp_done, uint32_t &n_pairs, uint32_t &n_evals,
+                                           uint32_t *wmw)
 {
     const int q = lane >> 3;
     for (int c0 = 0; c0 < nb; c0 += 32) {
@@ -219,6 +227,10 @@ __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0
             px.last = (int)(b0 + jj - s);
         }
         if (a.contrib) a.contrib[contrib_base(a, tile, s) + (size_t)((b0 - s + c0) >> 5) * 256 + threadIdx.x] = bits;
+        if (wmw) {
+            const uint32_t wbits = __reduce_or_sync(kFull, bits);
+            if (lane == 0) wmw[(b0 - s + c0) >> 2] = wbits;        // chunk (b0 - s + c0) / 32, 8 words each
+        }
         if (__all_sync(kFull, px.done)) {
             warp_done = true;
             break;
@@ -244,6 +256,9 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
     FwdPixel st = {1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, !inside};
     bool warp_done = __all_sync(kFull, st.done);
     const uint32_t s = a.off[tile], e = a.off[tile + 1];
+    // this warp's contribution-mask word of chunk 0; chunk c's is 8 c words further, i.e.
+    // at offset (32 c) / 4
+    uint32_t *wmw = a.wmask ? a.wmask + wmask_base(tile, s) + warp : nullptr;
 #if SGAD_FWD_DOUBLE_BUFFER
     // Two staging buffers: batch k + 1 is staged into the other buffer before batch k is
     // walked, so one block barrier per batch both publishes the next batch and ends the
@@ -255,7 +270,7 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
         for (uint32_t b0 = s; b0 < e; b0 += B, parity ^= 1) {
             if (b0 + B < e) stage_batch<B>(sc, a, v, b0 + B, e, sm + (parity ^ 1) * B);
             const int nb = (int)min((uint32_t)B, e - b0);
-            if (!warp_done) walk_batch(sm + parity * B, nb, b0, s, tile, a, bx, by, qx, qy, lane, st, warp_done, n_pairs, n_evals);
+            if (!warp_done) walk_batch(sm + parity * B, nb, b0, s, tile, a, bx, by, qx, qy, lane, st, warp_done, n_pairs, n_evals, wmw);
             if (__syncthreads_and(st.done)) break;
         }
     }
@@ -265,7 +280,7 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
         stage_batch<B>(sc, a, v, b0, e, sm);
         __syncthreads();
         const int nb = (int)min((uint32_t)B, e - b0);
-        if (!warp_done) walk_batch(sm, nb, b0, s, tile, a, bx, by, qx, qy, lane, st, warp_done, n_pairs, n_evals);
+        if (!warp_done) walk_batch(sm, nb, b0, s, tile, a, bx, by, qx, qy, lane, st, warp_done, n_pairs, n_evals, wmw);
     }
 #endif
     if (inside) {
@@ -442,7 +457,6 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
         py[p] = by + (lane >> 3) + 4 * p;
         qy[p] = (float)py[p];
     }
-    const WarpRect wr = {(float)bx, (float)by, (float)(bx + 7), (float)(by + 4 * kBwdPx - 1)};
     const float qx = (float)px;
     const uint32_t s = a.off[tile];
     const int len = (int)(a.off[tile + 1] - s);
@@ -472,6 +486,13 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
         SCr[p] = SCg[p] = SCb[p] = SD[p] = SA[p] = 0.f;
     }
     const int warp_nc = __reduce_max_sync(kFull, (unsigned)(kBwdPx == 2 ? max(nc[0], nc[kBwdPx - 1]) : nc[0]));
+    // The forward warps (8x4 blocks) whose pixels are this warp's: their contribution
+    // masks hold the entries that reach a pixel here, valid for the chunks in front of
+    // their largest contributor count (the chunks the forward walked).
+    const int fw0 = ((by - ty * TH) >> 2) * (TW / 8) + ((bx - tx * TW) >> 3);
+    const int fnc0 = __reduce_max_sync(kFull, (unsigned)nc[0]);
+    const int fnc1 = kBwdPx == 2 ? (int)__reduce_max_sync(kFull, (unsigned)nc[kBwdPx - 1]) : 0;
+    const uint32_t *wm = a.wmask + wmask_base(tile, s);
     __syncthreads();     // the previous tile's readers of *s_nmax are done
     if (POSE && threadIdx.x < 12) s_pose[threadIdx.x] = 0.f;
     if (threadIdx.x == 0) *s_nmax = 0;
@@ -501,14 +522,18 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
         }
         __syncthreads();
         if (b0 < warp_nc) {
-            for (int c0 = ((nb - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
-                const int j = c0 + lane;
-                const uint32_t hits = __ballot_sync(kFull, j < nb && b0 + j < warp_nc && overlaps(sm[j], wr));
-                uint32_t mask = hits;
+            // the tile list's chunks (32 entries from the list start) that meet this batch,
+            // last first; each walks the entries that reach a pixel of the warp's block
+            for (int c = (b1 - 1) >> 5; c >= (b0 >> 5); --c) {
+                uint32_t mask = (32 * c < fnc0 ? wm[8 * c + fw0] : 0u) |
+                                (kBwdPx == 2 && 32 * c < fnc1 ? wm[8 * c + fw0 + TW / 8] : 0u);
+                const int lo = b0 - 32 * c, hi = b1 - 32 * c;             // batch range in the chunk
+                if (lo > 0) mask &= ~0u << lo;
+                if (hi < 32) mask &= (1u << hi) - 1u;
                 while (mask) {
                     const int bit = 31 - __clz(mask);
                     mask &= ~(1u << bit);
-                    const int jj = c0 + bit;
+                    const int jj = 32 * c + bit - b0;
                     float val[10];
 #pragma unroll
                     for (int q = 0; q < 10; ++q) val[q] = 0.f;

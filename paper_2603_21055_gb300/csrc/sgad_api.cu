@@ -14,7 +14,7 @@ void launch_scan_tiles(uint32_t *, uint32_t *, int, uint64_t, WsHeader *, uint32
 void launch_emit(const Scene &, const World *, const uint32_t *, uint32_t *, uint64_t *, WsHeader *, cudaStream_t);
 cudaError_t launch_sort_tiles(const uint32_t *, uint64_t *, uint64_t *, int, int, const WsHeader *, cudaStream_t);
 cudaError_t launch_composite(bool, int, int, const Scene &, const World *, const uint32_t *, const uint64_t *, float *,
-                             uint32_t *, float4 *, WsHeader *, const uint32_t *, uint32_t *, cudaStream_t);
+                             uint32_t *, float4 *, WsHeader *, const uint32_t *, uint32_t *, uint32_t *, cudaStream_t);
 bool valid_batch(int, bool);
 void launch_finalize(const Scene &, const World *, const float4 *, cudaStream_t);
 void launch_l1_batch(int, const float *const *, const float *const *, const float *const *, const float *const *,
@@ -174,6 +174,7 @@ struct Ws {
     uint64_t *keys() const { return reinterpret_cast<uint64_t *>(base + L.keys); }
     uint64_t *keys_alt() const { return reinterpret_cast<uint64_t *>(base + L.keys_alt); }
     uint32_t *contrib() const { return reinterpret_cast<uint32_t *>(base + L.contrib); }
+    uint32_t *wmask() const { return reinterpret_cast<uint32_t *>(base + L.wmask); }
 };
 
 sgad_status get_ws(const Scene &sc, uint64_t n_pix, void *workspace, size_t ws_bytes, int64_t key_cap, Ws &ws)
@@ -244,7 +245,7 @@ sgad_status run_composite(const sgad_ctx *ctx, bool fwd, int batch, int schedule
     uint32_t *contrib = (!fwd || ctx->opt.bwd_algorithm == SGAD_BWD_PAIRS) ? ws.contrib() : nullptr;
     const cudaError_t e = launch_composite(fwd, batch, schedule, sc, ws.world(), ws.tile_off(), ws.keys(), ws.pix_t(),
                                            ws.pix_n(), fwd ? nullptr : ws.gacc(), ws.hdr(), ws.tile_order(), contrib,
-                                           st);
+                                           ws.wmask(), st);
     return e == cudaSuccess ? SGAD_OK : cuda_fail(e, fwd ? "forward compositing launch" : "backward compositing launch");
 }
 

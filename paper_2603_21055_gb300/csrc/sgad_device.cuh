@@ -307,21 +307,10 @@ __device__ __forceinline__ bool gauss_alpha(const Staged &s, float qx, float qy,
     return alpha >= kAlphaFloor;
 }
 
-// Warp's pixel block inside a tile: 8 x 4 pixels per warp.
-struct WarpRect {
-    float x0, y0, x1, y1;
-};
-
-__device__ __forceinline__ bool overlaps(const Staged &s, const WarpRect &r)
-{
-    return s.a.z >= 0.0f && s.a.x + s.a.z >= r.x0 && s.a.x - s.a.z <= r.x1 && s.a.y + s.a.w >= r.y0 &&
-           s.a.y - s.a.w <= r.y1;
-}
-
 // Workspace layout (byte offsets, 256-aligned sections). Shared by the host API and the
 // kernels' launch code.
 struct Layout {
-    size_t header, world, gacc, tile_off, tile_cnt, tile_order, pix_t, pix_n, keys, keys_alt, contrib, total;
+    size_t header, world, gacc, tile_off, tile_cnt, tile_order, pix_t, pix_n, keys, keys_alt, contrib, wmask, total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -341,6 +330,7 @@ inline Layout make_layout(uint64_t n_gauss, uint64_t n_tiles, uint64_t n_pix, ui
     L.keys = o; o = align256(o + key_cap * 8);
     L.keys_alt = o; o = align256(o + key_cap * 8);
     L.contrib = o; o = align256(o + (key_cap * 8 + (n_tiles + 1) * 256) * 4);
+    L.wmask = o; o = align256(o + ((key_cap >> 2) + (n_tiles + 1) * 16 + 8) * 4);
     L.total = o;
     return L;
 }

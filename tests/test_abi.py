@@ -101,15 +101,19 @@ def _cam(w=64, h=48):
 def test_workspace_size_arithmetic():
     """Workspace = header + 64 B per Gaussian + tile offsets/counters/order + 8 B per view
     pixel + 16 B per key of key arrays + 32 B per key (+ 1 KB per tile) of contribution
-    words, each section rounded to 256 B."""
+    words + one word per 4 keys (+ 16 per tile and 8) of per-warp contribution masks, each
+    section rounded to 256 B."""
     ctx = B.sgad_create()
     kfs = (B.sgad_keyframe * 1)()
     kfs[0].cam = _cam()
     views = (B.sgad_camera * 2)(_cam(), _cam(100, 70))
     n0 = B.sgad_workspace_size(ctx, kfs, views, 0)
     n1 = B.sgad_workspace_size(ctx, kfs, views, 1000)
-    # two 8-byte key arrays and 32 bytes of contribution words per key
-    assert n1 - n0 == 2 * ((1000 * 8 + 255) // 256 * 256) + 1000 * 32
+    r = lambda x: (x + 255) // 256 * 256
+    tiles = 4 * 3 + 7 * 5
+    # two 8-byte key arrays, 32 bytes of contribution words per key, the mask words
+    masks = r(4 * ((1000 >> 2) + 16 * (tiles + 1) + 8)) - r(4 * (16 * (tiles + 1) + 8))
+    assert n1 - n0 == 2 * r(1000 * 8) + 1000 * 32 + masks
     ng, npx = 64 * 48, 64 * 48 + 100 * 70
     assert n0 >= 256 + 64 * ng + 8 * npx
     B.sgad_destroy(ctx)
