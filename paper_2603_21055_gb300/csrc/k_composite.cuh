@@ -12,17 +12,21 @@
 // box reaches its block, the four groups side by side in the same instructions. Small
 // groups cut the (pixel, entry) pairs a walk evaluates for nothing: an entry whose box
 // touches the warp's block usually misses most of its pixels. A group stops when its
-// pixels are done, a warp when its groups are, the block when all warps are.
+// pixels are done, a warp when its groups are, the block when all warps are. For every
+// 32-entry chunk it walked, a warp also writes the OR of its lanes' contribution bits:
+// which entries reached a pixel of its block.
 //
 // Backward: 128 threads per tile, each warp an 8x8 pixel block and each lane the pixels
 // (x, y) and (x, y + 4). The same lists are walked from the tile's largest contributor
-// count down to 0. (Splitting the warp into groups as in the forward walks fewer
-// entries here too, but each step then carries more state and a group-wise reduction,
-// and it measured slower.) Each pixel starts from its saved final transmittance and
-// recovers the transmittance in front of entry i by division,
-// T_i = T_{i+1} / (1 - alpha_i), which is stable because alpha <= 0.99. Per
-// (pixel, entry) it forms the gradient of the colour,
-// depth and alpha terms; the moments of the lane's two pixels are summed in registers,
+// count down to 0, each warp over exactly the entries that reached a pixel of its block
+// (the masks of the two forward warps that cover it, for the chunks in front of their
+// largest contributor counts), so no step is spent on an entry that contributes nowhere
+// in the block. (Splitting the warp into groups as in the forward walks fewer entries
+// too, but each step then carries more state and a group-wise reduction, and it measured
+// slower.) Each pixel starts from its saved final transmittance and recovers the
+// transmittance in front of entry i by division, T_i = T_{i+1} / (1 - alpha_i), which
+// is stable because alpha <= 0.99. Per (pixel, entry) it forms the gradient of the
+// colour, depth and alpha terms; the moments of the lane's two pixels are summed in registers,
 // reduced over the warp with a reduce-scatter and accumulated per staged Gaussian in
 // shared memory. At the end of the batch each staging thread turns them into d mu, d s,
 // d opacity and d colour and adds them to the per-Gaussian accumulator with two 16-byte
