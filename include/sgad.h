@@ -192,8 +192,10 @@ sgad_status sgad_count_keys(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_k
 /* Forward splatting (Sec. 3.2, splat(G, p_k)) of all keyframes into all views:
  * projection and tile binning of every (Gaussian, view) pair, a per-tile sort by
  * (depth, index), and front-to-back compositing of colour, depth and alpha.
- * out[k] receives view k. The per-pixel final transmittance and contributor count and
- * the sorted tile lists are kept in the workspace for sgad_backward(). If the keys do
+ * out[k] receives view k. The per-pixel final transmittance and contributor count, the
+ * sorted tile lists and, per warp of 8x4 pixels and chunk of 32 list entries, the mask
+ * of entries that reached one of those pixels are kept in the workspace for
+ * sgad_backward(). If the keys do
  * not fit in key_capacity the outputs are left untouched and sgad_check() reports
  * SGAD_ERR_KEY_OVERFLOW together with the count needed. */
 sgad_status sgad_forward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
@@ -201,9 +203,10 @@ sgad_status sgad_forward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                          void *workspace, size_t ws_bytes, int64_t key_capacity, void *stream);
 
 /* Adjoint of the last sgad_forward() on this workspace (same kfs, views and options):
- * walks every pixel's list back to front, recomputing transmittance by division from
- * the saved final value, and accumulates d loss / d (offset, colour, opacity logit,
- * scale) of every learnable keyframe, summed over views. */
+ * walks every pixel's list back to front over the entries the forward's masks mark,
+ * recomputing transmittance by division from the saved final value, and accumulates
+ * d loss / d (offset, colour, opacity logit, scale) of every learnable keyframe, summed
+ * over views. */
 sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                           const sgad_camera *views, int32_t n_views,
                           const sgad_image_grads *grad_in, sgad_keyframe_grads *grads_out,
