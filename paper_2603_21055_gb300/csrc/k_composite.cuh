@@ -16,19 +16,19 @@
 // 32-entry chunk it walked, a warp also writes the OR of its lanes' contribution bits:
 // which entries reached a pixel of its block.
 //
-// Backward: 128 threads per tile, each warp an 8x8 pixel block and each lane the pixels
-// (x, y) and (x, y + 4). The same lists are walked from the tile's largest contributor
-// count down to 0, each warp over exactly the entries that reached a pixel of its block
-// (the masks of the two forward warps that cover it, for the chunks in front of their
-// largest contributor counts), so no step is spent on an entry that contributes nowhere
-// in the block. (Splitting the warp into groups as in the forward walks fewer entries
+// Backward: 256 threads per tile, each warp an 8x4 pixel block and each lane one pixel
+// (two pixels per lane on 8x8 blocks is a build option). The same lists are walked from
+// the tile's largest contributor count down to 0, each warp over exactly the entries that
+// reached a pixel of its block (the mask of the forward warp with the same block, or of
+// the two that cover an 8x8 block, for the chunks in front of their largest contributor
+// counts), so no step is spent on an entry that contributes nowhere in the block. (Splitting the warp into groups as in the forward walks fewer entries
 // too, but each step then carries more state and a group-wise reduction, and it measured
 // slower.) Each pixel starts from its saved final transmittance and recovers the
 // transmittance in front of entry i by division, T_i = T_{i+1} / (1 - alpha_i), which
 // is stable because alpha <= 0.99. Per (pixel, entry) it forms the gradient of the
-// colour, depth and alpha terms; the moments of the lane's two pixels are summed in registers,
-// reduced over the warp with a reduce-scatter and accumulated per staged Gaussian in
-// shared memory. At the end of the batch each staging thread turns them into d mu, d s,
+// colour, depth and alpha terms; the moments of the lane's pixels are summed in
+// registers, reduced over the warp with a reduce-scatter (two entries at a time) and
+// accumulated per staged Gaussian in shared memory. At the end of the batch each staging thread turns them into d mu, d s,
 // d opacity and d colour and adds them to the per-Gaussian accumulator with two 16-byte
 // vector atomics.
 //
@@ -48,12 +48,12 @@
 namespace sgad {
 
 constexpr int kFwdThreads = 256;
-// Backward pixels per lane: 2 (each warp an 8x8 block, 128 threads per tile) or 1 (each
-// warp an 8x4 block, 256 threads per tile). One pixel walks 1.3x the (warp, entry) hits
-// with half the arithmetic per hit and no spills; on the room workload both take the
-// same time, and 2 stays the default.
+// Backward pixels per lane: 1 (each warp an 8x4 block, 256 threads per tile; the
+// default) or 2 (each warp an 8x8 block, 128 threads per tile). One pixel per lane walks
+// more (warp, entry) steps with half the arithmetic each and leaves the registers for
+// reducing two entries at a time (SGAD_BWD_PAIRED).
 #ifndef SGAD_BWD_PX
-#define SGAD_BWD_PX 2
+#define SGAD_BWD_PX 1
 #endif
 constexpr int kBwdPx = SGAD_BWD_PX;
 static_assert(kBwdPx == 1 || kBwdPx == 2, "one or two backward pixels per lane");
@@ -377,6 +377,61 @@ __device__ __forceinline__ int scatter10_slot(int lane)
     return 5 * g + (q ? 3 + r : r);
 }
 
+// Backward entries per reduction: 1, or 2 (the default: two consecutive entries of a
+// warp's walk are evaluated, then their moments reduced together, so that the two
+// shuffle chains overlap).
+#ifndef SGAD_BWD_PAIRED
+#define SGAD_BWD_PAIRED 2
+#endif
+
+// warp_reduce_scatter10 of two value sets at once (their shuffles interleaved); each lane
+// ends with the totals of the same slot of both.
+__device__ __forceinline__ void warp_reduce_scatter10x2(float (&v)[10], float (&u)[10], int lane, float &tv,
+                                                        float &tu)
+{
+    {
+        const bool up = (lane & 16) != 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const float sv = up ? v[i] : v[i + 5], kv = up ? v[i + 5] : v[i];
+            const float su = up ? u[i] : u[i + 5], ku = up ? u[i + 5] : u[i];
+            v[i] = kv + __shfl_xor_sync(kFull, sv, 16);
+            u[i] = ku + __shfl_xor_sync(kFull, su, 16);
+        }
+    }
+    {
+        const bool up = (lane & 8) != 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float hv = i + 3 < 5 ? v[i + 3] : 0.f, hu = i + 3 < 5 ? u[i + 3] : 0.f;
+            const float sv = up ? v[i] : hv, kv = up ? hv : v[i];
+            const float su = up ? u[i] : hu, ku = up ? hu : u[i];
+            v[i] = kv + __shfl_xor_sync(kFull, sv, 8);
+            u[i] = ku + __shfl_xor_sync(kFull, su, 8);
+        }
+    }
+    {
+        const bool up = (lane & 4) != 0;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float hv = i + 2 < 3 ? v[i + 2] : 0.f, hu = i + 2 < 3 ? u[i + 2] : 0.f;
+            const float sv = up ? v[i] : hv, kv = up ? hv : v[i];
+            const float su = up ? u[i] : hu, ku = up ? hu : u[i];
+            v[i] = kv + __shfl_xor_sync(kFull, sv, 4);
+            u[i] = ku + __shfl_xor_sync(kFull, su, 4);
+        }
+    }
+    {
+        const bool up = (lane & 2) != 0;
+        const float sv = up ? v[0] : v[1], kv = up ? v[1] : v[0];
+        const float su = up ? u[0] : u[1], ku = up ? u[1] : u[0];
+        v[0] = kv + __shfl_xor_sync(kFull, sv, 2);
+        u[0] = ku + __shfl_xor_sync(kFull, su, 2);
+    }
+    tv = v[0] + __shfl_xor_sync(kFull, v[0], 1);
+    tu = u[0] + __shfl_xor_sync(kFull, u[0], 1);
+}
+
 // Chain rule of one staged Gaussian from its ten accumulated pair moments (colour (3),
 // depth, G, G dx, G dy, G dx^2, G dx dy, G dy^2 with G = dL/dpower) down to d mu, d s,
 // d opacity and d colour, added to its accumulator.
@@ -526,6 +581,43 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
         }
         __syncthreads();
         if (b0 < warp_nc) {
+            // the gradient terms of one entry at the lane's pixels in front of their
+            // contributor counts (list position lim), added to val
+            auto pair_terms = [&](const Staged &st, int lim, float (&val)[10]) {
+#pragma unroll
+                for (int p = 0; p < kBwdPx; ++p) {
+                    if (lim >= nc[p]) continue;
+                    float dx, dy, ep, alpha;
+                    if (!gauss_alpha(st, qx, qy[p], dx, dy, ep, alpha)) continue;
+                    const float om = __fsub_rn(1.0f, alpha);
+                    const float rom = __fdividef(1.0f, om);     // om >= 0.01: fast reciprocal
+                    const float Ti = T[p] * rom;
+                    const float w = alpha * Ti;
+                    val[0] += w * gr[p];
+                    val[1] += w * gg[p];
+                    val[2] += w * gb[p];
+                    val[3] += w * gD[p];
+                    const float dal = Ti * ((st.c.x - SCr[p]) * gr[p] + (st.c.y - SCg[p]) * gg[p] +
+                                            (st.c.z - SCb[p]) * gb[p] + (st.c.w - SD[p]) * gD[p] +
+                                            (1.0f - SA[p]) * gA[p]) -
+                                      (Tf[p] * rom) * bgdot[p];
+                    SCr[p] = alpha * st.c.x + om * SCr[p];
+                    SCg[p] = alpha * st.c.y + om * SCg[p];
+                    SCb[p] = alpha * st.c.z + om * SCb[p];
+                    SD[p] = alpha * st.c.w + om * SD[p];
+                    SA[p] = alpha + om * SA[p];
+                    if (!(st.b.w * ep > kAlphaCap)) {
+                        const float G = dal * alpha;
+                        val[4] += G;
+                        val[5] += G * dx;
+                        val[6] += G * dy;
+                        val[7] += G * dx * dx;
+                        val[8] += G * dx * dy;
+                        val[9] += G * dy * dy;
+                    }
+                    T[p] = Ti;
+                }
+            };
             // the tile list's chunks (32 entries from the list start) that meet this batch,
             // last first; each walks the entries that reach a pixel of the warp's block
             for (int c = (b1 - 1) >> 5; c >= (b0 >> 5); --c) {
@@ -534,50 +626,31 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
                 const int lo = b0 - 32 * c, hi = b1 - 32 * c;             // batch range in the chunk
                 if (lo > 0) mask &= ~0u << lo;
                 if (hi < 32) mask &= (1u << hi) - 1u;
+                // every marked entry reaches a pixel of the block, so every step reduces
                 while (mask) {
                     const int bit = 31 - __clz(mask);
                     mask &= ~(1u << bit);
                     const int jj = 32 * c + bit - b0;
-                    float val[10];
-#pragma unroll
-                    for (int q = 0; q < 10; ++q) val[q] = 0.f;
-                    bool contrib = false;
-                    const Staged st = sm[jj];
-#pragma unroll
-                    for (int p = 0; p < kBwdPx; ++p) {
-                        if (b0 + jj >= nc[p]) continue;
-                        float dx, dy, ep, alpha;
-                        if (!gauss_alpha(st, qx, qy[p], dx, dy, ep, alpha)) continue;
-                        contrib = true;
-                        const float om = __fsub_rn(1.0f, alpha);
-                        const float rom = __fdividef(1.0f, om);     // om >= 0.01: fast reciprocal
-                        const float Ti = T[p] * rom;
-                        const float w = alpha * Ti;
-                        val[0] += w * gr[p];
-                        val[1] += w * gg[p];
-                        val[2] += w * gb[p];
-                        val[3] += w * gD[p];
-                        const float dal = Ti * ((st.c.x - SCr[p]) * gr[p] + (st.c.y - SCg[p]) * gg[p] +
-                                                (st.c.z - SCb[p]) * gb[p] + (st.c.w - SD[p]) * gD[p] +
-                                                (1.0f - SA[p]) * gA[p]) -
-                                          (Tf[p] * rom) * bgdot[p];
-                        SCr[p] = alpha * st.c.x + om * SCr[p];
-                        SCg[p] = alpha * st.c.y + om * SCg[p];
-                        SCb[p] = alpha * st.c.z + om * SCb[p];
-                        SD[p] = alpha * st.c.w + om * SD[p];
-                        SA[p] = alpha + om * SA[p];
-                        if (!(st.b.w * ep > kAlphaCap)) {
-                            const float G = dal * alpha;
-                            val[4] += G;
-                            val[5] += G * dx;
-                            val[6] += G * dy;
-                            val[7] += G * dx * dx;
-                            val[8] += G * dx * dy;
-                            val[9] += G * dy * dy;
-                        }
-                        T[p] = Ti;
+                    int jj2 = -1;
+                    if (SGAD_BWD_PAIRED == 2 && mask) {
+                        const int bit2 = 31 - __clz(mask);
+                        mask &= ~(1u << bit2);
+                        jj2 = 32 * c + bit2 - b0;
                     }
-                    if (__any_sync(kFull, contrib)) {
+                    float val[10], val2[10];
+#pragma unroll
+                    for (int q = 0; q < 10; ++q) val[q] = val2[q] = 0.f;
+                    pair_terms(sm[jj], b0 + jj, val);
+                    if (jj2 >= 0) {
+                        pair_terms(sm[jj2], b0 + jj2, val2);
+                        float t1, t2;
+                        warp_reduce_scatter10x2(val, val2, lane, t1, t2);
+                        const int slot = scatter10_slot(lane);
+                        if ((lane & 1) == 0 && slot >= 0) {
+                            atomicAdd(&acc[jj][slot], t1);
+                            atomicAdd(&acc[jj2][slot], t2);
+                        }
+                    } else {
                         const float total = warp_reduce_scatter10(val, lane);
                         const int slot = scatter10_slot(lane);
                         if ((lane & 1) == 0 && slot >= 0) atomicAdd(&acc[jj][slot], total);
