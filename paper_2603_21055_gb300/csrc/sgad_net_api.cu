@@ -50,7 +50,7 @@ NetLayout layout(size_t px)
 
 struct Ws {
     NetLayout L;
-    char *base;
+    char *base = nullptr;
     uint32_t *status() const { return reinterpret_cast<uint32_t *>(base); }
     uint4 *at(size_t off) const { return reinterpret_cast<uint4 *>(base + off); }
 };
