@@ -154,7 +154,11 @@ typedef struct {
     int32_t fwd_schedule;        /* SGAD_SCHEDULE_* of forward compositing (default TILES) */
     int32_t bwd_schedule;        /* SGAD_SCHEDULE_* of backward compositing (default TILES) */
     int32_t bwd_algorithm;       /* SGAD_BWD_* (default WARP_REDUCE) */
-    int32_t reserved[3];         /* must be zero */
+    int32_t max_blocks;          /* persistent schedules: launch at most this many blocks
+                                    (0 = as many as are resident on the GPU, the default);
+                                    a small cap makes every block take many tiles, for
+                                    tests of the queue on small problems */
+    int32_t reserved[2];         /* must be zero */
 } sgad_options;
 
 typedef struct sgad_ctx sgad_ctx;
@@ -397,9 +401,10 @@ sgad_status sgad_adam_step_multi(int32_t n_tensors, const sgad_adam_tensor *tens
  * pixel, 49 B per key and ~1.1 KB per tile)
  * are rejected with SGAD_ERR_WORKSPACE_TOO_SMALL before anything is launched; a forward
  * whose keys exceed the room left returns SGAD_ERR_KEY_OVERFLOW. The call synchronises
- * `stream` to report that status. The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and should come before any stream capture on that
- * device. All calls share the one array and it keeps the last call's contents: calls
+ * `stream` to report that status. Every call looks up the array's device address in the
+ * current device's context (cudaGetSymbolAddress, a host-side lookup); the first call on
+ * a device also loads the library's device code there and should come before any stream
+ * capture on that device. All calls share the one array and it keeps the last call's contents: calls
  * that may run concurrently on the GPU (different streams or threads) race and must be
  * serialised by the caller. No backward pass is offered this way (its state would live
  * in the shared array). */

@@ -97,7 +97,8 @@ class sgad_options(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("bg", C.c_float * 3),
                 ("sort_smem_cap", C.c_int32), ("freeze_offset", C.c_int32), ("fwd_batch", C.c_int32),
                 ("bwd_batch", C.c_int32), ("fwd_schedule", C.c_int32), ("bwd_schedule", C.c_int32),
-                ("bwd_algorithm", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("bwd_algorithm", C.c_int32), ("max_blocks", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 SGAD_BWD_WARP_REDUCE = 0

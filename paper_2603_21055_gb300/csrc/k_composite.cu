@@ -34,8 +34,9 @@ bool valid_batch(int batch, bool fwd)
     return false;
 }
 
-// Blocks of the persistent grid: resident blocks per SM times SMs, at most one per tile.
-cudaError_t persistent_blocks(bool fwd, int batch, const Scene &sc, int *blocks)
+// Blocks of the persistent grid: resident blocks per SM times SMs, at most one per tile
+// and at most max_blocks when that is positive.
+cudaError_t persistent_blocks(bool fwd, int batch, const Scene &sc, int max_blocks, int *blocks)
 {
     int occ = 0, dev = 0, sms = 0;
     cudaError_t e = dispatch(fwd, batch, sc, CompositeArgs{}, 0, &occ, nullptr);
@@ -44,11 +45,12 @@ cudaError_t persistent_blocks(bool fwd, int batch, const Scene &sc, int *blocks)
     if (e != cudaSuccess) return e;
     long long n = (long long)(occ > 0 ? occ : 1) * sms;
     if (n > sc.n_tiles) n = sc.n_tiles;
+    if (max_blocks > 0 && n > max_blocks) n = max_blocks;
     *blocks = (int)n;
     return cudaSuccess;
 }
 
-cudaError_t launch_composite(bool fwd, int batch, int schedule, const Scene &sc, const World *world,
+cudaError_t launch_composite(bool fwd, int batch, int schedule, int max_blocks, const Scene &sc, const World *world,
                              const uint32_t *off, const uint64_t *entries, float *pix_t, uint32_t *pix_n, float4 *gacc,
                              WsHeader *hdr, const uint32_t *order, uint32_t *contrib, uint32_t *wmask,
                              cudaStream_t st)
@@ -68,7 +70,7 @@ cudaError_t launch_composite(bool fwd, int batch, int schedule, const Scene &sc,
     a.hdr = hdr;
     if (schedule == SGAD_SCHEDULE_PERSISTENT) {
         int blocks = 0;
-        cudaError_t e = persistent_blocks(fwd, batch, sc, &blocks);
+        cudaError_t e = persistent_blocks(fwd, batch, sc, max_blocks, &blocks);
         if (e != cudaSuccess) return e;
         a.order = order;
         a.queue = fwd ? &hdr->queue_fwd : &hdr->queue_bwd;

@@ -13,8 +13,9 @@ void launch_project_count(const Scene &, World *, uint32_t *, cudaStream_t);
 void launch_scan_tiles(uint32_t *, uint32_t *, int, uint64_t, WsHeader *, uint32_t *, cudaStream_t);
 void launch_emit(const Scene &, const World *, const uint32_t *, uint32_t *, uint64_t *, WsHeader *, cudaStream_t);
 cudaError_t launch_sort_tiles(const uint32_t *, uint64_t *, uint64_t *, int, int, const WsHeader *, cudaStream_t);
-cudaError_t launch_composite(bool, int, int, const Scene &, const World *, const uint32_t *, const uint64_t *, float *,
-                             uint32_t *, float4 *, WsHeader *, const uint32_t *, uint32_t *, uint32_t *, cudaStream_t);
+cudaError_t launch_composite(bool, int, int, int, const Scene &, const World *, const uint32_t *, const uint64_t *,
+                             float *, uint32_t *, float4 *, WsHeader *, const uint32_t *, uint32_t *, uint32_t *,
+                             cudaStream_t);
 bool valid_batch(int, bool);
 void launch_finalize(const Scene &, const World *, const float4 *, cudaStream_t);
 void launch_l1_batch(int, const float *const *, const float *const *, const float *const *, const float *const *,
@@ -243,7 +244,7 @@ sgad_status run_composite(const sgad_ctx *ctx, bool fwd, int batch, int schedule
                           cudaStream_t st)
 {
     uint32_t *contrib = (!fwd || ctx->opt.bwd_algorithm == SGAD_BWD_PAIRS) ? ws.contrib() : nullptr;
-    const cudaError_t e = launch_composite(fwd, batch, schedule, sc, ws.world(), ws.tile_off(), ws.keys(), ws.pix_t(),
+    const cudaError_t e = launch_composite(fwd, batch, schedule, ctx->opt.max_blocks, sc, ws.world(), ws.tile_off(), ws.keys(), ws.pix_t(),
                                            ws.pix_n(), fwd ? nullptr : ws.gacc(), ws.hdr(), ws.tile_order(), contrib,
                                            ws.wmask(), st);
     return e == cudaSuccess ? SGAD_OK : cuda_fail(e, fwd ? "forward compositing launch" : "backward compositing launch");
@@ -377,8 +378,9 @@ sgad_status sgad_create(sgad_ctx **out, const sgad_options *opt)
     const bool shape_ok = (o.tile_w == 16 && o.tile_h == 16) || (o.tile_w == 8 && o.tile_h == 32) ||
                           (o.tile_w == 32 && o.tile_h == 8);
     if (!shape_ok) return fail(SGAD_ERR_UNSUPPORTED, "tile shape %dx%d not supported", o.tile_w, o.tile_h);
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
         if (o.reserved[i] != 0) return fail(SGAD_ERR_INVALID_ARG, "reserved options must be zero");
+    if (o.max_blocks < 0) return fail(SGAD_ERR_INVALID_ARG, "max_blocks must be >= 0");
     if (o.bwd_algorithm != SGAD_BWD_PAIRS && o.bwd_algorithm != SGAD_BWD_WARP_REDUCE)
         return fail(SGAD_ERR_INVALID_ARG, "unknown backward algorithm %d", o.bwd_algorithm);
     for (int c = 0; c < 3; ++c)

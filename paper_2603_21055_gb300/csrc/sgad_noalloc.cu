@@ -21,27 +21,24 @@ sgad_status report_error(sgad_status code, const char *msg);
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the array on the current device, looked up once per device.
+// Device address of the array in the current device's context. Looked up on every call
+// (a host-side lookup, no device work): a pointer cached across calls could outlive the
+// context it came from (after cudaDeviceReset the module is loaded again, possibly at
+// another address).
 cudaError_t scratch_address(void **out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_sgad_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_sgad_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
+
+// Bytes of workspace each key adds (make_layout: 8 B in each of the two key arrays, 32 B
+// of pair-parallel contribution words and 1 B of per-warp masks), and the most the
+// 256-byte alignment of those four sections can add on top.
+constexpr size_t kBytesPerKey = 8 + 8 + 32 + 1;
+constexpr size_t kKeySectionSlack = 4 * 256;
 
 }  // namespace
 
@@ -49,22 +46,31 @@ extern "C" sgad_status sgad_forward_noalloc(sgad_ctx *ctx, const sgad_keyframe *
                                             const sgad_camera *views, int32_t n_views, sgad_images *out,
                                             void *stream)
 {
-    // Size of the problem with no keys, then the most keys the rest of the array holds
-    // (each key takes 8 bytes in each of the two key arrays).
+    // Size of the problem with no keys, then the most keys the rest of the array holds,
+    // in closed form from the per-key bytes of the layout (checked once, and trimmed by
+    // a bounded bisection should the layout ever need more).
+    const size_t kScratch = SGAD_NOALLOC_SCRATCH_BYTES;
     size_t base = 0;
     sgad_status s = sgad_workspace_size(ctx, kfs, n_kf, views, n_views, 0, &base);
     if (s) return s;
-    if (base + 4096 * 16 > (size_t)SGAD_NOALLOC_SCRATCH_BYTES)
+    const int64_t kMinKeys = 4096;
+    if (base + kKeySectionSlack + (size_t)kMinKeys * kBytesPerKey > kScratch)
         return sgad::report_error(SGAD_ERR_WORKSPACE_TOO_SMALL,
                                   "sgad_forward_noalloc: problem too large for the static scratch "
                                   "(SGAD_NOALLOC_SCRATCH_BYTES); use sgad_forward with a workspace");
-    int64_t cap = (int64_t)(((size_t)SGAD_NOALLOC_SCRATCH_BYTES - base) / 16);
+    int64_t cap = (int64_t)((kScratch - base - kKeySectionSlack) / kBytesPerKey);
     size_t need = 0;
-    while (cap > 0) {          // the per-section 256-byte rounding can cost a few keys
-        s = sgad_workspace_size(ctx, kfs, n_kf, views, n_views, cap, &need);
-        if (s) return s;
-        if (need <= (size_t)SGAD_NOALLOC_SCRATCH_BYTES) break;
-        cap -= 64;
+    s = sgad_workspace_size(ctx, kfs, n_kf, views, n_views, cap, &need);
+    if (s) return s;
+    if (need > kScratch) {     // [lo fits, hi does not]
+        int64_t lo = kMinKeys, hi = cap;
+        for (int it = 0; it < 40 && hi - lo > 1; ++it) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            s = sgad_workspace_size(ctx, kfs, n_kf, views, n_views, mid, &need);
+            if (s) return s;
+            (need <= kScratch ? lo : hi) = mid;
+        }
+        cap = lo;
     }
     void *scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import compare_grads, compare_images, compare_keys, gpu_run, l1_grads
+from parity import compare_grads, compare_images, compare_keys, gpu_run, grad_stats_line, l1_grads
 
 pytestmark = pytest.mark.gpu
 
@@ -67,12 +67,17 @@ def test_every_split_matches_default(uneven, uneven_grads, tile):
 
 
 @pytest.mark.parametrize("tile", SHAPES)
-def test_persistent_split_against_oracle(uneven, uneven_grads, tile):
+@pytest.mark.parametrize("batches,max_blocks", [((192, 384), 0), ((512, 512), 6)])
+def test_persistent_split_against_oracle(uneven, uneven_grads, tile, batches, max_blocks):
+    """The persistent schedule against the oracle. With max_blocks = 6 (the batches the
+    room benchmark's autotuner picks) every block takes ~60 tiles from the queue, so the
+    per-block loop over tiles (state reset, next tile read, per-tile masks) is what runs;
+    with the resident grid most blocks take one tile."""
     o = oracle.opts(tile_w=tile[0], tile_h=tile[1])
     ref = oracle.render(uneven, o)
     _, g = l1_grads(uneven, ref)
-    res = gpu_run(uneven, grads_in=g, tile=tile, fwd_batch=192, bwd_batch=384, fwd_schedule="persistent",
-                  bwd_schedule="persistent")
+    res = gpu_run(uneven, grads_in=g, tile=tile, fwd_batch=batches[0], bwd_batch=batches[1],
+                  fwd_schedule="persistent", bwd_schedule="persistent", max_blocks=max_blocks)
     compare_keys(res, uneven, o)
     worst, n_near = compare_images(res, ref)
     og = oracle.backward(uneven, [{k: v.astype(np.float64) for k, v in x.items()} for x in g], o)
@@ -80,7 +85,9 @@ def test_persistent_split_against_oracle(uneven, uneven_grads, tile):
     # so the ~100 pixels with a near decision flag ~15% of the Gaussians (every Gaussian a
     # flagged walk reaches); those are still held to the near-decision bound.
     e = compare_grads(res, og, max_near_frac=0.2)
-    print("uneven %dx%d persistent: img %.2e near px %d grad ratio %.3f" % (tile + (worst, n_near, e)))
+    print("uneven %dx%d persistent %s cap %d: img %.2e near px %d grad ratio %.3f" %
+          (tile + (batches, max_blocks, worst, n_near, e)))
+    print(grad_stats_line("uneven %dx%d" % tile))
     assert e <= 1.0
 
 

@@ -6,7 +6,11 @@ plus the FP32 accumulation error, bounded by 1e-5 times the sum of the magnitude
 the summed products (A below); FP32 outputs and parameter gradients (long sums over
 pixels, accumulated with atomics) by 1e-4 A. Sizes: two frames of 5 x 150 pixels, so
 each image row spans a full 128-pixel tile and a ragged 22-pixel one, and the weight
-gradient's 64-pixel blocks end ragged too.
+gradient's 64-pixel blocks end ragged too; and two frames of 240 x 630 pixels (2,400
+row tiles of 128 pixels, the last of each row ragged; 4,800 weight-gradient blocks of 64
+pixels), several times the persistent grids, so that every block of the convolutions
+walks its two-stage TMA ring and flips its double TMEM accumulator many times and every
+weight-gradient block prefetches its next K block.
 """
 import numpy as np
 import pytest
@@ -15,16 +19,17 @@ from oracle import net as onet
 
 pytestmark = pytest.mark.gpu
 
-N, H, W = 2, 5, 150
+SIZES = {"5x150": (2, 5, 150), "240x630": (2, 240, 630)}
 
 
 def _bf(t):
     return t.float().cpu().numpy().astype(np.float64)
 
 
-@pytest.fixture(scope="module")
-def run():
+@pytest.fixture(scope="module", params=sorted(SIZES))
+def run(request):
     import torch
+    N, H, W = SIZES[request.param]
     from paper_2603_21055_gb300.proposal import ProposalNet
     rng = np.random.default_rng(11)
     params = [(w, rng.normal(0, 0.05, size=b.shape).astype(np.float32)) for w, b in onet.init_params(3)]

@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import (compare_grads, compare_images, compare_keys, compare_pose, gpu_run, l1_grads)
+from parity import (compare_grads, compare_images, compare_keys, compare_pose, gpu_run, grad_stats_line,
+                    l1_grads)
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +45,7 @@ def test_config1_backward(scene1):
     og = oracle.backward(scene1, [{k: v.astype(np.float64) for k, v in x.items()} for x in g])
     e = compare_grads(res, og)
     print("config1 grad error ratio %.3f" % e)
+    print(grad_stats_line("config1"))
     assert e <= 1.0
 
 
@@ -55,6 +57,7 @@ def test_crop_forward_backward(crop):
     og = oracle.backward(crop, [{k: v.astype(np.float64) for k, v in x.items()} for x in g])
     e = compare_grads(res, og)
     print("crop: keys %d aside %d img %.2e near px %d grad ratio %.3f" % (res["n_keys"], n_aside, worst, n_near, e))
+    print(grad_stats_line("crop"))
     assert e <= 1.0
 
 
@@ -232,6 +235,7 @@ def test_most_keyframes_and_views(scene1):
     og = oracle.backward(sc, [{k: v.astype(np.float64) for k, v in x.items()} for x in g])
     e = compare_grads(res, og)
     print("32 kf x 64 views: keys %d aside %d img %.2e grad ratio %.3f" % (res["n_keys"], n_aside, worst, e))
+    print(grad_stats_line("32kf x 64 views"))
     assert res["n_keys"] > 0 and e <= 1.0
 
 
