@@ -285,10 +285,10 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     ssim = ssim_term(mp.sp, mp.views, mp.images, mp.trgb, flush, peaks, peak_src)
     from paper_2603_21055_gb300 import binding as B
-    pairs = mp.sp.options.bwd_algorithm == B.SGAD_BWD_PAIRS
+    bwd_kernel = {B.SGAD_BWD_PAIRS: "k_composite_bwdp", B.SGAD_BWD_WARP_LOCAL: "k_composite_bwdl"}.get(
+        mp.sp.options.bwd_algorithm, "k_composite_bwd")
     fp32 = measured_fp32_tflops()
-    roof = roofline(stages, stats, scene, peaks, peak_src,
-                    bwd_kernel="k_composite_bwdp" if pairs else "k_composite_bwd", fp32=fp32)
+    roof = roofline(stages, stats, scene, peaks, peak_src, bwd_kernel=bwd_kernel, fp32=fp32)
     path = path_roofline(stages, stats, scene, peaks, fp32)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -327,7 +327,8 @@ def split_of(sp):
     """The work split a Splatter uses (after autotuning), for the JSON line."""
     from paper_2603_21055_gb300 import binding as B
     o = sp.options
-    bwd = ("pairs" if o.bwd_algorithm == B.SGAD_BWD_PAIRS else "warp_reduce batch %d" % o.bwd_batch)
+    bwd = {B.SGAD_BWD_PAIRS: "pairs", B.SGAD_BWD_WARP_LOCAL: "warp_local"}.get(
+        o.bwd_algorithm, "warp_reduce batch %d" % o.bwd_batch)
     return {"tile": "%dx%d" % (o.tile_w, o.tile_h), "fwd_batch": o.fwd_batch,
             "fwd_schedule": B.SCHEDULE_NAMES[o.fwd_schedule], "bwd": bwd,
             "bwd_schedule": B.SCHEDULE_NAMES[o.bwd_schedule], "chosen_by": "sgad_autotune"}

@@ -126,17 +126,23 @@ typedef struct {
                                        list length, longest first */
 #define SGAD_SCHEDULE_PER_VIEW 2    /* one launch per view (one block per tile) */
 
-/* Backward compositing algorithm (default WARP_REDUCE). Both give the same gradients up
+/* Backward compositing algorithm (default WARP_LOCAL). All give the same gradients up
  * to the order of floating-point additions.
+ *   WARP_LOCAL: every warp independently takes (tile, 8x4 pixel block) units from a queue
+ *     (heaviest tile first under the persistent schedule) and walks only the entries the
+ *     forward's per-warp masks mark for its block, 32 per round with no block-wide
+ *     barrier; per (entry, pixel) pair it keeps two numbers in shared memory, and one lane
+ *     per entry sums them (bwd_batch does not apply).
+ *   WARP_REDUCE: thread blocks walk the masked entries of a tile in batches of bwd_batch
+ *     staged entries per block-wide barrier, evaluate each at all 32 pixels of a warp's
+ *     block and reduce the per-pair moments over the warp.
  *   PAIRS: the forward records, per pixel and list chunk, which entries contributed
  *     (4 bytes per pixel per 32 entries walked); the backward walks only those pairs, one
  *     pixel per thread, and sums the per-pair moments per Gaussian with shared-memory
- *     atomics.
- *   WARP_REDUCE: the backward re-tests every (pixel, entry) pair whose alpha box reaches a
- *     warp's pixel block and reduces the per-pair moments over the warp (bwd_batch
- *     entries per barrier). */
+ *     atomics. */
 #define SGAD_BWD_WARP_REDUCE 0
 #define SGAD_BWD_PAIRS 1
+#define SGAD_BWD_WARP_LOCAL 2
 
 /* Options fixed at sgad_create() (sgad_autotune() may change tile shape, batches,
  * schedules and the backward algorithm). */
@@ -153,7 +159,7 @@ typedef struct {
     int32_t bwd_batch;           /* the same for the warp-reduced backward; 0 = default (256) */
     int32_t fwd_schedule;        /* SGAD_SCHEDULE_* of forward compositing (default TILES) */
     int32_t bwd_schedule;        /* SGAD_SCHEDULE_* of backward compositing (default TILES) */
-    int32_t bwd_algorithm;       /* SGAD_BWD_* (default WARP_REDUCE) */
+    int32_t bwd_algorithm;       /* SGAD_BWD_* (default WARP_LOCAL) */
     int32_t max_blocks;          /* persistent schedules: launch at most this many blocks
                                     (0 = as many as are resident on the GPU, the default);
                                     a small cap makes every block take many tiles, for
@@ -179,8 +185,8 @@ const char *sgad_last_error(void);
  * counters and heavy-first order (12 B per tile), the per-pixel state kept for the
  * backward pass (8 B per view pixel), two key arrays (16 B per key), the per-pixel
  * contribution words of the pair-parallel backward (32 B per key + 1 KB per tile) and
- * the per-warp contribution masks the forward leaves for the warp-reduced backward
- * (1 B per key + 64 B per tile). */
+ * the per-warp contribution masks the forward leaves for the warp-local and
+ * warp-reduced backwards (1 B per key + 64 B per tile). */
 sgad_status sgad_workspace_size(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                                 const sgad_camera *views, int32_t n_views, int64_t key_capacity,
                                 size_t *bytes);
@@ -220,8 +226,9 @@ sgad_status sgad_backward(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
  * Sweeps the tile shapes {16x16, 8x32, 32x8}, the batch sizes {128, 192, 256, 384, 512}
  * (forward also 768 and 1024)
  * and the schedules {TILES, PERSISTENT} of both compositing passes (and, for the
- * backward, the pair-parallel algorithm, reported with batch 0 and charged with the cost
- * of the contribution words its forward writes), timing each candidate
+ * backward, the warp-local algorithm, reported with batch -1, and the pair-parallel
+ * algorithm, reported with batch 0 and charged with the cost of the contribution words
+ * its forward writes), timing each candidate
  * with CUDA events on `stream` (median of `reps` runs after one warm-up), and stores the
  * fastest combination in ctx's options: per tile shape, binning + emission + sort is
  * timed once, then each (batch, schedule) of forward compositing, then of backward

@@ -103,6 +103,7 @@ class sgad_options(C.Structure):
 
 SGAD_BWD_WARP_REDUCE = 0
 SGAD_BWD_PAIRS = 1
+SGAD_BWD_WARP_LOCAL = 2
 
 
 SGAD_TUNE_PREP = 0

@@ -68,6 +68,31 @@ cudaError_t launch_composite(bool fwd, int batch, int schedule, int max_blocks, 
     a.pix_n = pix_n;
     a.gacc = gacc;
     a.hdr = hdr;
+    if (!fwd && batch < 0) {
+        // warp-local backward: resident warps take (tile, block) units from a queue, in
+        // the heavy-first tile order (persistent), in tile order, or view by view
+        int blocks = 0;
+        cudaError_t e = persistent_blocks(false, batch, sc, max_blocks, &blocks);
+        if (e != cudaSuccess) return e;
+        a.queue = &hdr->queue_bwd;
+        auto run = [&](int tile0, int n_tiles, const uint32_t *ord) {
+            a.tile0 = tile0;
+            a.n_launch_tiles = n_tiles;
+            a.order = ord;
+            cudaError_t r = cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), st);
+            if (r != cudaSuccess) return r;
+            return dispatch(false, batch, sc, a, blocks < n_tiles ? blocks : n_tiles, nullptr, st);
+        };
+        if (schedule == SGAD_SCHEDULE_PER_VIEW) {
+            for (int i = 0; i < sc.n_views; ++i) {
+                const ViewDev &v = sc.view[i];
+                e = run(v.tile_base, v.tiles_x * v.tiles_y, nullptr);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        }
+        return run(0, sc.n_tiles, schedule == SGAD_SCHEDULE_PERSISTENT ? order : nullptr);
+    }
     if (schedule == SGAD_SCHEDULE_PERSISTENT) {
         int blocks = 0;
         cudaError_t e = persistent_blocks(fwd, batch, sc, max_blocks, &blocks);

@@ -38,6 +38,14 @@
 // Gaussian atomic conflicts between neighbouring pixels), so the warp-reduced one above
 // is the default.
 //
+// A third backward, the warp-local one (k_composite_bwdl, the default), has no block-wide
+// barrier at all: every warp takes (tile, 8x4 pixel block) units from a queue and walks
+// only the entries its forward mask marks, 32 at a time. Each lane keeps its pixel's
+// reverse-walk state; per (entry, contributing pixel) it leaves two numbers in the warp's
+// shared memory (dL/dpower and the blend weight), and then one lane per entry sums its
+// pixels' moments and applies the chain rule. No (entry, lane) slot of a warp-wide
+// reduction is spent on a pixel the entry does not reach.
+//
 // Work split (CompositeArgs): either one block per tile (blockIdx.x + tile0), or a
 // persistent grid of resident blocks that take tiles from an atomic queue in the
 // heavy-first order written by the tile scan.
@@ -79,6 +87,8 @@ struct CompositeArgs {
     const uint32_t *order;        // persistent: heavy-first tile order; nullptr: one block per tile
     uint32_t *queue;              // persistent: next position in `order` (starts at 0)
     int32_t tile0;                // one block per tile: tile of block 0
+    int32_t n_launch_tiles;       // warp-local backward: tiles this launch covers (from
+                                  // tile0, or through `order` when it is set)
     // Contribution words (forward writes, pair-parallel backward reads; may be null):
     // for tile t, list chunk c (entries 32c .. 32c + 31) and forward thread i (its
     // pixel), word contrib[8 off[t] + 256 t + 256 c + i] has bit j set iff entry 32c + j
@@ -864,6 +874,241 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_composite_bwdp(const __grid
     }
 }
 
+// ------------------------------------------------------------------ warp-local backward
+//
+// Work unit: one 8x4 pixel block of one tile, lane = pixel (the block of forward warp wb,
+// whose contribution masks mark the entries that reached one of these pixels). Units are
+// taken from an atomic queue by single warps, heaviest tile first when the tile order is
+// given, so warps never wait for one another. A unit walks its marked entries from the
+// largest contributor count down in rounds of up to 32:
+//   1. gather: the next (lower) marked positions, highest first, one per lane;
+//   2. stage: each lane projects its entry into the warp's shared memory;
+//   3. walk: for each staged entry in order, every lane whose pixel it reaches recovers
+//      the transmittance by division, forms dL/dalpha from the suffix sums and stores
+//      (G = alpha dL/dalpha, zero at the alpha cap; w = alpha T) into a per-warp pair
+//      buffer, compacted by a ballot;
+//   4. reduce: lane j sums the ten moments of entry j over the pixels it reached (colour
+//      and depth: w times the pixel's image gradients; G, G dx, G dy, G dx^2, G dx dy,
+//      G dy^2), applies the chain rule and adds the result with two vector atomics.
+// The pair buffer holds kLocalPairCap pairs; a round that would overflow it reduces the
+// entries walked so far first. The per-pair arithmetic is the warp-reduced backward's.
+constexpr int kLocalThreads = 256;          // 8 independent warps per block
+constexpr int kLocalPairCap = 480;          // (G, w) pairs buffered per warp
+#ifndef SGAD_BWDL_MINBLOCKS
+#define SGAD_BWDL_MINBLOCKS 4
+#endif
+
+struct LocalWarpSmem {
+    Staged st[32];                  // the round's entries
+    float4 pg[32];                  // image gradients (r, g, b, depth) of the unit's pixels
+    float2 pairs[kLocalPairCap];    // (G, w) per contributing (entry, pixel) pair
+};
+constexpr size_t kLocalSmemBytes = (kLocalThreads / 32) * sizeof(LocalWarpSmem);
+
+__device__ __forceinline__ uint32_t lane_mask_lt(int lane) { return (1u << lane) - 1u; }
+
+// Moments of the round's entries [j0, j1) (lane j holds entry j: its contributing-pixel
+// mask cm, first pair index base, Gaussian g and world record w0), the chain rule, and the
+// pose terms accumulated per lane. Whole warp.
+template <bool POSE>
+__device__ __forceinline__ void bwdl_reduce(const ViewDev &v, const CompositeArgs &a, const LocalWarpSmem &S, int j0,
+                                            int j1, int lane, uint32_t cm, int base, uint32_t g, float4 w0, int bx,
+                                            int by, float (&pose)[12])
+{
+    if (lane < j0 || lane >= j1 || cm == 0u) return;
+    const Staged st = S.st[lane];
+    float A[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) A[q] = 0.f;
+    int k = base;
+    uint32_t m = cm;
+    while (m) {
+        const int p = __ffs(m) - 1;
+        m &= m - 1u;
+        const float2 gw = S.pairs[k++];
+        const float4 pg = S.pg[p];
+        const float dx = __fsub_rn(st.a.x, (float)(bx + (p & 7)));
+        const float dy = __fsub_rn(st.a.y, (float)(by + (p >> 3)));
+        A[0] += gw.y * pg.x;
+        A[1] += gw.y * pg.y;
+        A[2] += gw.y * pg.z;
+        A[3] += gw.y * pg.w;
+        const float G = gw.x;
+        A[4] += G;
+        A[5] += G * dx;
+        A[6] += G * dy;
+        A[7] += G * dx * dx;
+        A[8] += G * dx * dy;
+        A[9] += G * dy * dy;
+    }
+    const float3 gt = chain_and_accumulate(A, st, project(w0, v), w0.w, v, a.gacc, g);
+    if (POSE) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            const float gq = (q >> 2) == 0 ? gt.x : ((q >> 2) == 1 ? gt.y : gt.z);
+            const int c = q & 3;
+            pose[q] += c == 3 ? gq : gq * (c == 0 ? w0.x : (c == 1 ? w0.y : w0.z));
+        }
+    }
+}
+
+template <int TW, int TH, bool POSE>
+__device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &a, int tile, int wb, LocalWarpSmem &S,
+                                          int lane)
+{
+    const ViewDev &v = sc.view[find_view_of_tile(sc, tile)];
+    const int local = tile - v.tile_base;
+    const int tx = local % v.tiles_x, ty = local / v.tiles_x;
+    const int bx = tx * TW + (wb % (TW / 8)) * 8, by = ty * TH + (wb / (TW / 8)) * 4;
+    const int px = bx + (lane & 7), py = by + (lane >> 3);
+    const float qx = (float)px, qy = (float)py;
+    const uint32_t s = a.off[tile];
+    const int len = (int)(a.off[tile + 1] - s);
+    const size_t hw = (size_t)v.W * v.H;
+
+    float Tf = 1.0f, gr = 0.f, gg = 0.f, gb = 0.f, gD = 0.f, gA = 0.f;
+    int nc = 0;
+    if (px < v.W && py < v.H) {
+        const size_t q = (size_t)py * v.W + px;
+        Tf = a.pix_t[v.pix_base + q];
+        nc = min((int)a.pix_n[v.pix_base + q], len);
+        if (v.g_rgb) {
+            gr = v.g_rgb[q];
+            gg = v.g_rgb[hw + q];
+            gb = v.g_rgb[2 * hw + q];
+        }
+        if (v.g_depth) gD = v.g_depth[q];
+        if (v.g_alpha) gA = v.g_alpha[q];
+    }
+    const int fnc = (int)__reduce_max_sync(kFull, (unsigned)nc);
+    if (fnc == 0) return;
+    __syncwarp();                       // the previous unit's readers of S are done
+    S.pg[lane] = make_float4(gr, gg, gb, gD);
+    const float bgdot = sc.bg[0] * gr + sc.bg[1] * gg + sc.bg[2] * gb;
+    float T = Tf, SCr = 0.f, SCg = 0.f, SCb = 0.f, SD = 0.f, SA = 0.f;
+    float pose[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) pose[q] = 0.f;
+
+    // chunk c of the tile list (entries 32c .. 32c + 31) has this block's mask at wm[8 c];
+    // a window of 32 chunks is held one per lane, lane L the chunk cw - L
+    const uint32_t *wm = a.wmask + wmask_base(tile, s) + wb;
+    int cw = (fnc - 1) >> 5;
+    uint32_t wl = cw - lane >= 0 ? wm[8 * (cw - lane)] : 0u;
+    int ci = -1;                        // window slot being consumed (-1: none yet)
+    uint32_t rem = 0u;                  // its bits not yet taken
+    for (;;) {
+        // 1. gather up to 32 marked positions, highest first
+        int n = 0, my_pos = 0;
+        while (n < 32) {
+            if (rem == 0u) {
+                const uint32_t after = ci >= 31 ? 0u : (~0u << (ci + 1));
+                const uint32_t nz = __ballot_sync(kFull, wl != 0u) & after;
+                if (nz) {
+                    ci = __ffs(nz) - 1;
+                    rem = __shfl_sync(kFull, wl, ci);
+                } else {
+                    cw -= 32;
+                    if (cw < 0) break;
+                    wl = cw - lane >= 0 ? wm[8 * (cw - lane)] : 0u;
+                    ci = -1;
+                    continue;
+                }
+            }
+            const int bit = 31 - __clz(rem);
+            rem &= ~(1u << bit);
+            if (lane == n) my_pos = 32 * (cw - ci) + bit;
+            ++n;
+        }
+        if (n == 0) break;
+        // 2. stage (lane j: entry j)
+        uint32_t my_g = 0u;
+        float4 my_w0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane < n) {
+            const uint64_t ent = a.entries[s + my_pos];
+            my_g = (uint32_t)ent;
+            const World w = a.world[my_g];
+            my_w0 = w.w0;
+            stage(project(w.w0, v), w.w1, __uint_as_float((uint32_t)(ent >> 32)), S.st[lane]);
+        }
+        __syncwarp();
+        // 3. walk, 4. reduce
+        uint32_t my_cm = 0u;
+        int my_base = 0, np = 0, j0 = 0;
+        for (int j = 0; j < n; ++j) {
+            if (np > kLocalPairCap - 32) {
+                __syncwarp();
+                bwdl_reduce<POSE>(v, a, S, j0, j, lane, my_cm, my_base, my_g, my_w0, bx, by, pose);
+                __syncwarp();
+                np = 0;
+                j0 = j;
+            }
+            const int lim = __shfl_sync(kFull, my_pos, j);
+            const Staged st = S.st[j];
+            bool hit = false;
+            float G = 0.f, wv = 0.f;
+            float dx, dy, ep, alpha;
+            if (lim < nc && gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) {
+                hit = true;
+                const float om = __fsub_rn(1.0f, alpha);
+                const float rom = __fdividef(1.0f, om);     // om >= 0.01: fast reciprocal
+                const float Ti = T * rom;
+                wv = alpha * Ti;
+                const float dal = Ti * ((st.c.x - SCr) * gr + (st.c.y - SCg) * gg + (st.c.z - SCb) * gb +
+                                        (st.c.w - SD) * gD + (1.0f - SA) * gA) -
+                                  (Tf * rom) * bgdot;
+                SCr = alpha * st.c.x + om * SCr;
+                SCg = alpha * st.c.y + om * SCg;
+                SCb = alpha * st.c.z + om * SCb;
+                SD = alpha * st.c.w + om * SD;
+                SA = alpha + om * SA;
+                if (!(st.b.w * ep > kAlphaCap)) G = dal * alpha;
+                T = Ti;
+            }
+            const uint32_t cm = __ballot_sync(kFull, hit);
+            if (hit) S.pairs[np + __popc(cm & lane_mask_lt(lane))] = make_float2(G, wv);
+            if (lane == j) {
+                my_cm = cm;
+                my_base = np;
+            }
+            np += __popc(cm);
+        }
+        __syncwarp();
+        bwdl_reduce<POSE>(v, a, S, j0, n, lane, my_cm, my_base, my_g, my_w0, bx, by, pose);
+        __syncwarp();                   // the next round overwrites the staged entries
+        if (n < 32) break;
+    }
+    if (POSE && v.d_pose) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            float x = pose[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+            if (lane == 0 && x != 0.f) atomicAdd(&v.d_pose[q], x);
+        }
+    }
+}
+
+template <int TW, int TH, bool POSE>
+__global__ void __launch_bounds__(kLocalThreads, SGAD_BWDL_MINBLOCKS)
+    k_composite_bwdl(const __grid_constant__ Scene sc, const CompositeArgs a)
+{
+    static_assert(TW * TH == 256 && TW % 8 == 0 && TH % 4 == 0, "tile must hold eight 8x4 blocks");
+    extern __shared__ float4 bwdl_smem[];
+    LocalWarpSmem &S = reinterpret_cast<LocalWarpSmem *>(bwdl_smem)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    if (a.hdr->overflow) return;
+    const uint32_t n_units = (uint32_t)a.n_launch_tiles * 8u;
+    for (;;) {
+        uint32_t u = 0u;
+        if (lane == 0) u = atomicAdd(a.queue, 1u);
+        u = __shfl_sync(kFull, u, 0);
+        if (u >= n_units) break;
+        const int tile = a.order ? (int)a.order[u >> 3] : a.tile0 + (int)(u >> 3);
+        bwdl_unit<TW, TH, POSE>(sc, a, tile, (int)(u & 7u), S, lane);
+    }
+}
+
 // ------------------------------------------------------------------ launch
 
 // Batch sizes the kernels are built for (entries staged per block-wide barrier).
@@ -947,14 +1192,42 @@ cudaError_t launch_bwdp(const Scene &sc, const CompositeArgs &a, int grid_blocks
     return cudaGetLastError();
 }
 
+template <int TW, int TH>
+cudaError_t launch_bwdl(const Scene &sc, const CompositeArgs &a, int grid_blocks, int *occupancy, cudaStream_t st)
+{
+    static int configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
+        e = cudaFuncSetAttribute(k_composite_bwdl<TW, TH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kLocalSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_composite_bwdl<TW, TH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kLocalSmemBytes);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) configured[dev] = 1;
+    }
+    if (occupancy)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_composite_bwdl<TW, TH, false>, kLocalThreads,
+                                                             kLocalSmemBytes);
+    if (grid_blocks <= 0) return cudaSuccess;
+    if (a.pose)
+        k_composite_bwdl<TW, TH, true><<<grid_blocks, kLocalThreads, kLocalSmemBytes, st>>>(sc, a);
+    else
+        k_composite_bwdl<TW, TH, false><<<grid_blocks, kLocalThreads, kLocalSmemBytes, st>>>(sc, a);
+    return cudaGetLastError();
+}
+
 // Dispatch on the batch size for one tile shape (instantiated in one translation unit per
-// shape); batch 0 in the backward selects the pair-parallel kernel. occupancy != nullptr:
-// only report the resident blocks per SM.
+// shape); in the backward, batch 0 selects the pair-parallel kernel and a negative batch
+// the warp-local one. occupancy != nullptr: only report the resident blocks per SM.
 template <int TW, int TH>
 cudaError_t launch_composite_shape(bool fwd, int batch, const Scene &sc, const CompositeArgs &a, int grid_blocks,
                                    int *occupancy, cudaStream_t st)
 {
     if (!fwd && batch == 0) return launch_bwdp<TW, TH>(sc, a, grid_blocks, occupancy, st);
+    if (!fwd && batch < 0) return launch_bwdl<TW, TH>(sc, a, grid_blocks, occupancy, st);
 #define SGAD_BATCH_CASE(Bv)                                                                     \
     case Bv:                                                                                    \
         return occupancy ? occupancy_tb<TW, TH, Bv>(fwd, occupancy)                            \

@@ -5,4 +5,5 @@ namespace sgad {
 template cudaError_t launch_composite_shape<16, 16>(bool, int, const Scene &, const CompositeArgs &, int, int *,
                                                    cudaStream_t);
 template cudaError_t launch_bwdp<16, 16>(const Scene &, const CompositeArgs &, int, int *, cudaStream_t);
+template cudaError_t launch_bwdl<16, 16>(const Scene &, const CompositeArgs &, int, int *, cudaStream_t);
 }  // namespace sgad

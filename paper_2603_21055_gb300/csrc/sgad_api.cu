@@ -250,7 +250,14 @@ sgad_status run_composite(const sgad_ctx *ctx, bool fwd, int batch, int schedule
     return e == cudaSuccess ? SGAD_OK : cuda_fail(e, fwd ? "forward compositing launch" : "backward compositing launch");
 }
 
-int bwd_batch_of(const sgad_options &o) { return o.bwd_algorithm == SGAD_BWD_PAIRS ? 0 : o.bwd_batch; }
+// The batch argument of the backward launch: 0 selects the pair-parallel kernel, a
+// negative value the warp-local one.
+int bwd_batch_of(const sgad_options &o)
+{
+    if (o.bwd_algorithm == SGAD_BWD_PAIRS) return 0;
+    if (o.bwd_algorithm == SGAD_BWD_WARP_LOCAL) return -1;
+    return o.bwd_batch;
+}
 
 // Output images of sgad_forward into the launch parameters.
 sgad_status bind_images(Scene &sc, const sgad_images *out, int n_views)
@@ -355,7 +362,7 @@ sgad_status sgad_default_options(sgad_options *opt)
     opt->bwd_batch = 256;
     opt->fwd_schedule = SGAD_SCHEDULE_TILES;
     opt->bwd_schedule = SGAD_SCHEDULE_TILES;
-    opt->bwd_algorithm = SGAD_BWD_WARP_REDUCE;
+    opt->bwd_algorithm = SGAD_BWD_WARP_LOCAL;
     return SGAD_OK;
 }
 
@@ -381,7 +388,8 @@ sgad_status sgad_create(sgad_ctx **out, const sgad_options *opt)
     for (int i = 0; i < 2; ++i)
         if (o.reserved[i] != 0) return fail(SGAD_ERR_INVALID_ARG, "reserved options must be zero");
     if (o.max_blocks < 0) return fail(SGAD_ERR_INVALID_ARG, "max_blocks must be >= 0");
-    if (o.bwd_algorithm != SGAD_BWD_PAIRS && o.bwd_algorithm != SGAD_BWD_WARP_REDUCE)
+    if (o.bwd_algorithm != SGAD_BWD_PAIRS && o.bwd_algorithm != SGAD_BWD_WARP_REDUCE &&
+        o.bwd_algorithm != SGAD_BWD_WARP_LOCAL)
         return fail(SGAD_ERR_INVALID_ARG, "unknown backward algorithm %d", o.bwd_algorithm);
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(o.bg[c])) return fail(SGAD_ERR_INVALID_ARG, "background must be finite");
@@ -732,7 +740,7 @@ sgad_status sgad_autotune(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
         s = timer.median(reps, st, [&] { return run_composite(&trial, true, fb, fs, sc, ws, st); }, &fwd_words);
         if (s) return s;
         const float words_cost = fwd_words > best_f ? fwd_words - best_f : 0.f;
-        static const int kBwdBatches[6] = {0, 128, 192, 256, 384, 512};     // 0: pair-parallel
+        static const int kBwdBatches[7] = {-1, 0, 128, 192, 256, 384, 512};  // -1: warp-local, 0: pair-parallel
         for (int sched : kScheds)
             for (int batch : kBwdBatches) {
                 float ms = 0.f;
@@ -758,8 +766,8 @@ sgad_status sgad_autotune(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
             best.tile_h = shape[1];
             best.fwd_batch = fb;
             best.fwd_schedule = fs;
-            best.bwd_algorithm = bb == 0 ? SGAD_BWD_PAIRS : SGAD_BWD_WARP_REDUCE;
-            best.bwd_batch = bb == 0 ? ctx->opt.bwd_batch : bb;
+            best.bwd_algorithm = bb == 0 ? SGAD_BWD_PAIRS : (bb < 0 ? SGAD_BWD_WARP_LOCAL : SGAD_BWD_WARP_REDUCE);
+            best.bwd_batch = bb <= 0 ? ctx->opt.bwd_batch : bb;
             best.bwd_schedule = bs;
         }
     }

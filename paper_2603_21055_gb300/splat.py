@@ -115,7 +115,7 @@ class Splatter:
 
     def __init__(self, tile=(16, 16), bg=(0.0, 0.0, 0.0), sort_smem_cap: int = 0, freeze_offset: bool = False,
                  fwd_batch: int = 0, bwd_batch: int = 0, fwd_schedule="tiles", bwd_schedule="tiles",
-                 bwd_algorithm: str = "warp_reduce", max_blocks: int = 0, options=None):
+                 bwd_algorithm: str = "warp_local", max_blocks: int = 0, options=None):
         """options: a complete sgad_options (e.g. another Splatter's tuned options), used
         instead of the other arguments. max_blocks caps the persistent grid (0: as many
         blocks as are resident)."""
@@ -134,7 +134,8 @@ class Splatter:
                 o.bwd_batch = int(bwd_batch)
             o.fwd_schedule = _schedule(fwd_schedule)
             o.bwd_schedule = _schedule(bwd_schedule)
-            o.bwd_algorithm = {"pairs": B.SGAD_BWD_PAIRS, "warp_reduce": B.SGAD_BWD_WARP_REDUCE}[bwd_algorithm]
+            o.bwd_algorithm = {"pairs": B.SGAD_BWD_PAIRS, "warp_reduce": B.SGAD_BWD_WARP_REDUCE,
+                               "warp_local": B.SGAD_BWD_WARP_LOCAL}[bwd_algorithm]
             o.max_blocks = int(max_blocks)
         self.options = o
         self.ctx = B.sgad_create(o)

@@ -33,7 +33,7 @@ def test_default_options_and_create():
     assert (o.tile_w, o.tile_h) == (16, 16) and o.freeze_offset == 0
     assert (o.fwd_batch, o.bwd_batch) == (512, 256)
     assert o.fwd_schedule == o.bwd_schedule == B.SGAD_SCHEDULE_TILES
-    assert o.bwd_algorithm == B.SGAD_BWD_WARP_REDUCE
+    assert o.bwd_algorithm == B.SGAD_BWD_WARP_LOCAL
     ctx = B.sgad_create(o)
     B.sgad_destroy(ctx)
     for w, h in ((8, 32), (32, 8)):
@@ -80,7 +80,8 @@ def test_autotune_validates_on_the_host():
     ("bwd_batch", 1024, B.SGAD_ERR_UNSUPPORTED),
     ("fwd_schedule", 3, B.SGAD_ERR_INVALID_ARG),
     ("bwd_schedule", -1, B.SGAD_ERR_INVALID_ARG),
-    ("bwd_algorithm", 2, B.SGAD_ERR_INVALID_ARG),
+    ("bwd_algorithm", 3, B.SGAD_ERR_INVALID_ARG),
+    ("max_blocks", -1, B.SGAD_ERR_INVALID_ARG),
 ])
 def test_create_rejects_bad_options(field, value, status):
     o = B.sgad_default_options()

@@ -59,7 +59,7 @@ def test_every_split_matches_default(uneven, uneven_grads, tile):
     base = gpu_run(uneven, grads_in=uneven_grads, tile=tile)
     for sched in SCHEDULES:
         for fb, bb in zip(BATCHES + (768, 1024), BATCHES[::-1] + (256, 128)):
-            for algo in ("pairs", "warp_reduce"):
+            for algo in ("pairs", "warp_reduce", "warp_local"):
                 res = gpu_run(uneven, grads_in=uneven_grads, tile=tile, fwd_batch=fb, bwd_batch=bb,
                               fwd_schedule=sched, bwd_schedule=sched, bwd_algorithm=algo)
                 _same_forward(res, base)
@@ -67,8 +67,9 @@ def test_every_split_matches_default(uneven, uneven_grads, tile):
 
 
 @pytest.mark.parametrize("tile", SHAPES)
-@pytest.mark.parametrize("batches,max_blocks", [((192, 384), 0), ((512, 512), 6)])
-def test_persistent_split_against_oracle(uneven, uneven_grads, tile, batches, max_blocks):
+@pytest.mark.parametrize("batches,max_blocks,algo", [((192, 384), 0, "warp_reduce"), ((512, 512), 6, "warp_reduce"),
+                                                     ((512, 512), 0, "warp_local"), ((512, 512), 6, "warp_local")])
+def test_persistent_split_against_oracle(uneven, uneven_grads, tile, batches, max_blocks, algo):
     """The persistent schedule against the oracle. With max_blocks = 6 (the batches the
     room benchmark's autotuner picks) every block takes ~60 tiles from the queue, so the
     per-block loop over tiles (state reset, next tile read, per-tile masks) is what runs;
@@ -77,7 +78,7 @@ def test_persistent_split_against_oracle(uneven, uneven_grads, tile, batches, ma
     ref = oracle.render(uneven, o)
     _, g = l1_grads(uneven, ref)
     res = gpu_run(uneven, grads_in=g, tile=tile, fwd_batch=batches[0], bwd_batch=batches[1],
-                  fwd_schedule="persistent", bwd_schedule="persistent", max_blocks=max_blocks)
+                  fwd_schedule="persistent", bwd_schedule="persistent", max_blocks=max_blocks, bwd_algorithm=algo)
     compare_keys(res, uneven, o)
     worst, n_near = compare_images(res, ref)
     og = oracle.backward(uneven, [{k: v.astype(np.float64) for k, v in x.items()} for x in g], o)
@@ -85,8 +86,8 @@ def test_persistent_split_against_oracle(uneven, uneven_grads, tile, batches, ma
     # so the ~100 pixels with a near decision flag ~15% of the Gaussians (every Gaussian a
     # flagged walk reaches); those are still held to the near-decision bound.
     e = compare_grads(res, og, max_near_frac=0.2)
-    print("uneven %dx%d persistent %s cap %d: img %.2e near px %d grad ratio %.3f" %
-          (tile + (batches, max_blocks, worst, n_near, e)))
+    print("uneven %dx%d persistent %s cap %d %s: img %.2e near px %d grad ratio %.3f" %
+          (tile + (batches, max_blocks, algo, worst, n_near, e)))
     print(grad_stats_line("uneven %dx%d" % tile))
     assert e <= 1.0
 
@@ -103,13 +104,13 @@ def test_autotune_times_every_candidate(uneven, uneven_grads):
     gout = [dict(d_offset=torch.empty_like(k.offset), d_rgb=torch.empty_like(k.rgb), d_logit=torch.empty_like(k.logit),
                  d_scale=torch.empty_like(k.scale)) for k in kfs]
     rows = sp.autotune(kfs, uneven.views, images, gin, gout, reps=2)
-    # per tile shape: the prep row, forward batches x schedules, backward (pair-parallel
-    # as batch 0, then the warp-reduced batches) x schedules
-    assert len(rows) == 3 * (1 + 2 * (len(BATCHES) + 2) + 2 * (len(BATCHES) + 1))
+    # per tile shape: the prep row, forward batches x schedules, backward (warp-local as
+    # batch -1, pair-parallel as batch 0, then the warp-reduced batches) x schedules
+    assert len(rows) == 3 * (1 + 2 * (len(BATCHES) + 2) + 2 * (len(BATCHES) + 2))
     assert all(r["ms"] > 0 for r in rows)
     o = sp.options
     assert (o.tile_w, o.tile_h) in SHAPES and o.fwd_batch in BATCHES + (768, 1024) and o.bwd_batch in BATCHES
-    assert o.bwd_algorithm in (B.SGAD_BWD_PAIRS, B.SGAD_BWD_WARP_REDUCE)
+    assert o.bwd_algorithm in (B.SGAD_BWD_PAIRS, B.SGAD_BWD_WARP_REDUCE, B.SGAD_BWD_WARP_LOCAL)
     assert o.fwd_schedule in (B.SGAD_SCHEDULE_TILES, B.SGAD_SCHEDULE_PERSISTENT)
     # the chosen split renders what the default split of that tile shape renders
     sp.forward(kfs, uneven.views, images)

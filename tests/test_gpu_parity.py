@@ -61,12 +61,19 @@ def test_crop_forward_backward(crop):
     assert e <= 1.0
 
 
-def test_crop_pair_parallel_backward(crop):
-    """The pair-parallel backward (the non-default algorithm) against the oracle."""
-    ref, g = _grads_for(crop)
-    res = gpu_run(crop, grads_in=g, bwd_algorithm="pairs")
-    og = oracle.backward(crop, [{k: v.astype(np.float64) for k, v in x.items()} for x in g])
-    assert compare_grads(res, og) <= 1.0
+@pytest.mark.parametrize("algo", ["pairs", "warp_reduce", "warp_local"])
+def test_backward_algorithms(scene1, crop, algo):
+    """Every backward algorithm against the oracle, on the plane and the room crop, and
+    under the persistent schedule with a grid of 3 blocks (each block, or each of its
+    warps, takes many tiles from the queue)."""
+    for sc in (scene1, crop):
+        ref, g = _grads_for(sc)
+        og = oracle.backward(sc, [{k: v.astype(np.float64) for k, v in x.items()} for x in g])
+        for split in (dict(), dict(bwd_schedule="persistent", fwd_schedule="persistent", max_blocks=3)):
+            res = gpu_run(sc, grads_in=g, bwd_algorithm=algo, **split)
+            e = compare_grads(res, og)
+            print(grad_stats_line("%s %s %s" % (sc.name, algo, "capped persistent" if split else "tiles")))
+            assert e <= 1.0
 
 
 @pytest.mark.parametrize("tile", [(8, 32), (32, 8)])
@@ -181,7 +188,7 @@ def test_invalid_arguments_return_status(scene1):
         B.SGAD_ERR_INVALID_ARG            # NULL output images
 
 
-@pytest.mark.parametrize("algo", ["warp_reduce", "pairs"])
+@pytest.mark.parametrize("algo", ["warp_reduce", "pairs", "warp_local"])
 def test_view_pose_gradient(scene1, crop, algo):
     """d loss / d (world->cam 3x4) of every view against the oracle's pose adjoint, on the
     plane and on the two-view room crop, with both backward algorithms."""
