@@ -985,7 +985,10 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
     __syncwarp();                       // the previous unit's readers of S are done
     S.pg[lane] = make_float4(gr, gg, gb, gD);
     const float bgdot = sc.bg[0] * gr + sc.bg[1] * gg + sc.bg[2] * gb;
-    float T = Tf, SCr = 0.f, SCg = 0.f, SCb = 0.f, SD = 0.f, SA = 0.f;
+    // Reverse-walk state: transmittance, and the suffix sums of colour and depth behind
+    // the current entry already dotted with this pixel's image gradients (Sg = S_C . g_C
+    // + S_D g_D, updated as Sg <- alpha (c . g) + (1 - alpha) Sg) plus the alpha suffix.
+    float T = Tf, Sg = 0.f, SA = 0.f;
     float pose[12];
 #pragma unroll
     for (int q = 0; q < 12; ++q) pose[q] = 0.f;
@@ -1054,13 +1057,9 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
                 const float rom = __fdividef(1.0f, om);     // om >= 0.01: fast reciprocal
                 const float Ti = T * rom;
                 wv = alpha * Ti;
-                const float dal = Ti * ((st.c.x - SCr) * gr + (st.c.y - SCg) * gg + (st.c.z - SCb) * gb +
-                                        (st.c.w - SD) * gD + (1.0f - SA) * gA) -
-                                  (Tf * rom) * bgdot;
-                SCr = alpha * st.c.x + om * SCr;
-                SCg = alpha * st.c.y + om * SCg;
-                SCb = alpha * st.c.z + om * SCb;
-                SD = alpha * st.c.w + om * SD;
+                const float cg = st.c.x * gr + st.c.y * gg + st.c.z * gb + st.c.w * gD;
+                const float dal = Ti * ((cg - Sg) + (1.0f - SA) * gA) - (Tf * rom) * bgdot;
+                Sg = alpha * cg + om * Sg;
                 SA = alpha + om * SA;
                 if (!(st.b.w * ep > kAlphaCap)) G = dal * alpha;
                 T = Ti;
