@@ -882,53 +882,94 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_composite_bwdp(const __grid
 // given, so warps never wait for one another. A unit walks its marked entries from the
 // largest contributor count down in rounds of up to 32:
 //   1. gather: the next (lower) marked positions, highest first, one per lane;
-//   2. stage: each lane projects its entry into the warp's shared memory;
-//   3. walk: for each staged entry in order, every lane whose pixel it reaches recovers
-//      the transmittance by division, forms dL/dalpha from the suffix sums and stores
-//      (G = alpha dL/dalpha, zero at the alpha cap; w = alpha T) into a per-warp pair
-//      buffer, compacted by a ballot;
-//   4. reduce: lane j sums the ten moments of entry j over the pixels it reached (colour
-//      and depth: w times the pixel's image gradients; G, G dx, G dy, G dx^2, G dx dy,
-//      G dy^2), applies the chain rule and adds the result with two vector atomics.
-// The pair buffer holds kLocalPairCap pairs; a round that would overflow it reduces the
-// entries walked so far first. The per-pair arithmetic is the warp-reduced backward's.
+//   2. stage: lane j projects entry j into the warp's shared memory and forms its box
+//      mask, the pixels of the block inside the entry's alpha >= 1/255 box;
+//   3. transpose the 32 x 32 bit matrix of box masks (five xor-shuffle steps), so that
+//      each lane holds the entries whose box covers its pixel, and drop those at or past
+//      the pixel's contributor count;
+//   4. walk: each lane visits only its own entries, in order, recovers the transmittance
+//      by division, forms dL/dalpha from its suffix sums and, where the entry contributes,
+//      stores (G = alpha dL/dalpha, zero at the alpha cap; w = alpha T) in the entry's
+//      slot range of a per-warp pair buffer (a slot per box pixel);
+//   5. reduce: the lanes' contribution bits are transposed back, and lane j sums the ten
+//      moments of entry j over the pixels it reached (colour and depth: w times the
+//      pixel's image gradients; G, G dx, G dy, G dx^2, G dx dy, G dy^2), applies the chain
+//      rule and adds the result with two vector atomics.
+// Entries whose box slots do not fit the pair buffer together are walked and reduced in
+// consecutive sub-ranges. The per-pair arithmetic is the warp-reduced backward's; no
+// lane steps through an entry whose box misses its pixel.
 constexpr int kLocalThreads = 256;          // 8 independent warps per block
-constexpr int kLocalPairCap = 480;          // (G, w) pairs buffered per warp
+constexpr int kLocalPairCap = 512;          // (G, w) slots per warp
 #ifndef SGAD_BWDL_MINBLOCKS
 #define SGAD_BWDL_MINBLOCKS 4
 #endif
 
 struct LocalWarpSmem {
-    Staged st[32];                  // the round's entries
+    float4 sa[32], sb[32], sc[32];  // the round's entries (Staged a, b, c)
     float4 pg[32];                  // image gradients (r, g, b, depth) of the unit's pixels
-    float2 pairs[kLocalPairCap];    // (G, w) per contributing (entry, pixel) pair
+    float2 pairs[kLocalPairCap];    // (G, w) per box pixel of each entry
+    uint32_t row[32];               // box mask of entry j over the block's pixels
+    int32_t base[32];               // first pair slot of entry j
+    int32_t pos[32];                // list position of entry j (descending in j)
 };
 constexpr size_t kLocalSmemBytes = (kLocalThreads / 32) * sizeof(LocalWarpSmem);
 
 __device__ __forceinline__ uint32_t lane_mask_lt(int lane) { return (1u << lane) - 1u; }
 
-// Moments of the round's entries [j0, j1) (lane j holds entry j: its contributing-pixel
-// mask cm, first pair index base, Gaussian g and world record w0), the chain rule, and the
-// pose terms accumulated per lane. Whole warp.
+// 32 x 32 bit transpose across the warp: lane j holds row j on entry; on return lane i
+// holds column i (bit j = bit i of row j). Swaps the off-diagonal blocks of halving size.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
+{
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000ffffu : (s == 8 ? 0x00ff00ffu : (s == 4 ? 0x0f0f0f0fu :
+                           (s == 2 ? 0x33333333u : 0x55555555u)));
+        const uint32_t y = __shfl_xor_sync(kFull, x, s);
+        x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
+    }
+    return x;
+}
+
+// Pixels (bit p: pixel (bx + p % 8, by + p / 8)) of an 8x4 block inside the box
+// |px - x| <= hx, |py - y| <= hy of a staged entry; hx < 0 marks an empty box.
+__device__ __forceinline__ uint32_t box_block_mask(const float4 a, float bxf, float byf)
+{
+    if (!(a.z >= 0.0f)) return 0u;
+    const float x0 = fmaxf(ceilf(a.x - a.z) - bxf, 0.0f), x1 = fminf(floorf(a.x + a.z) - bxf, 7.0f);
+    const float y0 = fmaxf(ceilf(a.y - a.w) - byf, 0.0f), y1 = fminf(floorf(a.y + a.w) - byf, 3.0f);
+    if (!(x0 <= x1) || !(y0 <= y1)) return 0u;
+    const int xl = (int)x0, xh = (int)x1, yl = (int)y0, yh = (int)y1;
+    const uint32_t cols = (0xffu >> (7 - (xh - xl))) << xl;
+    const uint32_t rows = (0xffffffffu >> (8 * (3 - (yh - yl)))) << (8 * yl);
+    return (cols * 0x01010101u) & rows;
+}
+
+// Moments of the entries [j0, j1) of a round (lane j holds entry j: the pixels it
+// contributed to, cm, its Gaussian g and world record w0; its pair slots start at
+// base_j - b0), the chain rule, and the pose terms accumulated per lane. Whole warp.
 template <bool POSE>
 __device__ __forceinline__ void bwdl_reduce(const ViewDev &v, const CompositeArgs &a, const LocalWarpSmem &S, int j0,
-                                            int j1, int lane, uint32_t cm, int base, uint32_t g, float4 w0, int bx,
-                                            int by, float (&pose)[12])
+                                            int j1, int lane, uint32_t cm, uint32_t g, float4 w0, float bxf, float byf,
+                                            int b0, float (&pose)[12])
 {
     if (lane < j0 || lane >= j1 || cm == 0u) return;
-    const Staged st = S.st[lane];
+    Staged st;
+    st.a = S.sa[lane];
+    st.b = S.sb[lane];
+    st.c = S.sc[lane];
+    const uint32_t row = S.row[lane];
+    const int base = S.base[lane] - b0;
     float A[10];
 #pragma unroll
     for (int q = 0; q < 10; ++q) A[q] = 0.f;
-    int k = base;
     uint32_t m = cm;
     while (m) {
         const int p = __ffs(m) - 1;
         m &= m - 1u;
-        const float2 gw = S.pairs[k++];
+        const float2 gw = S.pairs[base + __popc(row & lane_mask_lt(p))];
         const float4 pg = S.pg[p];
-        const float dx = __fsub_rn(st.a.x, (float)(bx + (p & 7)));
-        const float dy = __fsub_rn(st.a.y, (float)(by + (p >> 3)));
+        const float dx = __fsub_rn(st.a.x, bxf + (float)(p & 7));
+        const float dy = __fsub_rn(st.a.y, byf + (float)(p >> 3));
         A[0] += gw.y * pg.x;
         A[1] += gw.y * pg.y;
         A[2] += gw.y * pg.z;
@@ -960,6 +1001,7 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
     const int local = tile - v.tile_base;
     const int tx = local % v.tiles_x, ty = local / v.tiles_x;
     const int bx = tx * TW + (wb % (TW / 8)) * 8, by = ty * TH + (wb / (TW / 8)) * 4;
+    const float bxf = (float)bx, byf = (float)by;
     const int px = bx + (lane & 7), py = by + (lane >> 3);
     const float qx = (float)px, qy = (float)py;
     const uint32_t s = a.off[tile];
@@ -1024,57 +1066,81 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
             ++n;
         }
         if (n == 0) break;
-        // 2. stage (lane j: entry j)
-        uint32_t my_g = 0u;
+        // 2. stage (lane j: entry j) and the box masks
+        uint32_t my_g = 0u, row = 0u;
         float4 my_w0 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (lane < n) {
             const uint64_t ent = a.entries[s + my_pos];
             my_g = (uint32_t)ent;
             const World w = a.world[my_g];
             my_w0 = w.w0;
-            stage(project(w.w0, v), w.w1, __uint_as_float((uint32_t)(ent >> 32)), S.st[lane]);
+            Staged st;
+            stage(project(w.w0, v), w.w1, __uint_as_float((uint32_t)(ent >> 32)), st);
+            S.sa[lane] = st.a;
+            S.sb[lane] = st.b;
+            S.sc[lane] = st.c;
+            row = box_block_mask(st.a, bxf, byf);
         }
-        __syncwarp();
-        // 3. walk, 4. reduce
-        uint32_t my_cm = 0u;
-        int my_base = 0, np = 0, j0 = 0;
-        for (int j = 0; j < n; ++j) {
-            if (np > kLocalPairCap - 32) {
-                __syncwarp();
-                bwdl_reduce<POSE>(v, a, S, j0, j, lane, my_cm, my_base, my_g, my_w0, bx, by, pose);
-                __syncwarp();
-                np = 0;
-                j0 = j;
-            }
-            const int lim = __shfl_sync(kFull, my_pos, j);
-            const Staged st = S.st[j];
-            bool hit = false;
-            float G = 0.f, wv = 0.f;
-            float dx, dy, ep, alpha;
-            if (lim < nc && gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) {
-                hit = true;
-                const float om = __fsub_rn(1.0f, alpha);
-                const float rom = __fdividef(1.0f, om);     // om >= 0.01: fast reciprocal
-                const float Ti = T * rom;
-                wv = alpha * Ti;
-                const float cg = st.c.x * gr + st.c.y * gg + st.c.z * gb + st.c.w * gD;
-                const float dal = Ti * ((cg - Sg) + (1.0f - SA) * gA) - (Tf * rom) * bgdot;
-                Sg = alpha * cg + om * Sg;
-                SA = alpha + om * SA;
-                if (!(st.b.w * ep > kAlphaCap)) G = dal * alpha;
-                T = Ti;
-            }
-            const uint32_t cm = __ballot_sync(kFull, hit);
-            if (hit) S.pairs[np + __popc(cm & lane_mask_lt(lane))] = make_float2(G, wv);
-            if (lane == j) {
-                my_cm = cm;
-                my_base = np;
-            }
-            np += __popc(cm);
+        // pair slots: entry j owns popc(row_j) slots from base_j (exclusive prefix)
+        const int cnt = __popc(row);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
         }
+        S.row[lane] = row;
+        S.base[lane] = incl - cnt;
+        S.pos[lane] = lane < n ? my_pos : -1;
+        // 3. the entries whose box covers this pixel, before its contributor count
+        uint32_t mine = warp_transpose32(row, lane);
         __syncwarp();
-        bwdl_reduce<POSE>(v, a, S, j0, n, lane, my_cm, my_base, my_g, my_w0, bx, by, pose);
-        __syncwarp();                   // the next round overwrites the staged entries
+        {
+            int lo = 0, hi = n;                 // first j with pos_j < nc (positions descend)
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (S.pos[mid] >= nc) lo = mid + 1; else hi = mid;
+            }
+            mine &= lo >= 32 ? 0u : (~0u << lo);
+        }
+        // 4./5. walk and reduce, in sub-ranges whose box slots fit the pair buffer
+        int j0 = 0;
+        while (j0 < n) {
+            const int b0 = __shfl_sync(kFull, incl - cnt, j0);
+            const uint32_t fit = __ballot_sync(kFull, lane >= j0 && lane < n && incl - b0 <= kLocalPairCap);
+            const int j1 = fit ? 32 - __clz(fit) : j0 + 1;   // fit is a run of lanes from j0
+            const uint32_t range = (j1 >= 32 ? ~0u : ((1u << j1) - 1u)) & (~0u << j0);
+            uint32_t todo = mine & range, done = 0u;
+            while (__any_sync(kFull, todo != 0u)) {
+                if (todo) {
+                    const int j = __ffs(todo) - 1;
+                    todo &= todo - 1u;
+                    Staged st;
+                    st.a = S.sa[j];
+                    st.b = S.sb[j];
+                    st.c = S.sc[j];
+                    float dx, dy, ep, alpha;
+                    if (gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) {
+                        const float om = __fsub_rn(1.0f, alpha);
+                        const float rom = __fdividef(1.0f, om);     // om >= 0.01: fast reciprocal
+                        const float Ti = T * rom;
+                        const float cg = st.c.x * gr + st.c.y * gg + st.c.z * gb + st.c.w * gD;
+                        const float dal = Ti * ((cg - Sg) + (1.0f - SA) * gA) - (Tf * rom) * bgdot;
+                        Sg = alpha * cg + om * Sg;
+                        SA = alpha + om * SA;
+                        const float G = (st.b.w * ep > kAlphaCap) ? 0.f : dal * alpha;
+                        S.pairs[S.base[j] - b0 + __popc(S.row[j] & lane_mask_lt(lane))] = make_float2(G, alpha * Ti);
+                        T = Ti;
+                        done |= 1u << j;
+                    }
+                }
+            }
+            const uint32_t cm = warp_transpose32(done, lane);
+            __syncwarp();
+            bwdl_reduce<POSE>(v, a, S, j0, j1, lane, cm, my_g, my_w0, bxf, byf, b0, pose);
+            __syncwarp();               // the next sub-range overwrites the pair slots
+            j0 = j1;
+        }
         if (n < 32) break;
     }
     if (POSE && v.d_pose) {
