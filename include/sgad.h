@@ -182,8 +182,9 @@ const char *sgad_last_error(void);
 /* Bytes of workspace needed for a problem of this shape holding up to key_capacity
  * (tile, Gaussian) keys. Host arithmetic only. The workspace holds the per-Gaussian
  * world records and gradient accumulators (64 B per Gaussian), per-tile offsets,
- * counters and heavy-first order (12 B per tile), the per-pixel state kept for the
- * backward pass (8 B per view pixel), two key arrays (16 B per key), the per-pixel
+ * counters, heavy-first order and the list of tiles sorted exactly (16 B per tile), the
+ * per-pixel state kept for the backward pass (8 B per view pixel), two key arrays
+ * (16 B per key), the per-pixel
  * contribution words of the pair-parallel backward (32 B per key + 1 KB per tile) and
  * the per-warp contribution masks the forward leaves for the warp-local and
  * warp-reduced backwards (1 B per key + 64 B per tile). */
@@ -291,12 +292,15 @@ sgad_status sgad_state(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_
 
 /* Work counters of the last forward on this workspace (synchronises `stream`): keys
  * emitted, keys needed, (pixel, entry) pairs composited (the contributors: alpha >= 1/255
- * before the stop) and pairs whose alpha was evaluated. Host memory out. */
+ * before the stop), pairs whose alpha was evaluated, and tiles the one-pass bucket sort
+ * handed to the exact radix sort (a bucket of many near-equal depths, or a long list).
+ * Host memory out. */
 typedef struct {
     int64_t n_keys;
     int64_t keys_needed;
     int64_t n_pairs;
     int64_t n_evals;
+    int64_t n_sort_exact;
 } sgad_stats;
 
 sgad_status sgad_read_stats(sgad_ctx *ctx, void *workspace, size_t ws_bytes, sgad_stats *out,

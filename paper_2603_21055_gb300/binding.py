@@ -128,7 +128,7 @@ class sgad_adam_tensor(C.Structure):
 
 class sgad_stats(C.Structure):
     _fields_ = [("n_keys", C.c_int64), ("keys_needed", C.c_int64), ("n_pairs", C.c_int64),
-                ("n_evals", C.c_int64)]
+                ("n_evals", C.c_int64), ("n_sort_exact", C.c_int64)]
 
 
 SGAD_NET_LAYERS = 4

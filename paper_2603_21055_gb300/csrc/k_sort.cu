@@ -6,8 +6,20 @@
 // 64-bit integers gives exactly the front-to-back order by (depth, index) with ties
 // broken by the lower index; positive floats order like their bit patterns.
 //
-// One CTA per tile. A bucket of up to `cap` entries is sorted in shared memory by a
-// least-significant-digit radix sort on the depth field only: the bits that vary within
+// Default path (k_sort_tiles_bucket): one CTA per tile of up to 6,144 entries (and at
+// most `cap`) sorts it in one pass through shared memory. The depth field minus the
+// tile's smallest depth, shifted right so that the tile's range spans as many buckets as
+// the power of two at or above its entry count (at most 4,096), picks each entry's
+// bucket; a shared-memory atomic per entry gives both the bucket counts and each entry's
+// slot in its bucket; after a scan of the counts every entry is written to its bucket,
+// and each bucket is put in exact order (depth, then index) by one thread's insertion
+// sort. Buckets are small because the bucket width follows the tile's own depth range
+// (room workload: at most ~20 entries). A tile with a bucket of more than kBucketMax
+// entries (many equal or nearly equal depths), or with more entries than the bucket
+// path holds, is listed and sorted afterwards by the exact radix sort below.
+//
+// Exact path (k_sort_tiles over the listed tiles): a bucket of up to `cap` entries is
+// sorted in shared memory by a least-significant-digit radix sort on the depth field only: the bits that vary within
 // the tile (depth bits minus the tile's smallest, 8 bits per pass, so a tile whose
 // depths share their exponent needs three passes) are ranked stably, warp by warp, with
 // one match per 32 entries. Equal depths then sit in runs in input order; each run is
@@ -20,6 +32,7 @@
 
 namespace sgad {
 
+constexpr unsigned kFull32 = 0xffffffffu;
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadixBins = 256;
@@ -263,15 +276,33 @@ __device__ __forceinline__ void block_sort(const uint64_t *src, uint64_t *ks, So
 }
 
 template <int kPer>
+__device__ __forceinline__ void sort_tile_exact(const uint32_t *__restrict__ off, uint64_t *__restrict__ entries,
+                                                uint64_t *__restrict__ alt, int cap, int t, SortSmem &s,
+                                                uint64_t *ks);
+
+// The tiles the bucket sort listed (hdr->n_sort_exact of them in `list`), taken by the
+// blocks of a fixed grid in turn.
+template <int kPer>
 __global__ void __launch_bounds__(kSortThreads, kPer <= 12 ? 2 : 1)
     k_sort_tiles(const uint32_t *__restrict__ off, uint64_t *__restrict__ entries, uint64_t *__restrict__ alt, int cap,
-                 const WsHeader *hdr)
+                 const WsHeader *hdr, const uint32_t *__restrict__ list)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem &s = *reinterpret_cast<SortSmem *>(smem_raw);
     uint64_t *ks = reinterpret_cast<uint64_t *>(smem_raw + ((sizeof(SortSmem) + 15) & ~size_t(15)));
     if (hdr->overflow) return;
-    const int t = blockIdx.x;
+    const uint32_t n_list = hdr->n_sort_exact;
+    for (uint32_t k = blockIdx.x; k < n_list; k += gridDim.x) {
+        sort_tile_exact<kPer>(off, entries, alt, cap, (int)list[k], s, ks);
+        __syncthreads();
+    }
+}
+
+template <int kPer>
+__device__ __forceinline__ void sort_tile_exact(const uint32_t *__restrict__ off, uint64_t *__restrict__ entries,
+                                                uint64_t *__restrict__ alt, int cap, int t, SortSmem &s,
+                                                uint64_t *ks)
+{
     const uint32_t s0 = off[t];
     const int n = (int)(off[t + 1] - s0);
     if (n <= 1) return;
@@ -308,9 +339,137 @@ __global__ void __launch_bounds__(kSortThreads, kPer <= 12 ? 2 : 1)
         for (int i = threadIdx.x; i < n; i += kSortThreads) gk[i] = src[i];
 }
 
+// ------------------------------------------------------------------ bucket sort
+constexpr int kBucketThreads = 512;
+constexpr int kBucketPer = 12;                          // entries per thread
+constexpr int kBucketEntries = kBucketThreads * kBucketPer;
+constexpr int kBucketBinsLog2 = 12;                     // at most 4,096 buckets
+constexpr int kBucketMax = 64;                          // larger buckets: exact path
+
+__global__ void __launch_bounds__(kBucketThreads, 3)
+    k_sort_tiles_bucket(const uint32_t *__restrict__ off, uint64_t *__restrict__ entries, int cap, WsHeader *hdr,
+                        uint32_t *__restrict__ list)
+{
+    __shared__ uint32_t start[1 << kBucketBinsLog2];    // bucket counts, then bucket starts
+    __shared__ uint32_t red[2][kBucketThreads / 32];
+    __shared__ int heavy;
+    extern __shared__ uint64_t ks[];                     // the tile's entries, bucket by bucket
+    if (hdr->overflow) return;
+    const int t = blockIdx.x;
+    const uint32_t s0 = off[t];
+    const int n = (int)(off[t + 1] - s0);
+    if (n <= 1) return;
+    if (n > cap || n > kBucketEntries) {
+        if (threadIdx.x == 0) list[atomicAdd(&hdr->n_sort_exact, 1u)] = (uint32_t)t;
+        return;
+    }
+    const uint64_t *gk = entries + s0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // depth range of the tile
+    uint32_t mn = 0xffffffffu, mx = 0u;
+#pragma unroll
+    for (int r = 0; r < kBucketPer; ++r) {
+        const int i = threadIdx.x + r * kBucketThreads;
+        if (i < n) {
+            const uint32_t z = (uint32_t)(gk[i] >> 32);
+            mn = min(mn, z);
+            mx = max(mx, z);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(kFull32, mn, o));
+        mx = max(mx, __shfl_xor_sync(kFull32, mx, o));
+    }
+    if (lane == 0) {
+        red[0][w] = mn;
+        red[1][w] = mx;
+    }
+    const int bins_log2 = min(kBucketBinsLog2, 32 - __clz(n - 1));     // 2^bins_log2 >= n
+    const int nbins = 1 << bins_log2;
+    for (int i = threadIdx.x; i < nbins; i += kBucketThreads) start[i] = 0u;
+    if (threadIdx.x == 0) heavy = 0;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kBucketThreads / 32; ++i) {
+        mn = min(mn, red[0][i]);
+        mx = max(mx, red[1][i]);
+    }
+    const int range_bits = mx == mn ? 0 : 32 - __clz(mx - mn);
+    const int shift = range_bits > bins_log2 ? range_bits - bins_log2 : 0;
+    // counts, and each entry's slot in its bucket
+    uint32_t slot[kBucketPer];
+#pragma unroll
+    for (int r = 0; r < kBucketPer; ++r) {
+        const int i = threadIdx.x + r * kBucketThreads;
+        slot[r] = i < n ? atomicAdd(&start[((uint32_t)(gk[i] >> 32) - mn) >> shift], 1u) : 0u;
+    }
+    __syncthreads();
+    // exclusive scan of the counts (each thread nbins / 512 or one consecutive bins)
+    {
+        const int per = nbins > kBucketThreads ? nbins / kBucketThreads : 1;
+        const int b0 = threadIdx.x * per;
+        uint32_t v[8], sum = 0u;
+        bool big = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            v[j] = (j < per && b0 + j < nbins) ? start[b0 + j] : 0u;
+            sum += v[j];
+            big |= v[j] > (uint32_t)kBucketMax;
+        }
+        if (big) heavy = 1;
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull32, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) red[0][w] = inc;
+        __syncthreads();
+        uint32_t run = inc - sum;
+        for (int i = 0; i < w; ++i) run += red[0][i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < per && b0 + j < nbins) {
+                start[b0 + j] = run;
+                run += v[j];
+            }
+    }
+    __syncthreads();
+    if (heavy) {                                         // uniform: read after the barrier
+        if (threadIdx.x == 0) list[atomicAdd(&hdr->n_sort_exact, 1u)] = (uint32_t)t;
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < kBucketPer; ++r) {
+        const int i = threadIdx.x + r * kBucketThreads;
+        if (i < n) {
+            const uint64_t key = gk[i];
+            ks[start[((uint32_t)(key >> 32) - mn) >> shift] + slot[r]] = key;
+        }
+    }
+    __syncthreads();
+    // each bucket in exact 64-bit order (depth, then index)
+    for (int b = threadIdx.x; b < nbins; b += kBucketThreads) {
+        const int lo = (int)start[b], hi = b + 1 < nbins ? (int)start[b + 1] : n;
+        for (int i = lo + 1; i < hi; ++i) {
+            const uint64_t x = ks[i];
+            int j = i - 1;
+            while (j >= lo && ks[j] > x) {
+                ks[j + 1] = ks[j];
+                --j;
+            }
+            ks[j + 1] = x;
+        }
+    }
+    __syncthreads();
+    uint64_t *out = entries + s0;
+    for (int i = threadIdx.x; i < n; i += kBucketThreads) out[i] = ks[i];
+}
+
 template <int kPer>
 static cudaError_t launch_sort(const uint32_t *off, uint64_t *entries, uint64_t *alt, int n_tiles, int cap,
-                               const WsHeader *hdr, cudaStream_t st)
+                               WsHeader *hdr, uint32_t *list, cudaStream_t st)
 {
     // Raise the kernel's dynamic shared-memory limit once per device and size (outside
     // any stream capture, which only replays launches).
@@ -324,16 +483,32 @@ static cudaError_t launch_sort(const uint32_t *off, uint64_t *entries, uint64_t 
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = (int)smem;
     }
-    if (n_tiles > 0) k_sort_tiles<kPer><<<n_tiles, kSortThreads, smem, st>>>(off, entries, alt, cap, hdr);
+    static int bucket_configured[64] = {};
+    constexpr int bucket_smem = kBucketEntries * (int)sizeof(uint64_t);
+    if (dev < 0 || dev >= 64 || !bucket_configured[dev]) {
+        e = cudaFuncSetAttribute(k_sort_tiles_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, bucket_smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) bucket_configured[dev] = 1;
+    }
+    if (n_tiles <= 0) return cudaSuccess;
+    k_sort_tiles_bucket<<<n_tiles, kBucketThreads, bucket_smem, st>>>(off, entries, cap, hdr, list);
+    // the listed tiles: a fixed grid (two blocks per SM) so the launch can be captured
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = n_tiles < 2 * sms ? n_tiles : 2 * sms;
+    k_sort_tiles<kPer><<<grid, kSortThreads, smem, st>>>(off, entries, alt, cap, hdr, list);
     return cudaSuccess;
 }
 
-// cap in [64, 12288] (checked by the caller).
+// cap in [64, 12288] (checked by the caller). list: n_tiles words of workspace for the
+// tiles the bucket sort hands to the exact radix sort (counted in hdr->n_sort_exact,
+// which the forward clears).
 cudaError_t launch_sort_tiles(const uint32_t *off, uint64_t *entries, uint64_t *alt, int n_tiles, int cap,
-                              const WsHeader *hdr, cudaStream_t st)
+                              WsHeader *hdr, uint32_t *list, cudaStream_t st)
 {
-    if (cap <= kSortThreads * 12) return launch_sort<12>(off, entries, alt, n_tiles, cap, hdr, st);
-    return launch_sort<24>(off, entries, alt, n_tiles, cap, hdr, st);
+    if (cap <= kSortThreads * 12) return launch_sort<12>(off, entries, alt, n_tiles, cap, hdr, list, st);
+    return launch_sort<24>(off, entries, alt, n_tiles, cap, hdr, list, st);
 }
 
 }  // namespace sgad

@@ -12,7 +12,7 @@ namespace sgad {
 void launch_project_count(const Scene &, World *, uint32_t *, cudaStream_t);
 void launch_scan_tiles(uint32_t *, uint32_t *, int, uint64_t, WsHeader *, uint32_t *, cudaStream_t);
 void launch_emit(const Scene &, const World *, const uint32_t *, uint32_t *, uint64_t *, WsHeader *, cudaStream_t);
-cudaError_t launch_sort_tiles(const uint32_t *, uint64_t *, uint64_t *, int, int, const WsHeader *, cudaStream_t);
+cudaError_t launch_sort_tiles(const uint32_t *, uint64_t *, uint64_t *, int, int, WsHeader *, uint32_t *, cudaStream_t);
 cudaError_t launch_composite(bool, int, int, int, const Scene &, const World *, const uint32_t *, const uint64_t *,
                              float *, uint32_t *, float4 *, WsHeader *, const uint32_t *, uint32_t *, uint32_t *,
                              cudaStream_t);
@@ -170,6 +170,7 @@ struct Ws {
     uint32_t *tile_off() const { return reinterpret_cast<uint32_t *>(base + L.tile_off); }
     uint32_t *tile_cnt() const { return reinterpret_cast<uint32_t *>(base + L.tile_cnt); }
     uint32_t *tile_order() const { return reinterpret_cast<uint32_t *>(base + L.tile_order); }
+    uint32_t *sort_list() const { return reinterpret_cast<uint32_t *>(base + L.sort_list); }
     float *pix_t() const { return reinterpret_cast<float *>(base + L.pix_t); }
     uint32_t *pix_n() const { return reinterpret_cast<uint32_t *>(base + L.pix_n); }
     uint64_t *keys() const { return reinterpret_cast<uint64_t *>(base + L.keys); }
@@ -232,7 +233,8 @@ sgad_status run_forward_prep(sgad_ctx *ctx, const Scene &sc, const Ws &ws, int64
     mark(ctx, 1, st);
     launch_emit(sc, ws.world(), ws.tile_off(), ws.tile_cnt(), ws.keys(), ws.hdr(), st);
     mark(ctx, 2, st);
-    cudaError_t e = launch_sort_tiles(ws.tile_off(), ws.keys(), ws.keys_alt(), sc.n_tiles, ctx->sort_cap, ws.hdr(), st);
+    cudaError_t e = launch_sort_tiles(ws.tile_off(), ws.keys(), ws.keys_alt(), sc.n_tiles, ctx->sort_cap, ws.hdr(),
+                                      ws.sort_list(), st);
     if (e != cudaSuccess) return cuda_fail(e, "sort launch");
     mark(ctx, 3, st);
     return last_launch("binning / emission / sort");
@@ -463,6 +465,7 @@ sgad_status sgad_read_stats(sgad_ctx *ctx, void *workspace, size_t ws_bytes, sga
     out->keys_needed = h.needed;
     out->n_pairs = (int64_t)h.n_pairs;
     out->n_evals = (int64_t)h.n_evals;
+    out->n_sort_exact = h.n_sort_exact;
     return SGAD_OK;
 }
 

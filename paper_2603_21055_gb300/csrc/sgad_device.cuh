@@ -73,7 +73,8 @@ struct WsHeader {
     unsigned long long n_pairs;  // (pixel, entry) pairs composited by the last forward
     unsigned long long n_evals;  // (pixel, entry) pairs whose alpha the last forward evaluated
     uint32_t queue_bwd;          // persistent backward compositing: next tile-order position
-    uint32_t pad1[21];
+    uint32_t n_sort_exact;       // tiles the bucket sort handed to the exact radix sort
+    uint32_t pad1[20];
     int32_t sticky_err;          // first error since the last sgad_check()
     uint32_t sticky_needed;      // largest key count needed since the last sgad_check()
     uint32_t sticky_overrun;
@@ -310,7 +311,8 @@ __device__ __forceinline__ bool gauss_alpha(const Staged &s, float qx, float qy,
 // Workspace layout (byte offsets, 256-aligned sections). Shared by the host API and the
 // kernels' launch code.
 struct Layout {
-    size_t header, world, gacc, tile_off, tile_cnt, tile_order, pix_t, pix_n, keys, keys_alt, contrib, wmask, total;
+    size_t header, world, gacc, tile_off, tile_cnt, tile_order, sort_list, pix_t, pix_n, keys, keys_alt, contrib, wmask,
+        total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -325,6 +327,7 @@ inline Layout make_layout(uint64_t n_gauss, uint64_t n_tiles, uint64_t n_pix, ui
     L.tile_off = o; o = align256(o + (n_tiles + 1) * 4);
     L.tile_cnt = o; o = align256(o + (n_tiles + 1) * 4);
     L.tile_order = o; o = align256(o + n_tiles * 4);
+    L.sort_list = o; o = align256(o + n_tiles * 4);
     L.pix_t = o; o = align256(o + n_pix * 4);
     L.pix_n = o; o = align256(o + n_pix * 4);
     L.keys = o; o = align256(o + key_cap * 8);

@@ -291,7 +291,8 @@ class Splatter:
 
     def stats(self) -> dict:
         s = B.sgad_read_stats(self.ctx, self.ws_ptr, self.ws_bytes, self.stream())
-        return dict(n_keys=s.n_keys, keys_needed=s.keys_needed, n_pairs=s.n_pairs, n_evals=s.n_evals)
+        return dict(n_keys=s.n_keys, keys_needed=s.keys_needed, n_pairs=s.n_pairs, n_evals=s.n_evals,
+                    n_sort_exact=s.n_sort_exact)
 
     def profile(self, enable: bool = True) -> None:
         B.sgad_profile_enable(self.ctx, enable)

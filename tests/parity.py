@@ -27,7 +27,8 @@ def gpu_run(scene, grads_in=None, tile=(16, 16), sort_smem_cap=0, freeze_offset=
     status, nk, need = sp.check()
     assert status == 0, (status, nk, need)
     offs, entries, t_final, n_contrib = sp.state(kfs, scene.views)
-    res = dict(images=[{k: v.cpu().numpy() for k, v in im.items()} for im in images],
+    stats = sp.stats()
+    res = dict(images=[{k: v.cpu().numpy() for k, v in im.items()} for im in images], n_sort_exact=stats["n_sort_exact"],
                offsets=offs.cpu().numpy().astype(np.int64) & 0xffffffff,
                entries=entries.cpu().numpy().view(np.uint64), t_final=t_final.cpu().numpy(),
                n_contrib=n_contrib.cpu().numpy(), n_keys=nk, planned=n_keys)

@@ -100,7 +100,7 @@ def _cam(w=64, h=48):
 
 
 def test_workspace_size_arithmetic():
-    """Workspace = header + 64 B per Gaussian + tile offsets/counters/order + 8 B per view
+    """Workspace = header + 64 B per Gaussian + tile offsets/counters/order/sort list + 8 B per view
     pixel + 16 B per key of key arrays + 32 B per key (+ 1 KB per tile) of contribution
     words + one word per 4 keys (+ 16 per tile and 8) of per-warp contribution masks, each
     section rounded to 256 B."""

@@ -52,6 +52,7 @@ def test_config1_backward(scene1):
 def test_crop_forward_backward(crop):
     ref, g = _grads_for(crop)
     res = gpu_run(crop, grads_in=g)
+    assert res["n_sort_exact"] == 0           # every tile through the one-pass bucket sort
     n_aside = compare_keys(res, crop)
     worst, n_near = compare_images(res, ref)
     og = oracle.backward(crop, [{k: v.astype(np.float64) for k, v in x.items()} for x in g])
@@ -272,3 +273,5 @@ def test_equal_depth_runs(scene1, quantum):
     assert runs > (32 if quantum != 0.001 else 1)                      # the case it is meant to exercise
     compare_keys(res, sc)
     compare_images(res, ref)
+    if quantum == 0.0:
+        assert res["n_sort_exact"] > 0        # buckets of equal depths: the exact radix sort
