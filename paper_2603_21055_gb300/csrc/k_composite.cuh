@@ -4,17 +4,15 @@
 // entries staged per block-wide barrier (B).
 //
 // Forward: 256 threads per tile, one pixel per thread; each warp owns an 8x4 block of
-// pixels, split into four 4x2 groups of eight lanes. The tile's sorted list is consumed
-// in batches of B entries: the threads stage them (gathering each Gaussian's 32-byte
-// world record and projecting it into the view) into shared memory, then every warp
-// tests 32 staged Gaussians at a time against each group's pixel block (one lane per
-// Gaussian, a ballot per group) and each group walks only the ones whose alpha >= 1/255
-// box reaches its block, the four groups side by side in the same instructions. Small
-// groups cut the (pixel, entry) pairs a walk evaluates for nothing: an entry whose box
-// touches the warp's block usually misses most of its pixels. A group stops when its
-// pixels are done, a warp when its groups are, the block when all warps are. For every
-// 32-entry chunk it walked, a warp also writes the OR of its lanes' contribution bits:
-// which entries reached a pixel of its block.
+// pixels. The tile's sorted list is consumed in batches of B entries: the threads stage
+// them (gathering each Gaussian's 32-byte world record and projecting it into the view)
+// into shared memory; then every warp takes 32 staged Gaussians at a time: lane j forms
+// the mask of the block's pixels inside Gaussian j's alpha >= 1/255 box, a 32 x 32 bit
+// transpose gives each lane the Gaussians whose box covers its pixel, and each lane
+// walks only those, in order, until its pixel is done. A warp stops when its pixels are
+// done, the block when all warps are. For every 32-entry chunk it walked, a warp also
+// writes the OR of its lanes' contribution bits: which entries reached a pixel of its
+// block.
 //
 // Backward: 256 threads per tile, each warp an 8x4 pixel block and each lane one pixel
 // (two pixels per lane on 8x8 blocks is a build option). The same lists are walked from
@@ -138,6 +136,36 @@ __device__ __forceinline__ void stage_entry(const Scene &sc, const CompositeArgs
     }
 }
 
+__device__ __forceinline__ uint32_t lane_mask_lt(int lane) { return (1u << lane) - 1u; }
+
+// 32 x 32 bit transpose across the warp: lane j holds row j on entry; on return lane i
+// holds column i (bit j = bit i of row j). Swaps the off-diagonal blocks of halving size.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
+{
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000ffffu : (s == 8 ? 0x00ff00ffu : (s == 4 ? 0x0f0f0f0fu :
+                           (s == 2 ? 0x33333333u : 0x55555555u)));
+        const uint32_t y = __shfl_xor_sync(kFull, x, s);
+        x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
+    }
+    return x;
+}
+
+// Pixels (bit p: pixel (bx + p % 8, by + p / 8)) of an 8x4 block inside the box
+// |px - x| <= hx, |py - y| <= hy of a staged entry; hx < 0 marks an empty box.
+__device__ __forceinline__ uint32_t box_block_mask(const float4 a, float bxf, float byf)
+{
+    if (!(a.z >= 0.0f)) return 0u;
+    const float x0 = fmaxf(ceilf(a.x - a.z) - bxf, 0.0f), x1 = fminf(floorf(a.x + a.z) - bxf, 7.0f);
+    const float y0 = fmaxf(ceilf(a.y - a.w) - byf, 0.0f), y1 = fminf(floorf(a.y + a.w) - byf, 3.0f);
+    if (!(x0 <= x1) || !(y0 <= y1)) return 0u;
+    const int xl = (int)x0, xh = (int)x1, yl = (int)y0, yh = (int)y1;
+    const uint32_t cols = (0xffu >> (7 - (xh - xl))) << xl;
+    const uint32_t rows = (0xffffffffu >> (8 * (3 - (yh - yl)))) << (8 * yl);
+    return (cols * 0x01010101u) & rows;
+}
+
 // ------------------------------------------------------------------ forward
 
 // Double-buffered staging (one block barrier per batch instead of two) measured slower
@@ -176,69 +204,55 @@ struct FwdPixel {
     bool done;
 };
 
-// Box of a staged entry against the pixel rectangle [x0, x0 + w - 1] x [y0, y0 + h - 1]
-// (pixel centres); a negative half extent never overlaps.
-__device__ __forceinline__ bool box_overlaps(const float4 box, float x0, float y0, float w1, float h1)
-{
-    return box.z >= 0.0f && box.x + box.z >= x0 && box.x - box.z <= x0 + w1 && box.y + box.w >= y0 &&
-           box.y - box.w <= y0 + h1;
-}
-
 // Forward pixel of thread (warp, lane) in a TW-wide tile at pixel (ox, oy): the warp's
-// 8x4 block, group q = lane / 8 its 4x2 sub-block (4 (q & 1), 2 (q >> 1)).
+// 8x4 block, row-major (lane % 8, lane / 8).
 template <int TW>
 __device__ __forceinline__ int2 fwd_pixel(int ox, int oy, int warp, int lane)
 {
-    const int q = lane >> 3;
-    return make_int2(ox + (warp % (TW / 8)) * 8 + 4 * (q & 1) + (lane & 3),
-                     oy + (warp / (TW / 8)) * 4 + 2 * (q >> 1) + ((lane >> 2) & 1));
+    return make_int2(ox + (warp % (TW / 8)) * 8 + (lane & 7), oy + (warp / (TW / 8)) * 4 + (lane >> 3));
 }
 
 // The warp walks nb staged entries (list positions b0 - s ...) against its pixel block
-// (origin bx, by): 32 entries at a time, one ballot per 4x2 group of the entries whose
-// alpha box reaches the group's block (groups whose pixels are all done take none), then
-// each group walks its entries in order for every pixel not yet done.
+// (origin bx, by), 32 at a time: lane j forms entry j's box mask over the block's pixels
+// (the pixels inside its alpha >= 1/255 box), a bit transpose gives every lane the
+// entries whose box covers its pixel, and each lane not yet done walks its own entries
+// in order. Lanes are busy only with (pixel, entry) pairs inside the entry's box.
 __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0, uint32_t s, int tile,
-                                           const CompositeArgs &a, float bx, float by, float qx, float qy, int lane,
+                                           const CompositeArgs &a, float bxf, float byf, float qx, float qy, int lane,
                                            FwdPixel &px, bool &warp_done, uint32_t &n_pairs, uint32_t &n_evals,
                                            uint32_t *wmw)
 {
-    const int q = lane >> 3;
     for (int c0 = 0; c0 < nb; c0 += 32) {
         const int j = c0 + lane;
-        const float4 box = j < nb ? sm[j].a : make_float4(0.f, 0.f, -1.f, -1.f);
-        const uint32_t done = __ballot_sync(kFull, px.done);
-        uint32_t m[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const bool live = ((done >> (8 * r)) & 0xffu) != 0xffu;
-            m[r] = __ballot_sync(kFull, live && box_overlaps(box, bx + 4 * (r & 1), by + 2 * (r >> 1), 3.0f, 1.0f));
-        }
-        uint32_t mask = q == 0 ? m[0] : (q == 1 ? m[1] : (q == 2 ? m[2] : m[3]));
+        uint32_t mine = warp_transpose32(j < nb ? box_block_mask(sm[j].a, bxf, byf) : 0u, lane);
+        if (px.done) mine = 0u;
         uint32_t bits = 0;
-        while (mask) {
-            const int jj = c0 + __ffs(mask) - 1;
-            mask &= mask - 1;
-            if (px.done) continue;
-            const Staged st = sm[jj];
-            float dx, dy, ep, alpha;
-            ++n_evals;
-            if (!gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) continue;
-            const float test = __fmul_rn(px.T, __fsub_rn(1.0f, alpha));
-            if (test < kTStop) {
-                px.done = true;
-                continue;
+        while (__any_sync(kFull, mine != 0u)) {
+            if (mine) {
+                const int jj = __ffs(mine) - 1;
+                mine &= mine - 1u;
+                const Staged st = sm[c0 + jj];
+                float dx, dy, ep, alpha;
+                ++n_evals;
+                if (gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) {
+                    const float test = __fmul_rn(px.T, __fsub_rn(1.0f, alpha));
+                    if (test < kTStop) {
+                        px.done = true;
+                        mine = 0u;
+                    } else {
+                        ++n_pairs;
+                        bits |= 1u << jj;
+                        const float w = __fmul_rn(alpha, px.T);
+                        px.cr = __fmaf_rn(w, st.c.x, px.cr);
+                        px.cg = __fmaf_rn(w, st.c.y, px.cg);
+                        px.cb = __fmaf_rn(w, st.c.z, px.cb);
+                        px.dd = __fmaf_rn(w, st.c.w, px.dd);
+                        px.aa = __fadd_rn(px.aa, w);
+                        px.T = test;
+                        px.last = (int)(b0 + c0 + jj - s);
+                    }
+                }
             }
-            ++n_pairs;
-            bits |= 1u << (jj - c0);
-            const float w = __fmul_rn(alpha, px.T);
-            px.cr = __fmaf_rn(w, st.c.x, px.cr);
-            px.cg = __fmaf_rn(w, st.c.y, px.cg);
-            px.cb = __fmaf_rn(w, st.c.z, px.cb);
-            px.dd = __fmaf_rn(w, st.c.w, px.dd);
-            px.aa = __fadd_rn(px.aa, w);
-            px.T = test;
-            px.last = (int)(b0 + jj - s);
         }
         if (a.contrib) a.contrib[contrib_base(a, tile, s) + (size_t)((b0 - s + c0) >> 5) * 256 + threadIdx.x] = bits;
         if (wmw) {
@@ -913,36 +927,6 @@ struct LocalWarpSmem {
     int32_t pos[32];                // list position of entry j (descending in j)
 };
 constexpr size_t kLocalSmemBytes = (kLocalThreads / 32) * sizeof(LocalWarpSmem);
-
-__device__ __forceinline__ uint32_t lane_mask_lt(int lane) { return (1u << lane) - 1u; }
-
-// 32 x 32 bit transpose across the warp: lane j holds row j on entry; on return lane i
-// holds column i (bit j = bit i of row j). Swaps the off-diagonal blocks of halving size.
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
-{
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const uint32_t m = s == 16 ? 0x0000ffffu : (s == 8 ? 0x00ff00ffu : (s == 4 ? 0x0f0f0f0fu :
-                           (s == 2 ? 0x33333333u : 0x55555555u)));
-        const uint32_t y = __shfl_xor_sync(kFull, x, s);
-        x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
-    }
-    return x;
-}
-
-// Pixels (bit p: pixel (bx + p % 8, by + p / 8)) of an 8x4 block inside the box
-// |px - x| <= hx, |py - y| <= hy of a staged entry; hx < 0 marks an empty box.
-__device__ __forceinline__ uint32_t box_block_mask(const float4 a, float bxf, float byf)
-{
-    if (!(a.z >= 0.0f)) return 0u;
-    const float x0 = fmaxf(ceilf(a.x - a.z) - bxf, 0.0f), x1 = fminf(floorf(a.x + a.z) - bxf, 7.0f);
-    const float y0 = fmaxf(ceilf(a.y - a.w) - byf, 0.0f), y1 = fminf(floorf(a.y + a.w) - byf, 3.0f);
-    if (!(x0 <= x1) || !(y0 <= y1)) return 0u;
-    const int xl = (int)x0, xh = (int)x1, yl = (int)y0, yh = (int)y1;
-    const uint32_t cols = (0xffu >> (7 - (xh - xl))) << xl;
-    const uint32_t rows = (0xffffffffu >> (8 * (3 - (yh - yl)))) << (8 * yl);
-    return (cols * 0x01010101u) & rows;
-}
 
 // Moments of the entries [j0, j1) of a round (lane j holds entry j: the pixels it
 // contributed to, cm, its Gaussian g and world record w0; its pair slots start at
