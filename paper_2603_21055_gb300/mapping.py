@@ -98,6 +98,17 @@ class Mapper:
         if self.n_adam:
             B.sgad_adam_step_multi(self.adam, 0.9, 0.999, 1e-15, self.step_counter.data_ptr(), sp.stream())
 
+    def eval_loss(self):
+        """Render every view and put the mapping loss of Eq. 1 (the scene's weights) into
+        self.loss, on the device: no gradient step, no host synchronisation."""
+        sp = self.sp
+        sp.forward(self.kfs, self.views, self.images)
+        self.loss.zero_()
+        sp.l1_loss_grad(self.views, self.images, self.trgb, self.tdep, self.scene.rgb_weight,
+                        self.scene.depth_weight, self.d_rgb, self.d_dep, self.loss, self.valid)
+        if self.scene.ssim_weight != 0:
+            sp.ssim_loss_grad(self.views, self.images, self.trgb, self.scene.ssim_weight, self.d_rgb, self.loss)
+
     def capture(self):
         """Record one iteration as a CUDA graph (after one eager warm-up on a side stream)."""
         s = torch.cuda.Stream()
