@@ -75,7 +75,13 @@ typedef struct {
 /* One keyframe's Gaussians, one per pixel (Sec. 3.1, 3.2). All planes [H][W] device
  * FP32 (rgb [3][H][W]); cam.pose is cam->world. learnable = 0 marks a fixed neighbour
  * keyframe (Sec. 3.2: only the current frame's Gaussians are optimised): it is rendered
- * but receives no gradient. */
+ * but receives no gradient.
+ * world_transform (optional, device, 12 floats row-major 3x4 [R | t]): when not NULL,
+ * every centre mu of this keyframe is rendered at R mu + t, read from device memory by
+ * the projection kernels at launch time (so a transform a kernel updates takes effect
+ * without the host; rendering-based camera initialisation moves fixed Gaussians by
+ * W0^-1 E W0 instead of moving the view W0 by E). Only for fixed keyframes
+ * (learnable = 0; SGAD_ERR_INVALID_ARG otherwise). */
 typedef struct {
     const float *depth;          /* D: observed z-depth */
     const float *offset;         /* delta: learnable depth offset */
@@ -84,6 +90,7 @@ typedef struct {
     const float *scale;          /* s: isotropic standard deviation in metres */
     sgad_camera cam;
     int32_t learnable;
+    const float *world_transform;
 } sgad_keyframe;
 
 /* Rendered images of one view (device, caller-owned, fully overwritten). */
@@ -326,11 +333,14 @@ sgad_status sgad_profile_read(sgad_ctx *ctx, float *ms /* [SGAD_NUM_STAGES] */);
  * device float, zeroed by the caller; may be NULL). target_depth and d_depth may be NULL
  * when depth_weight == 0. valid_count is caller-owned device scratch of n_views uint32
  * (the valid-depth pixel count U_k per view; overwritten), required when depth_weight
- * != 0. */
+ * != 0. min_alpha: pixels whose rendered alpha (rendered[k].alpha) is at most min_alpha
+ * add no loss and get zero gradients (the silhouette mask of rendering-based tracking,
+ * Sec. 3.3 "Initialization"; the means keep their denominators); a negative value keeps
+ * every pixel and does not read the alpha images. */
 sgad_status sgad_l1_loss_grad(int32_t n_views, const sgad_camera *views,
                               const sgad_images *rendered, const float *const *target_rgb,
                               const float *const *target_depth, float rgb_weight,
-                              float depth_weight, float *const *d_rgb, float *const *d_depth,
+                              float depth_weight, float min_alpha, float *const *d_rgb, float *const *d_depth,
                               float *loss_accum, uint32_t *valid_count, void *stream);
 
 /* SSIM term of the mapping loss Eq. 1 (tau L_S, L_S the SSIM loss between the observed
@@ -398,6 +408,25 @@ typedef struct {
  * it, so the call can be captured once in a CUDA graph and replayed. */
 sgad_status sgad_adam_step_multi(int32_t n_tensors, const sgad_adam_tensor *tensors, float beta1,
                                  float beta2, float eps, int32_t *step_counter, void *stream);
+
+/* One step of the rendering-based camera initialisation of tracking (Sec. 3.3,
+ * "Initialization") on the device, with no host round trip. The view stays at its
+ * world->cam pose W0 (view_pose, host, row-major 3x4) and the fixed Gaussians move by
+ * M = W0^-1 E W0, where E is the camera correction accumulated so far: rendering
+ * M mu into W0 equals rendering mu into E W0. state (device, SGAD_POSE_STATE_FLOATS
+ * floats, caller-owned; set E and M to the identity [I | 0] and the rest to zero before
+ * the first step) holds E (state[0..11]), M (state[12..23], the keyframes'
+ * world_transform), the Adam moments m (24..29) and v (30..35), the step count (36) and
+ * the current pose E W0 (37..48). From d_pose (device, 12 floats: d loss / d W0 of the
+ * last sgad_backward), the gradient of a left twist xi = (omega, v) of the pose is
+ * d/d v = the translation column c of d_pose and d/d omega = vee(R0 G^T - G R0^T) +
+ * t0 x c (G its rotation block); Adam (beta1, beta2, eps, bias-corrected) with step
+ * lr_rot on omega and lr_trans on v gives xi, and E <- exp(xi) E (rotation by Rodrigues'
+ * formula, translation v). Evaluated in FP64 by one thread. */
+#define SGAD_POSE_STATE_FLOATS 64
+sgad_status sgad_pose_adam_step(const float *d_pose, const float *view_pose, float *state,
+                                float lr_rot, float lr_trans, float beta1, float beta2, float eps,
+                                void *stream);
 
 /* Forward splatting that allocates nothing, for callers that cannot allocate device
  * memory (code running in a host callback or a real-time loop where cudaMalloc would

@@ -24,7 +24,7 @@ SGAD_MAX_VIEWS = 64
 
 EXPORTS = ["sgad_default_options", "sgad_create", "sgad_destroy", "sgad_last_error", "sgad_workspace_size",
            "sgad_count_keys", "sgad_forward", "sgad_backward", "sgad_check", "sgad_state", "sgad_read_stats",
-           "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_adam_step",
+           "sgad_profile_enable", "sgad_profile_read", "sgad_l1_loss_grad", "sgad_pose_adam_step", "sgad_adam_step",
            "sgad_adam_step_multi", "sgad_forward_noalloc", "sgad_autotune", "sgad_get_options",
            "sgad_ssim_workspace_size", "sgad_ssim_loss_grad", "sgad_fma_burn",
            # include/sgad_gicp.h
@@ -52,7 +52,7 @@ class sgad_camera(C.Structure):
 class sgad_keyframe(C.Structure):
     _fields_ = [("depth", C.c_void_p), ("offset", C.c_void_p), ("rgb", C.c_void_p),
                 ("opacity_logit", C.c_void_p), ("scale", C.c_void_p), ("cam", sgad_camera),
-                ("learnable", C.c_int32)]
+                ("learnable", C.c_int32), ("world_transform", C.c_void_p)]
 
 
 class sgad_images(C.Structure):
@@ -179,7 +179,8 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         "sgad_read_stats": (st, [P, P, C.c_size_t, P, P]),
         "sgad_profile_enable": (st, [P, I32]),
         "sgad_profile_read": (st, [P, P]),
-        "sgad_l1_loss_grad": (st, [I32, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P]),
+        "sgad_l1_loss_grad": (st, [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, P, P, P, P, P]),
+        "sgad_pose_adam_step": (st, [P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P]),
         "sgad_adam_step": (st, [I64, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I32, I32, P]),
         "sgad_adam_step_multi": (st, [I32, P, C.c_float, C.c_float, C.c_float, P, P]),
         "sgad_forward_noalloc": (st, [P, P, I32, P, I32, P, P]),
@@ -298,9 +299,20 @@ def sgad_profile_read(ctx):
 
 
 def sgad_l1_loss_grad(views, rendered, target_rgb, target_depth, rgb_weight, depth_weight, d_rgb, d_depth,
-                      loss_accum: int, valid_count: int, stream: int) -> None:
+                      loss_accum: int, valid_count: int, stream: int, min_alpha: float = -1.0) -> None:
     _call("sgad_l1_loss_grad", len(views), views, rendered, target_rgb, target_depth, float(rgb_weight),
-          float(depth_weight), d_rgb, d_depth, loss_accum, valid_count, stream)
+          float(depth_weight), float(min_alpha), d_rgb, d_depth, loss_accum, valid_count, stream)
+
+
+SGAD_POSE_STATE_FLOATS = 64
+
+
+def sgad_pose_adam_step(d_pose: int, view_pose, state: int, lr_rot: float, lr_trans: float, beta1: float = 0.9,
+                        beta2: float = 0.999, eps: float = 1e-12, stream: int = 0) -> None:
+    """view_pose: 12 host floats (row-major 3x4 world->cam); d_pose, state: device pointers."""
+    w0 = (C.c_float * 12)(*[float(x) for x in view_pose])
+    _call("sgad_pose_adam_step", d_pose, w0, state, float(lr_rot), float(lr_trans), float(beta1), float(beta2),
+          float(eps), stream)
 
 
 def sgad_ssim_workspace_size(views) -> int:

@@ -42,6 +42,13 @@ __global__ void __launch_bounds__(256) k_project_count(const __grid_constant__ S
         w0.x = __fmaf_rn(k.R[0], qx, __fmaf_rn(k.R[1], qy, __fmaf_rn(k.R[2], d, k.t[0])));
         w0.y = __fmaf_rn(k.R[3], qx, __fmaf_rn(k.R[4], qy, __fmaf_rn(k.R[5], d, k.t[1])));
         w0.z = __fmaf_rn(k.R[6], qx, __fmaf_rn(k.R[7], qy, __fmaf_rn(k.R[8], d, k.t[2])));
+        if (k.xform) {          // device transform of the centres: mu <- R mu + t
+            const float *X = k.xform;
+            const float mx = w0.x, my = w0.y, mz = w0.z;
+            w0.x = __fmaf_rn(X[0], mx, __fmaf_rn(X[1], my, __fmaf_rn(X[2], mz, X[3])));
+            w0.y = __fmaf_rn(X[4], mx, __fmaf_rn(X[5], my, __fmaf_rn(X[6], mz, X[7])));
+            w0.z = __fmaf_rn(X[8], mx, __fmaf_rn(X[9], my, __fmaf_rn(X[10], mz, X[11])));
+        }
         w0.w = k.scale[j];
         const float o = 1.0f / (1.0f + expf(-k.logit[j]));
         World w;
@@ -191,6 +198,7 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Scene sc, 
         const KfDev &k = sc.kf[find_kf(sc, g)];
         const uint32_t j = g - k.gbase;
         m = df_world_point(k, (int)(j % (uint32_t)k.W), (int)(j / (uint32_t)k.W), k.depth[j], k.offset[j]);
+        if (k.xform) m = df_transform(m, k.xform);
     }
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;

@@ -60,7 +60,7 @@ __device__ __forceinline__ float block_sum(float x, float *red)
 constexpr int kLossChunk = 4096;    // pixels per CTA
 
 struct LossView {
-    const float *rgb, *depth, *trgb, *tdep;
+    const float *rgb, *depth, *alpha, *trgb, *tdep;   // alpha: null unless masking
     float *drgb, *ddep;
     uint32_t *nvalid;
     uint32_t hw;
@@ -69,7 +69,7 @@ struct LossView {
 
 struct LossBatch {
     int32_t n;
-    float wrgb, wdep;
+    float wrgb, wdep, min_alpha;
     LossView v[SGAD_MAX_VIEWS];
 };
 
@@ -105,15 +105,16 @@ __global__ void __launch_bounds__(256) k_l1_grad(const __grid_constant__ LossBat
     const float inv_dep = nv > 0 ? B.wdep / (float)nv : 0.0f;
     float l = 0.f;
     for (size_t i = base + threadIdx.x; i < end; i += blockDim.x) {
+        const bool keep = !v.alpha || v.alpha[i] > B.min_alpha;     // silhouette mask
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float d = v.rgb[c * hw + i] - v.trgb[c * hw + i];
-            l += fabsf(d) * inv_rgb;
-            v.drgb[c * hw + i] = sgnf(d) * inv_rgb;
+            if (keep) l += fabsf(d) * inv_rgb;
+            v.drgb[c * hw + i] = keep ? sgnf(d) * inv_rgb : 0.0f;
         }
         if (v.ddep) {
             float gd = 0.f;
-            if (v.tdep && v.tdep[i] > 0.0f && inv_dep > 0.0f) {
+            if (keep && v.tdep && v.tdep[i] > 0.0f && inv_dep > 0.0f) {
                 const float d = v.depth[i] - v.tdep[i];
                 l += fabsf(d) * inv_dep;
                 gd = sgnf(d) * inv_dep;
@@ -129,20 +130,23 @@ __global__ void __launch_bounds__(256) k_l1_grad(const __grid_constant__ LossBat
 
 // views: per view (rgb, depth, target rgb, target depth or NULL, d_rgb, d_depth or NULL,
 // valid counter or NULL, pixel count).
-void launch_l1_batch(int n, const float *const *rgb, const float *const *depth, const float *const *trgb,
-                     const float *const *tdep, float *const *drgb, float *const *ddep, uint32_t *nvalid,
-                     const uint32_t *hw, float wrgb, float wdep, float *loss, cudaStream_t st)
+void launch_l1_batch(int n, const float *const *rgb, const float *const *depth, const float *const *alpha,
+                     const float *const *trgb, const float *const *tdep, float *const *drgb, float *const *ddep,
+                     uint32_t *nvalid, const uint32_t *hw, float wrgb, float wdep, float min_alpha, float *loss,
+                     cudaStream_t st)
 {
     LossBatch B;
     B.n = n;
     B.wrgb = wrgb;
     B.wdep = wdep;
+    B.min_alpha = min_alpha;
     uint32_t blocks = 0;
     const bool use_depth = wdep != 0.0f && tdep && ddep && nvalid;
     for (int i = 0; i < n; ++i) {
         LossView &v = B.v[i];
         v.rgb = rgb[i];
         v.depth = depth ? depth[i] : nullptr;
+        v.alpha = alpha ? alpha[i] : nullptr;
         v.trgb = trgb[i];
         v.tdep = use_depth ? tdep[i] : nullptr;
         v.drgb = drgb[i];
@@ -258,6 +262,114 @@ void launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float 
         k_adam<true><<<(unsigned)blocks, 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2);
     else
         k_adam<false><<<(unsigned)blocks, 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2);
+}
+
+// ------------------------------------------------- rendering-based camera initialisation
+//
+// State layout (device floats): E [0, 12), M = W0^-1 E W0 [12, 24), Adam m [24, 30) and
+// v [30, 36), step count [36], current pose E W0 [37, 49). 3x4 row-major [R | t].
+struct PoseArgs {
+    double W0[12];
+    double lr[6];
+    double b1, b2, eps;
+};
+
+__device__ void mat34_mul(const double *A, const double *B, double *C)     // C = A B (as 4x4)
+{
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 4; ++c) {
+            double s = c == 3 ? A[4 * r + 3] : 0.0;
+            for (int k = 0; k < 3; ++k) s += A[4 * r + k] * B[4 * k + c];
+            C[4 * r + c] = s;
+        }
+    }
+}
+
+__global__ void k_pose_adam_step(const float *__restrict__ d_pose, float *__restrict__ st, const PoseArgs a)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double *W = a.W0;
+    double G[9], c[3];
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) G[3 * r + k] = d_pose[4 * r + k];
+        c[r] = d_pose[4 * r + 3];
+    }
+    // M = R0 G^T; d/d omega = vee(M - M^T) + t0 x c; d/d v = c
+    double Mx[9];
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) {
+            double s = 0.0;
+            for (int q = 0; q < 3; ++q) s += W[4 * r + q] * G[3 * k + q];
+            Mx[3 * r + k] = s;
+        }
+    const double t0[3] = {W[3], W[7], W[11]};
+    double g[6];
+    g[0] = Mx[5] - Mx[7] + (t0[1] * c[2] - t0[2] * c[1]);
+    g[1] = Mx[6] - Mx[2] + (t0[2] * c[0] - t0[0] * c[2]);
+    g[2] = Mx[1] - Mx[3] + (t0[0] * c[1] - t0[1] * c[0]);
+    g[3] = c[0];
+    g[4] = c[1];
+    g[5] = c[2];
+    const double n = (double)st[36] + 1.0;
+    st[36] = (float)n;
+    double xi[6];
+    for (int i = 0; i < 6; ++i) {
+        const double m = a.b1 * (double)st[24 + i] + (1.0 - a.b1) * g[i];
+        const double v = a.b2 * (double)st[30 + i] + (1.0 - a.b2) * g[i] * g[i];
+        st[24 + i] = (float)m;
+        st[30 + i] = (float)v;
+        const double mh = m / (1.0 - pow(a.b1, n)), vh = v / (1.0 - pow(a.b2, n));
+        xi[i] = -a.lr[i] * mh / (sqrt(vh) + a.eps);
+    }
+    // exp(xi) = [Rodrigues(omega) | v]
+    const double th = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+    const double K[9] = {0.0, -xi[2], xi[1], xi[2], 0.0, -xi[0], -xi[1], xi[0], 0.0};
+    double K2[9];
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) {
+            double s = 0.0;
+            for (int q = 0; q < 3; ++q) s += K[3 * r + q] * K[3 * q + k];
+            K2[3 * r + k] = s;
+        }
+    const double sa = th < 1e-12 ? 1.0 : sin(th) / th;
+    const double sb = th < 1e-12 ? 0.0 : (1.0 - cos(th)) / (th * th);
+    double X[12];
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) X[4 * r + k] = (r == k ? 1.0 : 0.0) + sa * K[3 * r + k] + sb * K2[3 * r + k];
+        X[4 * r + 3] = xi[3 + r];
+    }
+    double E[12], En[12];
+    for (int i = 0; i < 12; ++i) E[i] = st[i];
+    mat34_mul(X, E, En);
+    // M = W0^-1 E W0 with W0^-1 = [R0^T | -R0^T t0]; pose = E W0
+    double Wi[12], EW[12], Mn[12];
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) Wi[4 * r + k] = W[4 * k + r];
+        Wi[4 * r + 3] = -(W[r] * t0[0] + W[4 + r] * t0[1] + W[8 + r] * t0[2]);
+    }
+    mat34_mul(En, W, EW);
+    mat34_mul(Wi, EW, Mn);
+    for (int i = 0; i < 12; ++i) {
+        st[i] = (float)En[i];
+        st[12 + i] = (float)Mn[i];
+        st[37 + i] = (float)EW[i];
+    }
+}
+
+cudaError_t launch_pose_adam_step(const float *d_pose, const float *W0, float *state, float lr_rot, float lr_trans,
+                                  float b1, float b2, float eps, cudaStream_t st)
+{
+    PoseArgs a;
+    for (int i = 0; i < 12; ++i) a.W0[i] = W0[i];
+    for (int i = 0; i < 3; ++i) {
+        a.lr[i] = lr_rot;
+        a.lr[3 + i] = lr_trans;
+    }
+    a.b1 = b1;
+    a.b2 = b2;
+    a.eps = eps;
+    k_pose_adam_step<<<1, 32, 0, st>>>(d_pose, state, a);
+    return cudaGetLastError();
 }
 
 }  // namespace sgad

@@ -19,7 +19,10 @@ cudaError_t launch_composite(bool, int, int, int, const Scene &, const World *, 
 bool valid_batch(int, bool);
 void launch_finalize(const Scene &, const World *, const float4 *, cudaStream_t);
 void launch_l1_batch(int, const float *const *, const float *const *, const float *const *, const float *const *,
-                     float *const *, float *const *, uint32_t *, const uint32_t *, float, float, float *, cudaStream_t);
+                     const float *const *, float *const *, float *const *, uint32_t *, const uint32_t *, float, float,
+                     float, float *, cudaStream_t);
+cudaError_t launch_pose_adam_step(const float *, const float *, float *, float, float, float, float, float,
+                                  cudaStream_t);
 void launch_adam(int64_t, float *, const float *, float *, float *, float, float, float, float, float, float, bool,
                  cudaStream_t);
 cudaError_t launch_adam_multi(int, const sgad_adam_tensor *, float, float, float, int32_t *, cudaStream_t);
@@ -132,6 +135,9 @@ sgad_status build_scene(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n
         d.rgb = k.rgb;
         d.logit = k.opacity_logit;
         d.scale = k.scale;
+        d.xform = k.world_transform;
+        if (k.world_transform && k.learnable)
+            return fail(SGAD_ERR_INVALID_ARG, "keyframe %d: a world transform is only allowed on a fixed keyframe", i);
         set_cam(k.cam, d.fx, d.fy, d.cx, d.cy, d.R, d.t);
         d.W = k.cam.width;
         d.H = k.cam.height;
@@ -601,8 +607,8 @@ sgad_status sgad_state(const sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_
 
 sgad_status sgad_l1_loss_grad(int32_t n_views, const sgad_camera *views, const sgad_images *rendered,
                               const float *const *target_rgb, const float *const *target_depth, float rgb_weight,
-                              float depth_weight, float *const *d_rgb, float *const *d_depth, float *loss_accum,
-                              uint32_t *valid_count, void *stream)
+                              float depth_weight, float min_alpha, float *const *d_rgb, float *const *d_depth,
+                              float *loss_accum, uint32_t *valid_count, void *stream)
 {
     if (n_views < 1 || !views || !rendered || !target_rgb || !d_rgb)
         return fail(SGAD_ERR_INVALID_ARG, "bad arguments to sgad_l1_loss_grad");
@@ -613,23 +619,42 @@ sgad_status sgad_l1_loss_grad(int32_t n_views, const sgad_camera *views, const s
         return fail(SGAD_ERR_INVALID_ARG, "depth term needs target_depth, d_depth and valid_count");
     if (n_views > SGAD_MAX_VIEWS) return fail(SGAD_ERR_INVALID_ARG, "too many views");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const float *rgb[SGAD_MAX_VIEWS], *dep[SGAD_MAX_VIEWS];
+    if (!std::isfinite(min_alpha)) return fail(SGAD_ERR_INVALID_ARG, "min_alpha must be finite");
+    const bool mask = min_alpha >= 0.0f;
+    const float *rgb[SGAD_MAX_VIEWS], *dep[SGAD_MAX_VIEWS], *alp[SGAD_MAX_VIEWS];
     uint32_t hw[SGAD_MAX_VIEWS];
     for (int i = 0; i < n_views; ++i) {
         if (!valid_camera(views[i])) return fail(SGAD_ERR_INVALID_ARG, "view %d: invalid camera", i);
         if (!rendered[i].rgb || !target_rgb[i] || !d_rgb[i] || (use_depth && (!rendered[i].depth || !target_depth[i])))
             return fail(SGAD_ERR_INVALID_ARG, "view %d: NULL image", i);
+        if (mask && !rendered[i].alpha) return fail(SGAD_ERR_INVALID_ARG, "view %d: NULL alpha image", i);
         rgb[i] = rendered[i].rgb;
         dep[i] = rendered[i].depth;
+        alp[i] = rendered[i].alpha;
         hw[i] = (uint32_t)views[i].width * (uint32_t)views[i].height;
     }
     if (use_depth) {
         cudaError_t e = cudaMemsetAsync(valid_count, 0, sizeof(uint32_t) * (size_t)n_views, st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     }
-    launch_l1_batch(n_views, rgb, dep, target_rgb, use_depth ? target_depth : nullptr, d_rgb, d_depth,
-                    use_depth ? valid_count : nullptr, hw, rgb_weight, depth_weight, loss_accum, st);
+    launch_l1_batch(n_views, rgb, dep, mask ? alp : nullptr, target_rgb, use_depth ? target_depth : nullptr, d_rgb,
+                    d_depth, use_depth ? valid_count : nullptr, hw, rgb_weight, depth_weight, min_alpha, loss_accum,
+                    st);
     return last_launch("sgad_l1_loss_grad");
+}
+
+sgad_status sgad_pose_adam_step(const float *d_pose, const float *view_pose, float *state, float lr_rot,
+                                float lr_trans, float beta1, float beta2, float eps, void *stream)
+{
+    if (!d_pose || !view_pose || !state) return fail(SGAD_ERR_INVALID_ARG, "NULL argument to sgad_pose_adam_step");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f) ||
+        !std::isfinite(lr_rot) || !std::isfinite(lr_trans))
+        return fail(SGAD_ERR_INVALID_ARG, "bad hyper-parameters in sgad_pose_adam_step");
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(view_pose[i])) return fail(SGAD_ERR_INVALID_ARG, "view_pose must be finite");
+    const cudaError_t e = launch_pose_adam_step(d_pose, view_pose, state, lr_rot, lr_trans, beta1, beta2, eps,
+                                                static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SGAD_OK : cuda_fail(e, "sgad_pose_adam_step");
 }
 
 sgad_status sgad_adam_step(int64_t n, float *param, const float *grad, float *m, float *v, float lr, float beta1,

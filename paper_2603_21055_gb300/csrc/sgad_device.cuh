@@ -28,6 +28,7 @@ constexpr uint32_t kInvalidTile = 0xffffffffu;
 
 struct KfDev {
     const float *depth, *offset, *rgb, *logit, *scale;
+    const float *xform;          // optional world transform of the centres (device 3x4), or null
     float *d_offset, *d_rgb, *d_logit, *d_scale;
     float fx, fy, cx, cy;
     float R[9], t[3];            // cam -> world
@@ -252,6 +253,16 @@ __device__ __forceinline__ dvec3 df_world_point(const KfDev &k, int u, int v, fl
     m.y = df_add(df_add(df_add(df_mul_f(px, k.R[3]), df_mul_f(py, k.R[4])), df_mul_f(d, k.R[5])), {k.t[1], 0.0f});
     m.z = df_add(df_add(df_add(df_mul_f(px, k.R[6]), df_mul_f(py, k.R[7])), df_mul_f(d, k.R[8])), {k.t[2], 0.0f});
     return m;
+}
+
+// mu <- R mu + t with the keyframe's device transform (3x4 row-major), in double-float.
+__device__ __forceinline__ dvec3 df_transform(const dvec3 &m, const float *X)
+{
+    dvec3 r;
+    r.x = df_add(df_add(df_add(df_mul_f(m.x, X[0]), df_mul_f(m.y, X[1])), df_mul_f(m.z, X[2])), {X[3], 0.0f});
+    r.y = df_add(df_add(df_add(df_mul_f(m.x, X[4]), df_mul_f(m.y, X[5])), df_mul_f(m.z, X[6])), {X[7], 0.0f});
+    r.z = df_add(df_add(df_add(df_mul_f(m.x, X[8]), df_mul_f(m.y, X[9])), df_mul_f(m.z, X[10])), {X[11], 0.0f});
+    return r;
 }
 
 __device__ __forceinline__ float df_view_depth(const dvec3 &m, const ViewDev &v)

@@ -40,6 +40,7 @@ class DeviceKeyframe:
     logit: torch.Tensor              # (H, W)
     scale: torch.Tensor              # (H, W)
     learnable: bool = True
+    world_transform: Optional[torch.Tensor] = None   # (12,) device 3x4 applied to the centres (fixed keyframes)
 
     @property
     def n(self) -> int:
@@ -155,7 +156,8 @@ class Splatter:
     @staticmethod
     def _kf_key(kfs):
         return tuple((k.depth.data_ptr(), k.offset.data_ptr(), k.rgb.data_ptr(), k.logit.data_ptr(),
-                      k.scale.data_ptr(), id(k.cam), bool(k.learnable)) for k in kfs)
+                      k.scale.data_ptr(), id(k.cam), bool(k.learnable),
+                      k.world_transform.data_ptr() if k.world_transform is not None else 0) for k in kfs)
 
     def kf_structs(self, kfs: Sequence[DeviceKeyframe]):
         key = ("kf", self._kf_key(kfs))
@@ -164,7 +166,7 @@ class Splatter:
             arr = (B.sgad_keyframe * len(kfs))()
             for i, k in enumerate(kfs):
                 arr[i] = B.sgad_keyframe(_ptr(k.depth), _ptr(k.offset), _ptr(k.rgb), _ptr(k.logit), _ptr(k.scale),
-                                         _cam(k.cam), int(k.learnable))
+                                         _cam(k.cam), int(k.learnable), _ptr(k.world_transform))
             if len(self._cache) > 64:
                 self._cache.clear()
             self._cache[key] = (arr, list(kfs))        # keep the keyframes (and cameras) alive
@@ -320,7 +322,10 @@ class Splatter:
         return offs, entries, t_final, n_contrib
 
     def l1_loss_grad(self, views, images, target_rgb, target_depth, rgb_weight, depth_weight, d_rgb, d_depth,
-                     loss_accum: Optional[torch.Tensor] = None, valid_count: Optional[torch.Tensor] = None):
+                     loss_accum: Optional[torch.Tensor] = None, valid_count: Optional[torch.Tensor] = None,
+                     min_alpha: float = -1.0):
+        """Eq. 1's L1 terms and their image gradients; min_alpha >= 0 keeps only pixels whose
+        rendered alpha exceeds it (silhouette mask)."""
         va = self.view_structs(views)
         rend = (B.sgad_images * len(views))()
         for i, im in enumerate(images):
@@ -331,7 +336,8 @@ class Splatter:
         dd = B.ptr_array([_ptr(t) for t in d_depth]) if d_depth is not None else None
         B.sgad_l1_loss_grad(va, rend, tr, td, rgb_weight, depth_weight, dr, dd,
                             _ptr(loss_accum) if loss_accum is not None else None,
-                            valid_count.data_ptr() if valid_count is not None else None, self.stream())
+                            valid_count.data_ptr() if valid_count is not None else None, self.stream(),
+                            min_alpha=min_alpha)
 
     def ssim_loss_grad(self, views, images, target_rgb, weight, d_rgb, loss_accum: Optional[torch.Tensor] = None):
         """tau L_S of Eq. 1 for every view, ADDED to d_rgb (call after l1_loss_grad)."""

@@ -2,26 +2,29 @@
 
 The paper can start tracking a new frame by estimating its camera from the rendering
 error of the previous frame's Gaussians against the new RGB-D frame. `PoseRefiner`
-does that with the library: every iteration renders the fixed Gaussians into the
-current pose estimate (sgad_forward), takes the L1 colour + depth loss gradient
-(sgad_l1_loss_grad), and runs the adjoint with the view-pose output (sgad_backward,
-d_pose = d loss / d W for the world->cam 3x4 matrix W = [R | t]). The 12 numbers are
-projected onto a left twist (omega, v) of W (W <- exp(xi) W):
+does that with the library, all on the device with no host round trip per iteration:
+every iteration renders the fixed Gaussians into the view (sgad_forward), takes the
+silhouette-masked L1 colour + depth loss gradient (sgad_l1_loss_grad with min_alpha),
+runs the adjoint with the view-pose output (sgad_backward, d_pose = d loss / d W for the
+world->cam 3x4 matrix W = [R | t]) and updates the camera (sgad_pose_adam_step): the 12
+numbers are projected onto a left twist (omega, v) of the pose (W <- exp(xi) W),
 
     d L / d v     = sum_g d L / d t_g                   (the translation column of d L / d W)
     d L / d omega = sum_g t_g x d L / d t_g
                   = vee(R G^T - G R^T) + t x d L / d v  (G the rotation block of d L / d W)
 
-and the pose takes an Adam step on the twist (the host handles 6 numbers per iteration).
+and the twist takes an Adam step. The view itself stays at the initial pose W0; the
+accumulated correction E moves the fixed Gaussians instead, by M = W0^-1 E W0 (the
+keyframes' device world transform), since rendering M mu into W0 is rendering mu into
+E W0. The pose estimate is E W0.
 
 Pixels the previous frame's Gaussians do not cover render dark with no depth; left in
 the loss they pull the camera towards covering more of the frame instead of towards
-alignment. As in silhouette-masked tracking, the image gradients are therefore kept only
-where the rendered alpha exceeds `silhouette` (0.99): an elementwise mask applied to the
-library's L1 gradients (glue around the library calls, not part of the splatting path).
-The default weights favour colour (1.0) over depth (0.1): the composited depth is not
-normalised by alpha and its errors at depth discontinuities would otherwise move the
-minimum away from the true pose (measured on the oracle's renders of a room).
+alignment. As in silhouette-masked tracking, the loss and its image gradients are
+therefore kept only where the rendered alpha exceeds `silhouette` (0.99). The default
+weights favour colour (1.0) over depth (0.1): the composited depth is not normalised by
+alpha and its errors at depth discontinuities would otherwise move the minimum away from
+the true pose (measured on the oracle's renders of a room).
 """
 from __future__ import annotations
 
@@ -65,16 +68,22 @@ def exp_twist(xi: np.ndarray) -> np.ndarray:
 class PoseRefiner:
     """Camera of one new RGB-D frame against fixed Gaussians (typically the previous
     keyframe's). kfs: DeviceKeyframe list (their learnable flags are ignored: the
-    Gaussians are not updated); camera: intrinsics and the initial world->cam pose;
-    target_rgb (3,H,W) and target_depth (H,W): the new frame."""
+    Gaussians are not updated); camera: intrinsics and the initial world->cam pose W0;
+    target_rgb (3,H,W) and target_depth (H,W): the new frame. step() only launches
+    library calls on the current stream; the loss history and the pose are read back
+    when asked for."""
 
     def __init__(self, kfs, camera, target_rgb: torch.Tensor, target_depth: torch.Tensor,
                  rgb_weight: float = 1.0, depth_weight: float = 0.1, lr_rot: float = 2e-3, lr_trans: float = 2e-3,
                  silhouette: float = 0.99):
         from .synth import Camera
-        self.kfs = [splat.DeviceKeyframe(k.cam, k.depth, k.offset, k.rgb, k.logit, k.scale, False) for k in kfs]
+        self.state = torch.zeros(B.SGAD_POSE_STATE_FLOATS, device="cuda")
+        self._reset_state()
+        self.kfs = [splat.DeviceKeyframe(k.cam, k.depth, k.offset, k.rgb, k.logit, k.scale, False,
+                                         world_transform=self.state[12:24]) for k in kfs]
         self.cam = Camera(camera.width, camera.height, camera.fx, camera.fy, camera.cx, camera.cy,
                           np.asarray(camera.pose, np.float32).copy())
+        self.W0 = np.asarray(self.cam.pose, np.float32).reshape(12).copy()
         self.trgb = [target_rgb.float().contiguous()]
         self.tdep = [target_depth.float().contiguous()]
         self.rgb_weight, self.depth_weight = rgb_weight, depth_weight
@@ -86,61 +95,58 @@ class PoseRefiner:
         self.d_pose = torch.zeros(12, device="cuda")
         self.loss = torch.zeros(1, device="cuda")
         self.valid = torch.zeros(1, dtype=torch.int32, device="cuda")
-        self.lr = np.array([lr_rot] * 3 + [lr_trans] * 3)
-        self.m = np.zeros(6)
-        self.v = np.zeros(6)
-        self.t = 0
+        self.lr = np.array([lr_rot, lr_trans], np.float64)
         self.sp.plan(self.kfs, [self.cam], slack=1.5)
-        self.history: List[float] = []
+        self._hist: List[torch.Tensor] = []
+
+    def _reset_state(self) -> None:
+        eye = torch.tensor([1.0, 0, 0, 0, 0, 1.0, 0, 0, 0, 0, 1.0, 0], device="cuda")
+        self.state.zero_()
+        self.state[0:12].copy_(eye)                  # E
+        self.state[12:24].copy_(eye)                 # M = W0^-1 E W0
 
     @property
     def pose(self) -> np.ndarray:
-        return np.asarray(self.cam.pose, np.float64)
+        """Current world->cam pose estimate E W0 (3x4; reads the device state)."""
+        if int(self.state[36].item()) == 0:
+            return self.W0.reshape(3, 4).astype(np.float64)
+        return self.state[37:49].double().cpu().numpy().reshape(3, 4)
 
-    def _set_pose(self, W: np.ndarray) -> None:
-        # a new camera object, so the library's cached launch structures are rebuilt
-        from .synth import Camera
-        c = self.cam
-        self.cam = Camera(c.width, c.height, c.fx, c.fy, c.cx, c.cy, np.asarray(W[:3], np.float32).copy())
+    @property
+    def history(self) -> List[float]:
+        """Loss of every step's starting pose (reads the device values)."""
+        return [float(x) for x in torch.cat(self._hist).cpu()] if self._hist else []
 
-    def step(self) -> float:
-        """One iteration; returns the loss of the pose it started from."""
+    def step(self) -> torch.Tensor:
+        """One iteration; returns the (device) loss of the pose it started from."""
         views = [self.cam]
         self.sp.forward(self.kfs, views, self.images)
-        s, _, need = self.sp.check()
-        if s != 0:                                  # more keys than planned: re-plan and redo
-            self.sp.reserve(self.kfs, views, int(need * 1.5) + 4096)
-            self.sp.forward(self.kfs, views, self.images)
         self.loss.zero_()
         self.sp.l1_loss_grad(views, self.images, self.trgb, self.tdep, self.rgb_weight, self.depth_weight,
-                             self.d_rgb, self.d_dep, self.loss, self.valid)
-        mask = (self.images[0]["alpha"] > self.silhouette).float()
-        self.d_rgb[0].mul_(mask)
-        self.d_dep[0].mul_(mask)
+                             self.d_rgb, self.d_dep, self.loss, self.valid, min_alpha=self.silhouette)
         gin = [dict(rgb=self.d_rgb[0], depth=self.d_dep[0], pose=self.d_pose)]
         self.sp.backward(self.kfs, views, gin, [None] * len(self.kfs))
-        d_pose = self.d_pose.cpu().numpy()
-        # the masked L1 objective the step descends (for the history)
-        loss = float(self.rgb_weight * (mask * (self.images[0]["rgb"] - self.trgb[0]).abs()).mean()
-                     + self.depth_weight * (mask * (self.images[0]["depth"] - self.tdep[0]).abs()).mean())
-        g = twist_gradient(self.cam.pose, d_pose)
-        self.t += 1
-        self.m = 0.9 * self.m + 0.1 * g
-        self.v = 0.999 * self.v + 0.001 * g * g
-        mh = self.m / (1 - 0.9 ** self.t)
-        vh = self.v / (1 - 0.999 ** self.t)
-        xi = -self.lr * mh / (np.sqrt(vh) + 1e-12)
-        W = np.vstack([np.asarray(self.cam.pose, np.float64), [0, 0, 0, 1]])
-        self._set_pose(exp_twist(xi) @ W)
-        self.history.append(loss)
-        return loss
+        B.sgad_pose_adam_step(self.d_pose.data_ptr(), self.W0, self.state.data_ptr(), self.lr[0], self.lr[1],
+                              stream=self.sp.stream())
+        loss = self.loss.clone()
+        self._hist.append(loss)
+        return loss[0]
 
     def run(self, iters: int, decay: bool = True) -> np.ndarray:
-        """`iters` steps, the step size decayed by a half cosine to 5 % of its start."""
+        """`iters` steps, the step size decayed by a half cosine to 5 % of its start. The
+        key capacity is checked once at the end; if any forward ran out of room the
+        workspace grows and the run starts again from the initial pose."""
         lr0 = self.lr.copy()
-        for i in range(iters):
-            if decay:
-                self.lr = lr0 * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * i / max(1, iters))))
-            self.step()
-        self.lr = lr0
+        for attempt in range(2):
+            for i in range(iters):
+                if decay:
+                    self.lr = lr0 * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * i / max(1, iters))))
+                self.step()
+            self.lr = lr0
+            s, _, need = self.sp.check()
+            if s == 0:
+                break
+            self.sp.reserve(self.kfs, [self.cam], int(need * 1.5) + 4096)
+            self._reset_state()
+            self._hist = []
         return self.pose

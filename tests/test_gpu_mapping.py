@@ -162,10 +162,17 @@ def test_packed_window_matches_separate_tensors(scene1):
         m2.step_eager()
         torch.cuda.synchronize()
         assert abs(float(m1.loss) - float(m2.loss)) <= 1e-6 * abs(float(m1.loss))
+    # Adam's first steps move each parameter by about lr times the sign of its gradient;
+    # a gradient that cancels to rounding noise can take either sign depending on the order
+    # of the backward's atomic additions, so a few parameters may differ by up to
+    # 2 x lr per step; everything else agrees to rounding
     for a, b in zip(m1.kfs, m2.kfs):
-        for n in ("offset", "rgb", "logit", "scale"):
+        for n, lr in (("offset", 0.01), ("rgb", 0.0025), ("logit", 0.05), ("scale", 0.005)):
             x, y = getattr(a, n), getattr(b, n)
-            assert torch.allclose(x, y, rtol=1e-5, atol=1e-7), n
+            close = torch.isclose(x, y, rtol=1e-5, atol=1e-7)
+            assert float(close.float().mean()) >= 0.999, n
+            d = (x - y).abs() if n != "scale" else (x.log() - y.log()).abs()
+            assert float(d.max()) <= 3 * 2 * lr * 1.01, (n, float(d.max()))
     host = buf[:n_state].cpu()                                   # the prefix is the updated state
     off = (m2.kfs[0].rgb.data_ptr() - buf.data_ptr()) // 4
     assert torch.equal(host[off:off + m2.kfs[0].rgb.numel()], m2.kfs[0].rgb.flatten().cpu())
