@@ -1023,33 +1023,40 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
     // a window of 32 chunks is held one per lane, lane L the chunk cw - L
     const uint32_t *wm = a.wmask + wmask_base(tile, s) + wb;
     int cw = (fnc - 1) >> 5;
-    uint32_t wl = cw - lane >= 0 ? wm[8 * (cw - lane)] : 0u;
-    int ci = -1;                        // window slot being consumed (-1: none yet)
-    uint32_t rem = 0u;                  // its bits not yet taken
+    uint32_t wl = cw - lane >= 0 ? wm[8 * (cw - lane)] : 0u;     // bits of chunk cw - lane not yet taken
     for (;;) {
-        // 1. gather up to 32 marked positions, highest first
-        int n = 0, my_pos = 0;
+        // 1. gather up to 32 marked positions, highest first, into S.pos: a scan of the
+        // lanes' remaining bit counts orders the window's chunks, and each lane writes the
+        // highest bits of its chunk that still fit the round
+        int n = 0;
         while (n < 32) {
-            if (rem == 0u) {
-                const uint32_t after = ci >= 31 ? 0u : (~0u << (ci + 1));
-                const uint32_t nz = __ballot_sync(kFull, wl != 0u) & after;
-                if (nz) {
-                    ci = __ffs(nz) - 1;
-                    rem = __shfl_sync(kFull, wl, ci);
-                } else {
-                    cw -= 32;
-                    if (cw < 0) break;
-                    wl = cw - lane >= 0 ? wm[8 * (cw - lane)] : 0u;
-                    ci = -1;
-                    continue;
-                }
+            const int cnt = __popc(wl);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
             }
-            const int bit = 31 - __clz(rem);
-            rem &= ~(1u << bit);
-            if (lane == n) my_pos = 32 * (cw - ci) + bit;
-            ++n;
+            const int total = __shfl_sync(kFull, incl, 31);
+            if (total == 0) {
+                cw -= 32;
+                if (cw < 0) break;
+                wl = cw - lane >= 0 ? wm[8 * (cw - lane)] : 0u;
+                continue;
+            }
+            const int excl = incl - cnt;
+            int take = 32 - n - excl;
+            take = take < 0 ? 0 : (take > cnt ? cnt : take);
+            for (int t = 0; t < take; ++t) {
+                const int bit = 31 - __clz(wl);
+                wl &= ~(1u << bit);
+                S.pos[n + excl + t] = 32 * (cw - lane) + bit;
+            }
+            n += total < 32 - n ? total : 32 - n;
         }
         if (n == 0) break;
+        __syncwarp();
+        const int my_pos = lane < n ? S.pos[lane] : 0;
         // 2. stage (lane j: entry j) and the box masks
         uint32_t my_g = 0u, row = 0u;
         float4 my_w0 = make_float4(0.f, 0.f, 0.f, 0.f);
