@@ -188,8 +188,8 @@ const char *sgad_last_error(void);
 
 /* Bytes of workspace needed for a problem of this shape holding up to key_capacity
  * (tile, Gaussian) keys. Host arithmetic only. The workspace holds the per-Gaussian
- * world records and gradient accumulators (64 B per Gaussian), per-tile offsets,
- * counters, heavy-first order and the list of tiles sorted exactly (16 B per tile), the
+ * world records and gradient accumulators (64 B per Gaussian), the tile rectangle of
+ * every (Gaussian, view) pair (8 B each), per-tile offsets, counters, heavy-first order and the list of tiles sorted exactly (16 B per tile), the
  * per-pixel state kept for the backward pass (8 B per view pixel), two key arrays
  * (16 B per key), the per-pixel
  * contribution words of the pair-parallel backward (32 B per key + 1 KB per tile) and
@@ -437,9 +437,8 @@ sgad_status sgad_pose_adam_step(const float *d_pose, const float *view_pose, flo
  * Same arguments and results as sgad_forward(), without the workspace: the scratch is a
  * static device array of SGAD_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
  * that loads the library holds until the process exits. Problems whose workspace does
- * not fit (the workspace of sgad_workspace_size: 64 B per Gaussian, 8 B per view
- * pixel, 49 B per key and ~1.1 KB per tile)
- * are rejected with SGAD_ERR_WORKSPACE_TOO_SMALL before anything is launched; a forward
+ * not fit (the workspace of sgad_workspace_size: 64 B per Gaussian, 8 B per Gaussian
+ * and view, 8 B per view pixel, 49 B per key and ~1.1 KB per tile) are rejected with SGAD_ERR_WORKSPACE_TOO_SMALL before anything is launched; a forward
  * whose keys exceed the room left returns SGAD_ERR_KEY_OVERFLOW. The call synchronises
  * `stream` to report that status. Every call looks up the array's device address in the
  * current device's context (cudaGetSymbolAddress, a host-side lookup); the first call on

@@ -7,9 +7,10 @@
 //   k_scan_tiles    : exclusive scan of the per-tile counts -> list offsets; flags a
 //                     key overflow.
 //   k_emit          : per Gaussian and view, one 8-byte entry (f32 depth bits << 32 |
-//                     Gaussian index) per tile of the rectangle, written into the tile's
-//                     bucket. The depth is evaluated in double-float so the key is the
-//                     exactly-rounded f32 of the view depth.
+//                     Gaussian index) per tile of the rectangle the count kernel left in
+//                     the workspace (8 bytes per Gaussian and view), written into the
+//                     tile's bucket. The depth is evaluated in double-float so the key is
+//                     the exactly-rounded f32 of the view depth.
 #include "sgad_device.cuh"
 
 namespace sgad {
@@ -24,7 +25,7 @@ __device__ __forceinline__ uint32_t lanemask_lt()
 }
 
 __global__ void __launch_bounds__(256) k_project_count(const __grid_constant__ Scene sc, World *__restrict__ world,
-                                                       uint32_t *__restrict__ tile_cnt)
+                                                       uint32_t *__restrict__ tile_cnt, uint2 *__restrict__ rects)
 {
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = g < sc.n_gauss;
@@ -61,7 +62,10 @@ __global__ void __launch_bounds__(256) k_project_count(const __grid_constant__ S
         const ViewDev &v = sc.view[vi];
         Rect r;
         int n = 0;
-        if (valid) n = bin_rect(project(w0, v), v, sc.tw_log2, sc.th_log2, r);
+        if (valid) {
+            n = bin_rect(project(w0, v), v, sc.tw_log2, sc.th_log2, r);
+            if (rects) rects[(size_t)vi * sc.n_gauss + g] = pack_rect(r, n);
+        }
         const int maxn = __reduce_max_sync(full, n);
         for (int i = 0; i < maxn; ++i) {
             uint32_t tile = kInvalidTile;
@@ -184,17 +188,15 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t *__restrict__ cnt,
         order[atomicAdd(&cls_cnt[order_class(off[i + 1] - off[i])], 1u)] = (uint32_t)i;
 }
 
-__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Scene sc, const World *__restrict__ world,
+__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Scene sc, const uint2 *__restrict__ rects,
                                               const uint32_t *__restrict__ off, uint32_t *__restrict__ cursor,
                                               uint64_t *__restrict__ entries, WsHeader *hdr)
 {
     if (hdr->overflow) return;
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = g < sc.n_gauss;
-    float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f);
     dvec3 m = {};
     if (valid) {
-        w0 = world[g].w0;
         const KfDev &k = sc.kf[find_kf(sc, g)];
         const uint32_t j = g - k.gbase;
         m = df_world_point(k, (int)(j % (uint32_t)k.W), (int)(j / (uint32_t)k.W), k.depth[j], k.offset[j]);
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Scene sc, 
         const ViewDev &v = sc.view[vi];
         Rect r;
         int n = 0;
-        if (valid) n = bin_rect(project(w0, v), v, sc.tw_log2, sc.th_log2, r);
+        if (valid) n = unpack_rect(rects[(size_t)vi * sc.n_gauss + g], r);     // the count kernel's rectangle
         const int maxn = __reduce_max_sync(full, n);
         if (maxn == 0) continue;
         uint64_t key = 0;
@@ -235,10 +237,10 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Scene sc, 
     }
 }
 
-void launch_project_count(const Scene &sc, World *world, uint32_t *tile_cnt, cudaStream_t st)
+void launch_project_count(const Scene &sc, World *world, uint32_t *tile_cnt, uint2 *rects, cudaStream_t st)
 {
     const unsigned blocks = (sc.n_gauss + 255) / 256;
-    if (blocks) k_project_count<<<blocks, 256, 0, st>>>(sc, world, tile_cnt);
+    if (blocks) k_project_count<<<blocks, 256, 0, st>>>(sc, world, tile_cnt, rects);
 }
 
 void launch_scan_tiles(uint32_t *cnt, uint32_t *off, int n_tiles, uint64_t key_cap, WsHeader *hdr, uint32_t *order,
@@ -247,11 +249,11 @@ void launch_scan_tiles(uint32_t *cnt, uint32_t *off, int n_tiles, uint64_t key_c
     k_scan_tiles<<<1, 1024, 0, st>>>(cnt, off, n_tiles, key_cap, hdr, order);
 }
 
-void launch_emit(const Scene &sc, const World *world, const uint32_t *off, uint32_t *cursor, uint64_t *entries,
+void launch_emit(const Scene &sc, const uint2 *rects, const uint32_t *off, uint32_t *cursor, uint64_t *entries,
                  WsHeader *hdr, cudaStream_t st)
 {
     const unsigned blocks = (sc.n_gauss + 255) / 256;
-    if (blocks) k_emit<<<blocks, 256, 0, st>>>(sc, world, off, cursor, entries, hdr);
+    if (blocks) k_emit<<<blocks, 256, 0, st>>>(sc, rects, off, cursor, entries, hdr);
 }
 
 }  // namespace sgad

@@ -9,9 +9,9 @@
 #include "sgad_device.cuh"
 
 namespace sgad {
-void launch_project_count(const Scene &, World *, uint32_t *, cudaStream_t);
+void launch_project_count(const Scene &, World *, uint32_t *, uint2 *, cudaStream_t);
 void launch_scan_tiles(uint32_t *, uint32_t *, int, uint64_t, WsHeader *, uint32_t *, cudaStream_t);
-void launch_emit(const Scene &, const World *, const uint32_t *, uint32_t *, uint64_t *, WsHeader *, cudaStream_t);
+void launch_emit(const Scene &, const uint2 *, const uint32_t *, uint32_t *, uint64_t *, WsHeader *, cudaStream_t);
 cudaError_t launch_sort_tiles(const uint32_t *, uint64_t *, uint64_t *, int, int, WsHeader *, uint32_t *, cudaStream_t);
 cudaError_t launch_composite(bool, int, int, int, const Scene &, const World *, const uint32_t *, const uint64_t *,
                              float *, uint32_t *, float4 *, WsHeader *, const uint32_t *, uint32_t *, uint32_t *,
@@ -173,6 +173,7 @@ struct Ws {
     WsHeader *hdr() const { return reinterpret_cast<WsHeader *>(base + L.header); }
     World *world() const { return reinterpret_cast<World *>(base + L.world); }
     float4 *gacc() const { return reinterpret_cast<float4 *>(base + L.gacc); }
+    uint2 *rects() const { return reinterpret_cast<uint2 *>(base + L.rects); }
     uint32_t *tile_off() const { return reinterpret_cast<uint32_t *>(base + L.tile_off); }
     uint32_t *tile_cnt() const { return reinterpret_cast<uint32_t *>(base + L.tile_cnt); }
     uint32_t *tile_order() const { return reinterpret_cast<uint32_t *>(base + L.tile_order); }
@@ -188,7 +189,7 @@ struct Ws {
 sgad_status get_ws(const Scene &sc, uint64_t n_pix, void *workspace, size_t ws_bytes, int64_t key_cap, Ws &ws)
 {
     if (key_cap < 0 || key_cap >= 0xffffffffll) return fail(SGAD_ERR_INVALID_ARG, "key_capacity out of range");
-    ws.L = make_layout(sc.n_gauss, (uint64_t)sc.n_tiles, n_pix, (uint64_t)key_cap);
+    ws.L = make_layout(sc.n_gauss, (uint64_t)sc.n_views, (uint64_t)sc.n_tiles, n_pix, (uint64_t)key_cap);
     if (!workspace) return fail(SGAD_ERR_INVALID_ARG, "workspace is NULL");
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
         return fail(SGAD_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
@@ -224,7 +225,7 @@ sgad_status run_binning_count(const sgad_options &o, const Scene &sc, const Ws &
     cudaError_t e = cudaMemsetAsync(ws.hdr(), 0, clear_sticky ? sizeof(WsHeader) : kHeaderPerCall, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.tile_cnt(), 0, ((size_t)sc.n_tiles + 1) * 4, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    launch_project_count(sc, ws.world(), ws.tile_cnt(), st);
+    launch_project_count(sc, ws.world(), ws.tile_cnt(), ws.rects(), st);
     launch_scan_tiles(ws.tile_cnt(), ws.tile_off(), sc.n_tiles, (uint64_t)key_cap, ws.hdr(),
                       uses_order(o) ? ws.tile_order() : nullptr, st);
     return last_launch("binning");
@@ -237,7 +238,7 @@ sgad_status run_forward_prep(sgad_ctx *ctx, const Scene &sc, const Ws &ws, int64
     sgad_status s = run_binning_count(ctx->opt, sc, ws, key_cap, false, st);
     if (s) return s;
     mark(ctx, 1, st);
-    launch_emit(sc, ws.world(), ws.tile_off(), ws.tile_cnt(), ws.keys(), ws.hdr(), st);
+    launch_emit(sc, ws.rects(), ws.tile_off(), ws.tile_cnt(), ws.keys(), ws.hdr(), st);
     mark(ctx, 2, st);
     cudaError_t e = launch_sort_tiles(ws.tile_off(), ws.keys(), ws.keys_alt(), sc.n_tiles, ctx->sort_cap, ws.hdr(),
                                       ws.sort_list(), st);
@@ -487,7 +488,7 @@ sgad_status sgad_workspace_size(const sgad_ctx *ctx, const sgad_keyframe *kfs, i
     if (s) return s;
     if (key_capacity < 0 || key_capacity >= 0xffffffffll)
         return fail(SGAD_ERR_INVALID_ARG, "key_capacity out of range");
-    *bytes = make_layout(sc.n_gauss, (uint64_t)sc.n_tiles, n_pix, (uint64_t)key_capacity).total;
+    *bytes = make_layout(sc.n_gauss, (uint64_t)sc.n_views, (uint64_t)sc.n_tiles, n_pix, (uint64_t)key_capacity).total;
     return SGAD_OK;
 }
 

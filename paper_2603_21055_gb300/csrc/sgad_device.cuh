@@ -176,6 +176,23 @@ __device__ __forceinline__ int bin_rect(const Proj &p, const ViewDev &v, int tw_
     return r.nx * r.ny;
 }
 
+// Tile rectangle of a (Gaussian, view) pair as the binning count leaves it for the key
+// emission: (tx0 | ty0 << 16, nx | ny << 16); nx = ny = 0 when it lists no tile.
+__device__ __forceinline__ uint2 pack_rect(const Rect &r, int n)
+{
+    return n > 0 ? make_uint2((uint32_t)r.tx0 | ((uint32_t)r.ty0 << 16), (uint32_t)r.nx | ((uint32_t)r.ny << 16))
+                 : make_uint2(0u, 0u);
+}
+
+__device__ __forceinline__ int unpack_rect(const uint2 q, Rect &r)
+{
+    r.tx0 = (int)(q.x & 0xffffu);
+    r.ty0 = (int)(q.x >> 16);
+    r.nx = (int)(q.y & 0xffffu);
+    r.ny = (int)(q.y >> 16);
+    return r.nx * r.ny;
+}
+
 // ------------------------------------------- double-float (Dekker/Knuth) arithmetic
 //
 // Used only for the view depth that goes into the sort key, so the key equals the
@@ -322,19 +339,20 @@ __device__ __forceinline__ bool gauss_alpha(const Staged &s, float qx, float qy,
 // Workspace layout (byte offsets, 256-aligned sections). Shared by the host API and the
 // kernels' launch code.
 struct Layout {
-    size_t header, world, gacc, tile_off, tile_cnt, tile_order, sort_list, pix_t, pix_n, keys, keys_alt, contrib, wmask,
-        total;
+    size_t header, world, gacc, rects, tile_off, tile_cnt, tile_order, sort_list, pix_t, pix_n, keys, keys_alt, contrib,
+        wmask, total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-inline Layout make_layout(uint64_t n_gauss, uint64_t n_tiles, uint64_t n_pix, uint64_t key_cap)
+inline Layout make_layout(uint64_t n_gauss, uint64_t n_views, uint64_t n_tiles, uint64_t n_pix, uint64_t key_cap)
 {
     Layout L;
     size_t o = 0;
     L.header = o; o = align256(o + sizeof(WsHeader));
     L.world = o; o = align256(o + n_gauss * sizeof(World));
     L.gacc = o; o = align256(o + n_gauss * 32);
+    L.rects = o; o = align256(o + n_gauss * n_views * 8);
     L.tile_off = o; o = align256(o + (n_tiles + 1) * 4);
     L.tile_cnt = o; o = align256(o + (n_tiles + 1) * 4);
     L.tile_order = o; o = align256(o + n_tiles * 4);
