@@ -438,15 +438,16 @@ sgad_status sgad_pose_adam_step(const float *d_pose, const float *view_pose, flo
  * static device array of SGAD_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
  * that loads the library holds until the process exits. Problems whose workspace does
  * not fit (the workspace of sgad_workspace_size: 64 B per Gaussian, 8 B per Gaussian
- * and view, 8 B per view pixel, 49 B per key and ~1.1 KB per tile) are rejected with SGAD_ERR_WORKSPACE_TOO_SMALL before anything is launched; a forward
- * whose keys exceed the room left returns SGAD_ERR_KEY_OVERFLOW. The call synchronises
- * `stream` to report that status. Every call looks up the array's device address in the
- * current device's context (cudaGetSymbolAddress, a host-side lookup); the first call on
- * a device also loads the library's device code there and should come before any stream
- * capture on that device. All calls share the one array and it keeps the last call's contents: calls
- * that may run concurrently on the GPU (different streams or threads) race and must be
- * serialised by the caller. No backward pass is offered this way (its state would live
- * in the shared array). */
+ * and view, 8 B per view pixel, 49 B per key and ~1.1 KB per tile) are rejected with
+ * SGAD_ERR_WORKSPACE_TOO_SMALL before anything is launched; a forward whose keys exceed
+ * the room left returns SGAD_ERR_KEY_OVERFLOW. The call synchronises `stream` to report
+ * that status. Every call looks up the array's device address in the current device's
+ * context (cudaGetSymbolAddress, a host-side lookup); the first call on a device also
+ * loads the library's device code there and should come before any stream capture on
+ * that device. All calls share the one array and it keeps the last call's contents:
+ * calls that may run concurrently on the GPU (different streams or threads) race and
+ * must be serialised by the caller. No backward pass is offered this way (its state
+ * would live in the shared array). */
 #define SGAD_NOALLOC_SCRATCH_BYTES (64u << 20)
 sgad_status sgad_forward_noalloc(sgad_ctx *ctx, const sgad_keyframe *kfs, int32_t n_kf,
                                  const sgad_camera *views, int32_t n_views, sgad_images *out,
