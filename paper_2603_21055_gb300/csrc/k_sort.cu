@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kBucketThreads, 3)
     k_sort_tiles_bucket(const uint32_t *__restrict__ off, uint64_t *__restrict__ entries, int cap, WsHeader *hdr,
                         uint32_t *__restrict__ list)
 {
-    __shared__ uint32_t start[1 << kBucketBinsLog2];    // bucket counts, then bucket starts
+    __shared__ __align__(16) uint32_t start[1 << kBucketBinsLog2];    // bucket counts, then bucket starts
     __shared__ uint32_t red[2][kBucketThreads / 32];
     __shared__ int heavy;
     extern __shared__ uint64_t ks[];                     // the tile's entries, bucket by bucket
@@ -405,15 +405,27 @@ __global__ void __launch_bounds__(kBucketThreads, 3)
         slot[r] = i < n ? atomicAdd(&start[((uint32_t)(gk[i] >> 32) - mn) >> shift], 1u) : 0u;
     }
     __syncthreads();
-    // exclusive scan of the counts (each thread nbins / 512 or one consecutive bins)
+    // exclusive scan of the counts (each thread nbins / 512 or one consecutive bins, read
+    // and written as 16-byte vectors when there are four or eight: conflict-free)
     {
         const int per = nbins > kBucketThreads ? nbins / kBucketThreads : 1;
         const int b0 = threadIdx.x * per;
-        uint32_t v[8], sum = 0u;
+        uint32_t v[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, sum = 0u;
         bool big = false;
+        if (per >= 4) {
+            const uint4 lo = reinterpret_cast<const uint4 *>(start + b0)[0];
+            v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+            if (per == 8) {
+                const uint4 hi = reinterpret_cast<const uint4 *>(start + b0)[1];
+                v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < per && b0 + j < nbins) v[j] = start[b0 + j];
+        }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            v[j] = (j < per && b0 + j < nbins) ? start[b0 + j] : 0u;
             sum += v[j];
             big |= v[j] > (uint32_t)kBucketMax;
         }
@@ -428,12 +440,20 @@ __global__ void __launch_bounds__(kBucketThreads, 3)
         __syncthreads();
         uint32_t run = inc - sum;
         for (int i = 0; i < w; ++i) run += red[0][i];
+        uint32_t o[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (j < per && b0 + j < nbins) {
-                start[b0 + j] = run;
-                run += v[j];
-            }
+        for (int j = 0; j < 8; ++j) {
+            o[j] = run;
+            run += v[j];
+        }
+        if (per >= 4) {
+            reinterpret_cast<uint4 *>(start + b0)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            if (per == 8) reinterpret_cast<uint4 *>(start + b0)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < per && b0 + j < nbins) start[b0 + j] = o[j];
+        }
     }
     __syncthreads();
     if (heavy) {                                         // uniform: read after the barrier
