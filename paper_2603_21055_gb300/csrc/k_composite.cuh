@@ -930,42 +930,63 @@ constexpr size_t kLocalSmemBytes = (kLocalThreads / 32) * sizeof(LocalWarpSmem);
 
 // Moments of the entries [j0, j1) of a round (lane j holds entry j: the pixels it
 // contributed to, cm, its Gaussian g and world record w0; its pair slots start at
-// base_j - b0), the chain rule, and the pose terms accumulated per lane. Whole warp.
+// base_j - b0), the chain rule, and the pose terms accumulated per lane. When the range
+// holds at most 16 entries, the lane 16 away from entry j's lane sums the moments of the
+// entry's bottom two pixel rows and hands them over with one shuffle per moment, so no
+// lane is idle and each walks at most half of an entry's pixels. Whole warp.
 template <bool POSE>
 __device__ __forceinline__ void bwdl_reduce(const ViewDev &v, const CompositeArgs &a, const LocalWarpSmem &S, int j0,
                                             int j1, int lane, uint32_t cm, uint32_t g, float4 w0, float bxf, float byf,
                                             int b0, float (&pose)[12])
 {
-    if (lane < j0 || lane >= j1 || cm == 0u) return;
+    const bool split = j1 - j0 <= 16;
+    const uint32_t cm_x = __shfl_xor_sync(kFull, cm, 16);
+    const bool own = lane >= j0 && lane < j1;
+    int e = -1;
+    uint32_t m = 0u;
+    if (own) {
+        e = lane;
+        m = split ? (cm & 0xffffu) : cm;
+    } else if (split && (lane ^ 16) >= j0 && (lane ^ 16) < j1) {
+        e = lane ^ 16;
+        m = cm_x & 0xffff0000u;
+    }
+    float A[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) A[q] = 0.f;
+    if (m) {
+        const float4 sa = S.sa[e];
+        const uint32_t row = S.row[e];
+        const int base = S.base[e] - b0;
+        while (m) {
+            const int p = __ffs(m) - 1;
+            m &= m - 1u;
+            const float2 gw = S.pairs[base + __popc(row & lane_mask_lt(p))];
+            const float4 pg = S.pg[p];
+            const float dx = __fsub_rn(sa.x, bxf + (float)(p & 7));
+            const float dy = __fsub_rn(sa.y, byf + (float)(p >> 3));
+            A[0] += gw.y * pg.x;
+            A[1] += gw.y * pg.y;
+            A[2] += gw.y * pg.z;
+            A[3] += gw.y * pg.w;
+            const float G = gw.x;
+            A[4] += G;
+            A[5] += G * dx;
+            A[6] += G * dy;
+            A[7] += G * dx * dx;
+            A[8] += G * dx * dy;
+            A[9] += G * dy * dy;
+        }
+    }
+    if (split) {
+#pragma unroll
+        for (int q = 0; q < 10; ++q) A[q] += __shfl_xor_sync(kFull, A[q], 16);
+    }
+    if (!own || cm == 0u) return;
     Staged st;
     st.a = S.sa[lane];
     st.b = S.sb[lane];
     st.c = S.sc[lane];
-    const uint32_t row = S.row[lane];
-    const int base = S.base[lane] - b0;
-    float A[10];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) A[q] = 0.f;
-    uint32_t m = cm;
-    while (m) {
-        const int p = __ffs(m) - 1;
-        m &= m - 1u;
-        const float2 gw = S.pairs[base + __popc(row & lane_mask_lt(p))];
-        const float4 pg = S.pg[p];
-        const float dx = __fsub_rn(st.a.x, bxf + (float)(p & 7));
-        const float dy = __fsub_rn(st.a.y, byf + (float)(p >> 3));
-        A[0] += gw.y * pg.x;
-        A[1] += gw.y * pg.y;
-        A[2] += gw.y * pg.z;
-        A[3] += gw.y * pg.w;
-        const float G = gw.x;
-        A[4] += G;
-        A[5] += G * dx;
-        A[6] += G * dy;
-        A[7] += G * dx * dx;
-        A[8] += G * dx * dy;
-        A[9] += G * dy * dy;
-    }
     const float3 gt = chain_and_accumulate(A, st, project(w0, v), w0.w, v, a.gacc, g);
     if (POSE) {
 #pragma unroll
@@ -1072,16 +1093,6 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
             S.sc[lane] = st.c;
             row = box_block_mask(st.a, bxf, byf);
         }
-        // pair slots: entry j owns popc(row_j) slots from base_j (exclusive prefix)
-        const int cnt = __popc(row);
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        S.row[lane] = row;
-        S.base[lane] = incl - cnt;
         S.pos[lane] = lane < n ? my_pos : -1;
         // 3. the entries whose box covers this pixel, before its contributor count
         uint32_t mine = warp_transpose32(row, lane);
@@ -1094,6 +1105,19 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
             }
             mine &= lo >= 32 ? 0u : (~0u << lo);
         }
+        // pair slots: entry j owns one slot per pixel it may reach (inside its box, before
+        // the pixel's contributor count), popc(row_j) slots from base_j (exclusive prefix)
+        row = warp_transpose32(mine, lane);
+        const int cnt = __popc(row);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        S.row[lane] = row;
+        S.base[lane] = incl - cnt;
+        __syncwarp();
         // 4./5. walk and reduce, in sub-ranges whose box slots fit the pair buffer
         int j0 = 0;
         while (j0 < n) {
