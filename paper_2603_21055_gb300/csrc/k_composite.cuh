@@ -168,32 +168,68 @@ __device__ __forceinline__ uint32_t box_block_mask(const float4 a, float bxf, fl
 
 // ------------------------------------------------------------------ forward
 
-// Double-buffered staging (one block barrier per batch instead of two) measured slower
-// on the room workload (the prefetched last batch and the halved occupancy cost more than
-// the barrier saves); it stays available at build time.
-#ifndef SGAD_FWD_DOUBLE_BUFFER
-#define SGAD_FWD_DOUBLE_BUFFER 0
-#endif
-constexpr int kFwdBuffers = SGAD_FWD_DOUBLE_BUFFER ? 2 : 1;
+// Forward shared memory for batch B: the staged entries.
+template <int B>
+constexpr size_t fwd_smem_bytes()
+{
+    return (size_t)B * sizeof(Staged);
+}
 
-// Resident-block target of the forward kernel for batch B: as many blocks as the staging
-// buffers let share an SM (227 KB), at most SGAD_FWD_MINBLOCKS; it bounds the registers.
+// Resident-block target of the forward kernel for batch B: as many blocks as the shared
+// memory lets share an SM (227 KB), at most SGAD_FWD_MINBLOCKS; it bounds the registers.
 template <int B>
 constexpr int fwd_min_blocks()
 {
-    const int fit = (227 * 1024) / (kFwdBuffers * B * (int)sizeof(Staged) + 1024);
+    const int fit = (int)((227 * 1024) / (fwd_smem_bytes<B>() + 1024));
     return fit < 1 ? 1 : (fit > SGAD_FWD_MINBLOCKS ? SGAD_FWD_MINBLOCKS : fit);
 }
 
-// Stage entries [b0, min(b0 + B, e)) of the tile list into buf (one or more per thread).
-template <int B>
-__device__ __forceinline__ void stage_batch(const Scene &sc, const CompositeArgs &a, const ViewDev &v, uint32_t b0,
-                                            uint32_t e, Staged *buf)
+// The box of a staged entry as tile-relative masks, in place of its half extents (a.z,
+// a.w): bit i of the column mask is set when tile column i (pixel x = ox + i) lies in
+// [ceil(x - hx), floor(x + hx)], the row mask likewise; both zero for an empty box. The
+// same pixel sets as box_block_mask, computed once per (entry, tile) instead of per warp.
+template <int TW, int TH>
+__device__ __forceinline__ void box_tile_masks(float4 &a, float oxf, float oyf)
 {
-#pragma unroll
+    uint32_t cm = 0u, rm = 0u;
+    if (a.z >= 0.0f) {
+        const float x0 = fmaxf(ceilf(a.x - a.z) - oxf, 0.0f), x1 = fminf(floorf(a.x + a.z) - oxf, (float)(TW - 1));
+        const float y0 = fmaxf(ceilf(a.y - a.w) - oyf, 0.0f), y1 = fminf(floorf(a.y + a.w) - oyf, (float)(TH - 1));
+        if (x0 <= x1 && y0 <= y1) {
+            const int xl = (int)x0, xh = (int)x1, yl = (int)y0, yh = (int)y1;
+            cm = (~0u >> (31 - (xh - xl))) << xl;
+            rm = (~0u >> (31 - (yh - yl))) << yl;
+        }
+    }
+    a.z = __uint_as_float(cm);
+    a.w = __uint_as_float(rm);
+}
+
+// The 8x4 block mask (bit p: pixel (p % 8, p / 8) of the block) of an entry staged with
+// tile masks, for the block at tile column 8 cb (csh = 8 cb) and tile row 4 rb (rsh = 4 rb).
+__device__ __forceinline__ uint32_t block_mask_from_tile(const float2 m, int csh, int rsh)
+{
+    const uint32_t cols = (__float_as_uint(m.x) >> csh) & 0xffu;
+    const uint32_t rows = (__float_as_uint(m.y) >> rsh) & 0xfu;
+    // row bit k -> byte k all ones: the four copies of rows at bit offsets 0, 7, 14, 21
+    // put bit k at bit 8 k without overlapping
+    return (cols * 0x01010101u) & (((rows * 0x00204081u) & 0x01010101u) * 0xffu);
+}
+
+// Stage entries [b0, min(b0 + B, e)) of a tile list whose tile origin is (oxf, oyf).
+template <int TW, int TH, int B>
+__device__ __forceinline__ void stage_batch(const Scene &sc, const CompositeArgs &a, const ViewDev &v, uint32_t b0,
+                                            uint32_t e, float oxf, float oyf, Staged *buf)
+{
+#pragma unroll 1
     for (int r = 0; r < (B + kFwdThreads - 1) / kFwdThreads; ++r) {
         const int k = r * kFwdThreads + threadIdx.x;
-        if (k < B && b0 + k < e) stage_entry(sc, a, v, a.entries[b0 + k], buf[k]);
+        if (k < B && b0 + k < e) {
+            Staged st;
+            stage_entry(sc, a, v, a.entries[b0 + k], st);
+            box_tile_masks<TW, TH>(st.a, oxf, oyf);
+            buf[k] = st;
+        }
     }
 }
 
@@ -212,19 +248,20 @@ __device__ __forceinline__ int2 fwd_pixel(int ox, int oy, int warp, int lane)
     return make_int2(ox + (warp % (TW / 8)) * 8 + (lane & 7), oy + (warp / (TW / 8)) * 4 + (lane >> 3));
 }
 
-// The warp walks nb staged entries (list positions b0 - s ...) against its pixel block
-// (origin bx, by), 32 at a time: lane j forms entry j's box mask over the block's pixels
-// (the pixels inside its alpha >= 1/255 box), a bit transpose gives every lane the
-// entries whose box covers its pixel, and each lane not yet done walks its own entries
-// in order. Lanes are busy only with (pixel, entry) pairs inside the entry's box.
+// The warp walks nb staged entries (list positions b0 - s ...) against its pixel block,
+// 32 at a time: lane j forms entry j's block mask (the block's pixels inside its alpha >=
+// 1/255 box, from the tile masks staged with it), a bit transpose gives every lane the
+// entries whose box covers its pixel, and each lane not yet done walks its own entries in
+// order. Lanes are busy only with (pixel, entry) pairs inside the entry's box.
 __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0, uint32_t s, int tile,
-                                           const CompositeArgs &a, float bxf, float byf, float qx, float qy, int lane,
+                                           const CompositeArgs &a, int csh, int rsh, float qx, float qy, int lane,
                                            FwdPixel &px, bool &warp_done, uint32_t &n_pairs, uint32_t &n_evals,
                                            uint32_t *wmw)
 {
     for (int c0 = 0; c0 < nb; c0 += 32) {
         const int j = c0 + lane;
-        uint32_t mine = warp_transpose32(j < nb ? box_block_mask(sm[j].a, bxf, byf) : 0u, lane);
+        uint32_t mine = warp_transpose32(
+            j < nb ? block_mask_from_tile(*reinterpret_cast<const float2 *>(&sm[j].a.z), csh, rsh) : 0u, lane);
         if (px.done) mine = 0u;
         uint32_t bits = 0;
         while (__any_sync(kFull, mine != 0u)) {
@@ -275,7 +312,6 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
     const int local = tile - v.tile_base;
     const int tx = local % v.tiles_x, ty = local / v.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float bx = (float)(tx * TW + (warp % (TW / 8)) * 8), by = (float)(ty * TH + (warp / (TW / 8)) * 4);
     const int2 pix = fwd_pixel<TW>(tx * TW, ty * TH, warp, lane);
     const int px = pix.x, py = pix.y;
     const bool inside = px < v.W && py < v.H;
@@ -287,30 +323,16 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
     // this warp's contribution-mask word of chunk 0; chunk c's is 8 c words further, i.e.
     // at offset (32 c) / 4
     uint32_t *wmw = a.wmask ? a.wmask + wmask_base(tile, s) + warp : nullptr;
-#if SGAD_FWD_DOUBLE_BUFFER
-    // Two staging buffers: batch k + 1 is staged into the other buffer before batch k is
-    // walked, so one block barrier per batch both publishes the next batch and ends the
-    // walk of this one (and tests for the early exit).
-    if (!__syncthreads_and(st.done) && s < e) {
-        stage_batch<B>(sc, a, v, s, e, sm);
-        __syncthreads();
-        int parity = 0;
-        for (uint32_t b0 = s; b0 < e; b0 += B, parity ^= 1) {
-            if (b0 + B < e) stage_batch<B>(sc, a, v, b0 + B, e, sm + (parity ^ 1) * B);
-            const int nb = (int)min((uint32_t)B, e - b0);
-            if (!warp_done) walk_batch(sm + parity * B, nb, b0, s, tile, a, bx, by, qx, qy, lane, st, warp_done, n_pairs, n_evals, wmw);
-            if (__syncthreads_and(st.done)) break;
-        }
-    }
-#else
     for (uint32_t b0 = s; b0 < e; b0 += B) {
         if (__syncthreads_and(st.done)) break;
-        stage_batch<B>(sc, a, v, b0, e, sm);
+        // tile origin from this thread's pixel (TW, TH are powers of two)
+        stage_batch<TW, TH, B>(sc, a, v, b0, e, (float)(px & ~(TW - 1)), (float)(py & ~(TH - 1)), sm);
         __syncthreads();
         const int nb = (int)min((uint32_t)B, e - b0);
-        if (!warp_done) walk_batch(sm, nb, b0, s, tile, a, bx, by, qx, qy, lane, st, warp_done, n_pairs, n_evals, wmw);
+        if (!warp_done)
+            walk_batch(sm, nb, b0, s, tile, a, 8 * (warp % (TW / 8)), 4 * (warp / (TW / 8)), qx, qy, lane, st,
+                       warp_done, n_pairs, n_evals, wmw);
     }
-#endif
     if (inside) {
         const size_t hw = (size_t)v.W * v.H, p = (size_t)py * v.W + px;
         v.rgb[p] = st.cr + st.T * sc.bg[0];
@@ -328,7 +350,7 @@ __global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks<B>())
     k_composite_fwd(const __grid_constant__ Scene sc, const CompositeArgs a)
 {
     extern __shared__ float4 fwd_smem[];
-    Staged *sm = reinterpret_cast<Staged *>(fwd_smem);     // kFwdBuffers x B staged entries
+    Staged *sm = reinterpret_cast<Staged *>(fwd_smem);     // B staged entries
     __shared__ int s_tile;
     if (a.hdr->overflow) return;
     uint32_t n_pairs = 0, n_evals = 0;
@@ -1204,7 +1226,7 @@ cudaError_t launch_composite_tb(bool fwd, const Scene &sc, const CompositeArgs &
     if (fwd) {
         // the dynamic staging buffers plus the kernel's static slot may pass the 48 KB
         // default: raise the limit (once per device)
-        constexpr size_t smem = (size_t)kFwdBuffers * B * sizeof(Staged);
+        constexpr size_t smem = fwd_smem_bytes<B>();
         static int configured[64] = {};
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -1246,7 +1268,7 @@ template <int TW, int TH, int B>
 cudaError_t occupancy_tb(bool fwd, int *blocks_per_sm)
 {
     if (fwd) {
-        constexpr size_t smem = (size_t)kFwdBuffers * B * sizeof(Staged);
+        constexpr size_t smem = fwd_smem_bytes<B>();
         const cudaError_t e = cudaFuncSetAttribute(k_composite_fwd<TW, TH, B>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
