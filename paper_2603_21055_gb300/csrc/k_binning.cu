@@ -67,11 +67,16 @@ __global__ void __launch_bounds__(256) k_project_count(const __grid_constant__ S
             if (rects) rects[(size_t)vi * sc.n_gauss + g] = pack_rect(r, n);
         }
         const int maxn = __reduce_max_sync(full, n);
+        uint32_t row = (uint32_t)(v.tile_base + r.ty0 * v.tiles_x + r.tx0);   // first tile of the current rectangle row
+        int col = 0;
         for (int i = 0; i < maxn; ++i) {
             uint32_t tile = kInvalidTile;
             if (i < n) {
-                const int ty = r.ty0 + i / r.nx, tx = r.tx0 + i % r.nx;
-                tile = (uint32_t)(v.tile_base + ty * v.tiles_x + tx);
+                tile = row + (uint32_t)col;
+                if (++col == r.nx) {
+                    col = 0;
+                    row += (uint32_t)v.tiles_x;
+                }
             }
             const uint32_t peers = __match_any_sync(full, tile);
             if (tile != kInvalidTile && (threadIdx.x & 31) == __ffs(peers) - 1)
@@ -213,11 +218,16 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Scene sc, 
         if (maxn == 0) continue;
         uint64_t key = 0;
         if (n > 0) key = ((uint64_t)__float_as_uint(df_view_depth(m, v)) << 32) | g;
+        uint32_t row = (uint32_t)(v.tile_base + r.ty0 * v.tiles_x + r.tx0);
+        int col = 0;
         for (int i = 0; i < maxn; ++i) {
             uint32_t tile = kInvalidTile;
             if (i < n) {
-                const int ty = r.ty0 + i / r.nx, tx = r.tx0 + i % r.nx;
-                tile = (uint32_t)(v.tile_base + ty * v.tiles_x + tx);
+                tile = row + (uint32_t)col;
+                if (++col == r.nx) {
+                    col = 0;
+                    row += (uint32_t)v.tiles_x;
+                }
             }
             const uint32_t peers = __match_any_sync(full, tile);
             const int leader = __ffs(peers) - 1;
