@@ -263,6 +263,8 @@ __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0
         uint32_t mine = warp_transpose32(
             j < nb ? block_mask_from_tile(*reinterpret_cast<const float2 *>(&sm[j].a.z), csh, rsh) : 0u, lane);
         if (px.done) mine = 0u;
+        n_evals += __popc(mine);            // less the candidates left when the pixel stops
+        const int pos0 = (int)(b0 + c0 - s);
         uint32_t bits = 0;
         while (__any_sync(kFull, mine != 0u)) {
             if (mine) {
@@ -270,14 +272,13 @@ __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0
                 mine &= mine - 1u;
                 const Staged st = sm[c0 + jj];
                 float dx, dy, ep, alpha;
-                ++n_evals;
                 if (gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) {
                     const float test = __fmul_rn(px.T, __fsub_rn(1.0f, alpha));
                     if (test < kTStop) {
                         px.done = true;
+                        n_evals -= __popc(mine);
                         mine = 0u;
                     } else {
-                        ++n_pairs;
                         bits |= 1u << jj;
                         const float w = __fmul_rn(alpha, px.T);
                         px.cr = __fmaf_rn(w, st.c.x, px.cr);
@@ -286,11 +287,12 @@ __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0
                         px.dd = __fmaf_rn(w, st.c.w, px.dd);
                         px.aa = __fadd_rn(px.aa, w);
                         px.T = test;
-                        px.last = (int)(b0 + c0 + jj - s);
+                        px.last = pos0 + jj;
                     }
                 }
             }
         }
+        n_pairs += __popc(bits);
         if (a.contrib) a.contrib[contrib_base(a, tile, s) + (size_t)((b0 - s + c0) >> 5) * 256 + threadIdx.x] = bits;
         if (wmw) {
             const uint32_t wbits = __reduce_or_sync(kFull, bits);
