@@ -458,7 +458,7 @@ def roofline(stages, stats, scene, peaks, src, bwd_kernel="k_composite_bwdp", fp
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     ng, nk = scene.n_gaussians, stats["n_keys"]
-    kernel_of = {"composite_bwd": bwd_kernel, "composite_fwd": "k_composite_fwd", "sort": "k_sort_tiles",
+    kernel_of = {"composite_bwd": bwd_kernel, "composite_fwd": "k_composite_fwd", "sort": "k_sort_tiles_bucket",
                  "emit": "k_emit", "binning": "k_project_count", "finalize": "k_finalize"}
     if name in ("composite_fwd", "composite_bwd"):
         per = FLOPS_FWD_PAIR if name == "composite_fwd" else FLOPS_BWD_PAIR
