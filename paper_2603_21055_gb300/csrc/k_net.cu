@@ -568,6 +568,182 @@ __global__ void __launch_bounds__(128) k_conv3x3_wgrad(const WgradArgs a)
     if (warp == 0) tc::tmem_dealloc(tmem, S::kCols);
 }
 
+// ------------------------------------------------------------------ weight gradient, TMA-fed
+//
+// The same sums, with the operands read in the layout the TMA boxes land in, so that no
+// shared-memory transpose is needed: a K block is 128 pixels of one output row; its three
+// input rows (pixels x0 - 1 .. x0 + 128) arrive as 3 x CI/8 slabs [pixel][8 channels] of
+// kSlabUnits units and the output-gradient row as CO/8 slabs of 128 units. Read with the
+// pixels as K and the channels as M (x) or N (dy), a slab is the MN-major canonical
+// layout: a core matrix is 8 pixels x 8 channels, 128 contiguous bytes; the next 8
+// channels are one slab further, the next 8 pixels 128 bytes further. For a fixed dx the
+// (dy, channel group) rows of the three input rows form one uniformly strided M
+// dimension of 3 CI rows that starts dx pixels into the slabs, so one M = 128 MMA per
+// (dx, 16-pixel K step) covers the three taps (dy, dx); the M rows after 3 CI read a slab
+// of ones (row 3 CI: the bias gradient, taken from dx = 0) and zero slabs, whose products
+// are not used. Accumulators: three TMEM blocks of CO columns (one per dx) for the whole
+// persistent block, added to dW with one atomic per (row, column) at the end.
+// One thread issues the TMA loads (two stages) and the MMAs; the four warps run the
+// epilogue. Every wait is bounded.
+constexpr int kWgPix = 128;                // pixels per K block
+constexpr int kWgGroups = 16;              // M groups read by an M = 128 MMA
+
+template <int CI, int CO>
+struct WgradTmaSmem {
+    static constexpr int kXBytes = kWgGroups * kSlabUnits * 16;       // slabs of x (+ ones, zeros)
+    static constexpr int kYBytes = (CO / 8) * kWgPix * 16;            // slabs of dy
+    static constexpr int kStage = kXBytes + kYBytes;
+    static constexpr uint32_t kTx = (uint32_t)(3 * (CI / 8) * kRowUnits * 16 + (CO / 8) * kWgPix * 16);
+    static constexpr size_t bytes = (size_t)2 * kStage + 1024;       // + alignment slack
+    static constexpr int kCols = 3 * CO <= 32 ? 32 : (3 * CO <= 64 ? 64 : 128);
+    static_assert(3 * (CI / 8) + 1 <= kWgGroups, "the three rows and the ones slab fit one M = 128 MMA");
+};
+
+// Instruction descriptor of kind::f16, bf16 A and B both MN-major (transposed), f32
+// accumulator, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N)
+{
+    return tc::idesc_bf16(M, N) | (1u << 15) | (1u << 16);
+}
+
+// Descriptor of an MN-major operand without swizzle: the leading byte offset is the
+// distance between core matrices adjacent in K (here 8 pixels, 128 bytes), the stride byte
+// offset the distance between core matrices adjacent in M or N (8 channels, one slab).
+// (The weight-gradient parity tests fail with the two offsets exchanged.)
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t mn_stride, uint32_t k_stride)
+{
+    return tc::sdesc(saddr, k_stride, mn_stride);
+}
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(128) k_conv3x3_wgrad_tma(const __grid_constant__ CUtensorMap xmap,
+                                                           const __grid_constant__ CUtensorMap ymap,
+                                                           const WgradArgs a)
+{
+    static_assert(CI % 16 == 0 && (CO == 16 || CO == 32), "channel counts");
+    using S = WgradTmaSmem<CI, CO>;
+    constexpr int kcx = CI / 8, kcy = CO / 8;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t full[2], empty[2];
+    __shared__ uint32_t taddr_s;
+    __shared__ int failed_s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int segs = (a.W + kWgPix - 1) / kWgPix;
+    const long long n_kb = (long long)a.N * a.H * segs;
+
+    if (warp == 0) tc::tmem_alloc(&taddr_s, S::kCols);
+    if (threadIdx.x == 32) {
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        failed_s = 0;
+    }
+    // the slabs after the three input rows: ones (first element of each unit) then zeros
+    for (int st = 0; st < 2; ++st) {
+        uint4 *x = reinterpret_cast<uint4 *>(base + (size_t)st * S::kStage);
+        for (int i = threadIdx.x; i < (kWgGroups - 3 * kcx) * kSlabUnits; i += blockDim.x) {
+            const int g = 3 * kcx + i / kSlabUnits;
+            x[g * kSlabUnits + i % kSlabUnits] = make_uint4(g == 3 * kcx ? 0x3F80u : 0u, 0u, 0u, 0u);
+        }
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = taddr_s;
+    constexpr uint32_t idesc = idesc_bf16_mn(128, CO);
+    long long issued = 0;                  // K blocks whose MMAs were issued
+
+    if (threadIdx.x == 0) {
+        const auto load = [&](long long kb, int st) {
+            const int xs = (int)(kb % segs);
+            const long long ry = kb / segs;
+            const int y = (int)(ry % a.H), n = (int)(ry / a.H);
+            const uint32_t xb = tc::smem_u32(base + (size_t)st * S::kStage), yb = xb + (uint32_t)S::kXBytes;
+            tc::mbar_arrive_expect_tx(&full[st], S::kTx);
+            for (int dy = 0; dy < 3; ++dy)
+                for (int kc = 0; kc < kcx; ++kc)
+                    tc::tma_load_4d(xb + (uint32_t)((dy * kcx + kc) * kSlabUnits * 16), &xmap, 8 * kc,
+                                    xs * kWgPix - 1, y + dy - 1, n, &full[st]);
+            for (int kc = 0; kc < kcy; ++kc)
+                tc::tma_load_4d(yb + (uint32_t)(kc * kWgPix * 16), &ymap, 8 * kc, xs * kWgPix, y, n, &full[st]);
+        };
+        int loaded = 0;                    // K blocks whose loads were issued
+        for (int i = 0; i < 2; ++i)
+            if (blockIdx.x + (long long)i * gridDim.x < n_kb) {
+                load(blockIdx.x + (long long)i * gridDim.x, i);
+                ++loaded;
+            }
+        bool ok = true;
+        for (long long j = 0;; ++j) {
+            const long long kb = blockIdx.x + j * gridDim.x;
+            if (kb >= n_kb) break;
+            const int st = (int)(j & 1);
+            if (!tc::mbar_wait_bounded(&full[st], (uint32_t)((j >> 1) & 1), kSpinLimit)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t xb = tc::smem_u32(base + (size_t)st * S::kStage), yb = xb + (uint32_t)S::kXBytes;
+#pragma unroll
+            for (int s = 0; s < kWgPix / 16; ++s)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx)
+                    tc::mma_bf16(tmem + (uint32_t)(dx * CO), sdesc_mn(xb + (uint32_t)(dx * 16 + s * 256), kSlabUnits * 16, 128),
+                                 sdesc_mn(yb + (uint32_t)(s * 256), kWgPix * 16, 128), idesc, (j | s) != 0);
+            tc::mma_commit(&empty[st]);
+            issued = j + 1;
+            const long long next = kb + 2 * (long long)gridDim.x;
+            if (next < n_kb) {
+                if (!tc::mbar_wait_bounded(&empty[st], (uint32_t)((j >> 1) & 1), kSpinLimit)) {
+                    ok = false;
+                    break;
+                }
+                load(next, st);
+                ++loaded;
+            }
+        }
+        // drain: the last MMAs have completed and no box is still landing
+        if (issued > 0 && !tc::mbar_wait_bounded(&empty[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1), kSpinLimit))
+            ok = false;
+        for (long long u = issued; u < loaded; ++u)
+            if (!tc::mbar_wait_bounded(&full[u & 1], (uint32_t)((u >> 1) & 1), kSpinLimit)) ok = false;
+        if (!ok) {
+            set_status(a.status, 2u);
+            failed_s = 1;
+        }
+        if (issued == 0) failed_s = failed_s | 2;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (failed_s == 0) {
+        const int row = 32 * warp + lane;
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+            for (int c0 = 0; c0 < CO; c0 += 16) {
+                uint32_t q[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(dx * CO + c0), q);
+                tc::tmem_wait_ld();
+                if (row < 3 * CI) {
+                    const int tap = 3 * (row / CI) + dx, ci = row % CI;
+                    float *dst = a.dw + ((size_t)tap * CI + ci) * CO + c0;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) atomicAdd(dst + c, __uint_as_float(q[c]));
+                } else if (row == 3 * CI && dx == 0) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) atomicAdd(a.db + c0 + c, __uint_as_float(q[c]));
+                }
+            }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, S::kCols);
+}
+
 // ------------------------------------------------------------------ launchers
 
 namespace {
@@ -630,15 +806,15 @@ cudaError_t encode_tiled(EncodeTiledFn *out)
 }
 
 // Tensor map of an NHWC bf16 activation with CI channels, as dims (CI, W, H, N), boxes of
-// 8 channels x 130 pixels x 1 row x 1 frame, zero fill outside.
-cudaError_t input_map(const void *base, int ci, int n, int h, int w, CUtensorMap *m)
+// 8 channels x box_px pixels x 1 row x 1 frame, zero fill outside.
+cudaError_t input_map(const void *base, int ci, int n, int h, int w, CUtensorMap *m, int box_px = kTileM + 2)
 {
     EncodeTiledFn fn = nullptr;
     cudaError_t e = encode_tiled(&fn);
     if (e != cudaSuccess) return e;
     const cuuint64_t dims[4] = {(cuuint64_t)ci, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
     const cuuint64_t strides[3] = {(cuuint64_t)ci * 2, (cuuint64_t)w * ci * 2, (cuuint64_t)h * w * ci * 2};
-    const cuuint32_t box[4] = {8, (cuuint32_t)(kTileM + 2), 1, 1};
+    const cuuint32_t box[4] = {8, (cuuint32_t)box_px, 1, 1};
     const cuuint32_t elem[4] = {1, 1, 1, 1};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, elem,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -679,9 +855,34 @@ cudaError_t launch_conv(const ConvArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+#ifndef SGAD_NET_WGRAD_TMA
+#define SGAD_NET_WGRAD_TMA 1
+#endif
+
 template <int CI, int CO>
 cudaError_t launch_wgrad(const WgradArgs &a, cudaStream_t st)
 {
+#if SGAD_NET_WGRAD_TMA
+    {
+        using S = WgradTmaSmem<CI, CO>;
+        cudaError_t e = set_smem(k_conv3x3_wgrad_tma<CI, CO>, S::bytes);
+        if (e != cudaSuccess) return e;
+        const long long blocks = (long long)a.N * a.H * ((a.W + kWgPix - 1) / kWgPix);
+        if (blocks <= 0) return cudaSuccess;
+        CUtensorMap xm, ym;
+        e = input_map(a.x, CI, a.N, a.H, a.W, &xm);
+        if (e == cudaSuccess) e = input_map(a.dy, CO, a.N, a.H, a.W, &ym, kWgPix);
+        if (e != cudaSuccess) return e;
+        int grid = resident_grid((const void *)k_conv3x3_wgrad_tma<CI, CO>, S::bytes, blocks);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long cap = (long long)sms * (512 / S::kCols);
+        if (grid > cap) grid = (int)cap;
+        k_conv3x3_wgrad_tma<CI, CO><<<grid, 128, S::bytes, st>>>(xm, ym, a);
+        return cudaGetLastError();
+    }
+#endif
     const size_t smem = WgradSmem<CI, CO>::bytes;
     cudaError_t e = set_smem(k_conv3x3_wgrad<CI, CO>, smem);
     if (e != cudaSuccess) return e;
