@@ -90,10 +90,12 @@ sgad_status sgad_net_backward(const sgad_net_params *params, sgad_net_grads *gra
 sgad_status sgad_net_check(void *workspace, size_t ws_bytes, void *stream);
 
 /* Device pointers into the workspace, for inspection and tests: x[0] the packed input
- * (NHWC bf16, 16 channels), x[1..3] the post-ReLU activations (NHWC bf16, 32 channels),
- * y4 the raw outputs (float pairs per pixel), dy4 the output gradient (NHWC bf16, 16
- * channels, two used) and dpre[0..2] the gradients of the pre-activations of layers
- * 0..2 (NHWC bf16, 32 channels). */
+ * (bf16, 16 channels), x[1..3] the post-ReLU activations (bf16, 32 channels), y4 the raw
+ * outputs (float pairs per pixel), dy4 the output gradient (bf16, 16 channels, two used)
+ * and dpre[0..2] the gradients of the pre-activations of layers 0..2 (bf16, 32
+ * channels). The bf16 tensors are chunk-planar: channel c of pixel (frame f, row y,
+ * column x) of a tensor with C channels is element c % 8 of the 16-byte unit
+ * ((f H + y) C/8 + c / 8) W + x. */
 typedef struct {
     const void *x[4];
     const float *y4;

@@ -157,7 +157,7 @@ sgad_status sgad_net_loss_grad(int32_t n_frames, int32_t height, int32_t width, 
     if (s) return s;
     if (!target_delta || !target_logit) return err(SGAD_ERR_INVALID_ARG, "sgad_net_loss_grad: a target is NULL");
     return launched(launch_loss(reinterpret_cast<const float2 *>(ws.base + ws.L.y4), target_delta, target_logit,
-                                logit_weight, ws.at(ws.L.dy4), loss_accum, (size_t)n_frames * height * width,
+                                logit_weight, ws.at(ws.L.dy4), loss_accum, (size_t)n_frames * height * width, width,
                                 static_cast<cudaStream_t>(stream)),
                     "net loss");
 }

@@ -7,7 +7,8 @@
 // holding elements (r, 8k .. 8k + 7). Core matrices (8 rows x 16 bytes) are therefore
 // 128 contiguous bytes; the descriptor's stride byte offset (between 8-row groups) is
 // 128 and its leading byte offset (between the two 8-element K chunks of one MMA) is the
-// distance between K chunks, R * 16 bytes for a dense array.
+// distance between K chunks, R * 16 bytes for a dense array. (The proposal net's weight
+// gradient also reads MN-major operands; its descriptors are described there.)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -115,21 +116,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
         : "memory");
 }
 
-// 8x8 bf16 blocks: ldmatrix with transposition then stmatrix without, i.e. a transposed
-// copy of four blocks; each thread supplies one source row address (ldmatrix) and one
-// destination row address (stmatrix): thread t addresses row (t % 8) of block (t / 8).
-__device__ __forceinline__ void transpose_copy_x4(uint32_t src_row, uint32_t dst_row)
-{
-    uint32_t r0, r1, r2, r3;
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(src_row)
-                 : "memory");
-    asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(dst_row), "r"(r0), "r"(r1),
-                 "r"(r2), "r"(r3)
-                 : "memory");
-}
-
 // Arrive once on *bar (count 1 per call).
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
@@ -141,21 +127,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
-}
-
-// 16-byte asynchronous copy global -> shared (Ampere cp.async); src_bytes 0 writes zeros.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-
-// Wait until at most N of this thread's most recent cp.async groups are pending.
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // TMA: copy one box of a rank-4 tiled tensor map at coordinates (c0 .. c3), innermost

@@ -5,12 +5,12 @@ kernel): a bf16 output may differ from the FP64 value by its rounding (2^-8 rela
 plus the FP32 accumulation error, bounded by 1e-5 times the sum of the magnitudes of
 the summed products (A below); FP32 outputs and parameter gradients (long sums over
 pixels, accumulated with atomics) by 1e-4 A. Sizes: two frames of 5 x 150 pixels, so
-each image row spans a full 128-pixel tile and a ragged 22-pixel one, and the weight
-gradient's 64-pixel blocks end ragged too; and two frames of 240 x 630 pixels (2,400
-row tiles of 128 pixels, the last of each row ragged; 4,800 weight-gradient blocks of 64
-pixels), several times the persistent grids, so that every block of the convolutions
+each image row spans a full 128-pixel tile and a ragged 22-pixel one (the weight
+gradient's 128-pixel K blocks the same); and two frames of 240 x 630 pixels (2,400 row
+tiles of 128 pixels, the last of each row ragged, and as many weight-gradient K blocks),
+several times the persistent grids, so that every block of the convolutions
 walks its two-stage TMA ring and flips its double TMEM accumulator many times and every
-weight-gradient block prefetches its next K block.
+weight-gradient block cycles through its three load stages.
 """
 import numpy as np
 import pytest
@@ -47,11 +47,16 @@ def run(request):
     assert net.check() == 0
     bufs = net.buffers()
     npx = N * H * W
-    x = [_bf(net.workspace_array(bufs.x[0], npx * 16)).reshape(N, H, W, 16)]
-    x += [_bf(net.workspace_array(bufs.x[l], npx * 32)).reshape(N, H, W, 32) for l in (1, 2, 3)]
+
+    def planar(ptr, c):
+        # chunk-planar units [frame][row][chunk][pixel] of 8 channels -> (N, H, W, c)
+        a = _bf(net.workspace_array(ptr, npx * c)).reshape(N, H, c // 8, W, 8)
+        return a.transpose(0, 1, 3, 2, 4).reshape(N, H, W, c)
+
+    x = [planar(bufs.x[0], 16)] + [planar(bufs.x[l], 32) for l in (1, 2, 3)]
     y4 = net.workspace_array(bufs.y4, npx * 2, torch.float32).cpu().numpy().astype(np.float64).reshape(N, H, W, 2)
-    dy4 = _bf(net.workspace_array(bufs.dy4, npx * 16)).reshape(N, H, W, 16)
-    dpre = [_bf(net.workspace_array(bufs.dpre[l], npx * 32)).reshape(N, H, W, 32) for l in range(3)]
+    dy4 = planar(bufs.dy4, 16)
+    dpre = [planar(bufs.dpre[l], 32) for l in range(3)]
     return dict(net=net, params=params, rgb=rgb.cpu().numpy(), depth=depth.cpu().numpy(), td=td.cpu().numpy(),
                 tl=tl.cpu().numpy(), delta=delta.cpu().numpy(), logit=logit.cpu().numpy(), x=x, y4=y4, dy4=dy4,
                 dpre=dpre, dw=[t.cpu().numpy().astype(np.float64) for t in net.dw],
