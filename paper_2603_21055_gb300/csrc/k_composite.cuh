@@ -945,6 +945,7 @@ constexpr int kLocalPairCap = 512;          // (G, w) slots per warp
 struct LocalWarpSmem {
     float4 sa[32], sb[32], sc[32];  // the round's entries (Staged a, b, c)
     float4 pg[32];                  // image gradients (r, g, b, depth) of the unit's pixels
+    float2 pq[32];                  // their coordinates (x, y)
     float2 pairs[kLocalPairCap];    // (G, w) per box pixel of each entry
     uint32_t row[32];               // box mask of entry j over the block's pixels
     int32_t base[32];               // first pair slot of entry j
@@ -960,8 +961,8 @@ constexpr size_t kLocalSmemBytes = (kLocalThreads / 32) * sizeof(LocalWarpSmem);
 // lane is idle and each walks at most half of an entry's pixels. Whole warp.
 template <bool POSE>
 __device__ __forceinline__ void bwdl_reduce(const ViewDev &v, const CompositeArgs &a, const LocalWarpSmem &S, int j0,
-                                            int j1, int lane, uint32_t cm, uint32_t g, float4 w0, float bxf, float byf,
-                                            int b0, float (&pose)[12])
+                                            int j1, int lane, uint32_t cm, uint32_t g, float4 w0, int b0,
+                                            float (&pose)[12])
 {
     const bool split = j1 - j0 <= 16;
     const uint32_t cm_x = __shfl_xor_sync(kFull, cm, 16);
@@ -987,8 +988,9 @@ __device__ __forceinline__ void bwdl_reduce(const ViewDev &v, const CompositeArg
             m &= m - 1u;
             const float2 gw = S.pairs[base + __popc(row & lane_mask_lt(p))];
             const float4 pg = S.pg[p];
-            const float dx = __fsub_rn(sa.x, bxf + (float)(p & 7));
-            const float dy = __fsub_rn(sa.y, byf + (float)(p >> 3));
+            const float2 pq = S.pq[p];
+            const float dx = __fsub_rn(sa.x, pq.x);
+            const float dy = __fsub_rn(sa.y, pq.y);
             A[0] += gw.y * pg.x;
             A[1] += gw.y * pg.y;
             A[2] += gw.y * pg.z;
@@ -1055,6 +1057,7 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
     if (fnc == 0) return;
     __syncwarp();                       // the previous unit's readers of S are done
     S.pg[lane] = make_float4(gr, gg, gb, gD);
+    S.pq[lane] = make_float2(qx, qy);
     const float bgdot = sc.bg[0] * gr + sc.bg[1] * gg + sc.bg[2] * gb;
     // Reverse-walk state: transmittance, and the suffix sums of colour and depth behind
     // the current entry already dotted with this pixel's image gradients (Sg = S_C . g_C
@@ -1176,7 +1179,7 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
             }
             const uint32_t cm = warp_transpose32(done, lane);
             __syncwarp();
-            bwdl_reduce<POSE>(v, a, S, j0, j1, lane, cm, my_g, my_w0, bxf, byf, b0, pose);
+            bwdl_reduce<POSE>(v, a, S, j0, j1, lane, cm, my_g, my_w0, b0, pose);
             __syncwarp();               // the next sub-range overwrites the pair slots
             j0 = j1;
         }
