@@ -15,6 +15,16 @@ step and excluded from the timed events; max over ranks. With --gpus N > 1 (torc
 every rank maps its own independent keyframe window (weak scaling, no collective on
 the data path).
 
+End to end (`e2e`): the same iteration through the public API with the window in a
+pinned host buffer, uploaded and read back every step; two device windows alternate so
+that a step's copies overlap the other window's iteration.
+
+At N = 1 the line also carries `secs_to_psnr` (mapping seconds to PSNR thresholds with
+the learned vs the zero-offset initialisation, the net trained inside the run) and
+`secondary_workloads` (batching, mapping, tracking, sequence and net, each run as its
+own `--workload` process after the headline measurement); `--no-learned` leaves both
+out, `--no-secondary` the latter.
+
 `--impl reference` times the FP64 CPU oracle (the correctness reference; there is no
 reference implementation of the paper's code) on a bounded sample of the same workload.
 """
@@ -56,7 +66,11 @@ def parse():
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-learned", action="store_true",
-                   help="room8: leave out the secs-to-PSNR record (learned vs plain initialisation)")
+                   help="room8: leave out the secs-to-PSNR record (learned vs plain initialisation) and the "
+                        "secondary-workload records")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="room8: leave out the secondary-workload records (batching, mapping, tracking, "
+                        "sequence, net)")
     p.add_argument("--json-out", default="")
     p.add_argument("--workload", choices=["room8", "batching", "mapping", "learned", "net", "ssim", "sequence",
                                                "tracking"],
@@ -325,6 +339,8 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(scene)
     if rank == 0 and world == 1 and not args.no_learned:
         line["secs_to_psnr"] = secs_to_psnr_record(args)
+    if rank == 0 and world == 1 and not args.no_learned and not args.no_secondary:
+        line["secondary_workloads"] = secondary_records()
     if rank == 0:
         out = json.dumps(line)
         print(out, flush=True)
@@ -333,6 +349,44 @@ def run_ours(args):
                 f.write(out + "\n")
     if world > 1:
         dist.destroy_process_group()
+
+
+# The secondary workloads of the default line: each runs as its own process (the same
+# bench with --workload) after the headline measurement, and the line keeps its figures.
+SECONDARY = {
+    "batching": ("value", "unit", "ms_per_step", "speedup_vs_per_view", "images_identical", "grad_rel_l2_diff",
+                 "autotuned", "default_split", "per_view_launches"),
+    "mapping": ("value", "unit", "ms_per_step", "mpix_per_s", "peak_device_bytes_torch", "keys", "psnr_db_before",
+                "psnr_db_after", "clocks"),
+    "tracking": ("value", "unit", "stage_ms_eager", "gicp_iterations_median", "ate_rmse_m", "rot_err_deg_max",
+                 "clocks"),
+    "sequence": ("value", "unit", "modes", "clocks"),
+    "net": ("value", "unit", "forward", "backward"),
+}
+
+
+def secondary_records(timeout_s: int = 600):
+    import subprocess
+    import tempfile
+    out = {}
+    for w, keys in SECONDARY.items():
+        with tempfile.NamedTemporaryFile(suffix=".json") as f:
+            t0 = time.perf_counter()
+            try:
+                r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", w, "--json-out",
+                                    f.name], stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, timeout=timeout_s)
+                rec = json.loads(open(f.name).read()) if r.returncode == 0 else None
+            except (subprocess.TimeoutExpired, ValueError):
+                rec, r = None, None
+            if rec is None:
+                err = (r.stderr.decode(errors="replace").strip().splitlines()[-1:] if r is not None else ["timeout"])
+                out[w] = {"failed": err[0] if err else "no output"}
+                continue
+            d = {"metric": rec.get("metric"), "config": rec.get("config", {}).get("workload")}
+            d.update({k: rec[k] for k in keys if k in rec})
+            d["wall_s"] = round(time.perf_counter() - t0, 1)
+            out[w] = d
+    return out
 
 
 def split_of(sp):
@@ -349,50 +403,101 @@ def split_of(sp):
 def run_e2e(mp, steps, stream, flush):
     """Same metric through the public API with host buffers: the window's keyframe planes,
     targets and loss slot live in one pinned host buffer laid out like the device copy of
-    splat.upload_window; each step copies it in (one copy), runs the iteration on a
+    splat.upload_window; every step copies it in (one copy), runs the iteration on a
     Mapper over those device views (the tuned options of `mp`), and reads the updated
-    parameters and the loss back (one copy); copies and iteration are one CUDA graph
-    replay."""
+    parameters and the loss back (one copy). Two device windows alternate so that a
+    step's copies overlap the other window's iteration: one CUDA graph replay runs two
+    steps (A, B) on the compute stream while a copy stream reads back the previous B,
+    uploads B, then (after A) reads back A and uploads the next A; the replay ends when
+    the copies have. Every step's upload and read-back are inside the timed region (the
+    last read-back of B after the last replay, inside the last timing)."""
+    import dataclasses
     import torch
     from paper_2603_21055_gb300 import splat
     from paper_2603_21055_gb300.mapping import Mapper
-    buf, n_state, kfs, trgb, tdep, loss = splat.upload_window(mp.scene)
-    m2 = Mapper(mp.scene, kfs=kfs, targets=(trgb, tdep), loss=loss, options=mp.sp.options)
-    for _ in range(3):
-        m2.step_eager()
-        torch.cuda.synchronize()
-        if m2.ensure_capacity():
-            break
-    assert m2.ensure_capacity(), "key capacity could not be met"
-    host_in = buf.cpu().pin_memory()
-    host_out = torch.empty(n_state, dtype=torch.float32, pin_memory=True)
+    # the window as the device-resident run has left it (its iterations have moved the
+    # parameters and with them the work per step), so both measure the same state
+    scene = dataclasses.replace(mp.scene, keyframes=[
+        dataclasses.replace(k, offset=d.offset.cpu().numpy(), rgb=d.rgb.cpu().numpy(), logit=d.logit.cpu().numpy(),
+                            scale=d.scale.cpu().numpy()) for k, d in zip(mp.scene.keyframes, mp.kfs)])
+    win = []
+    for _ in range(2):
+        buf, n_state, kfs, trgb, tdep, loss = splat.upload_window(scene)
+        m = Mapper(scene, kfs=kfs, targets=(trgb, tdep), loss=loss, options=mp.sp.options)
+        for _ in range(3):
+            m.step_eager()
+            torch.cuda.synchronize()
+            if m.ensure_capacity():
+                break
+        assert m.ensure_capacity(), "key capacity could not be met"
+        win.append((buf, m))
+    (buf_a, m_a), (buf_b, m_b) = win
+    host_in = buf_a.cpu().pin_memory()
+    host_out = [torch.empty(n_state, dtype=torch.float32, pin_memory=True) for _ in range(2)]
     bi = host_in.numel() * host_in.element_size()
-    bo = host_out.numel() * host_out.element_size()
+    bo = host_out[0].numel() * host_out[0].element_size()
+    cs = torch.cuda.Stream()
 
-    def body():
-        buf.copy_(host_in, non_blocking=True)
-        m2.step_eager()
-        host_out.copy_(buf[:n_state], non_blocking=True)
+    def pair():
+        main = torch.cuda.current_stream()
+        cs.wait_stream(main)
+        with torch.cuda.stream(cs):
+            host_out[1].copy_(buf_b[:n_state], non_blocking=True)     # the previous step B's result
+            buf_b.copy_(host_in, non_blocking=True)                  # this step B's inputs
+        in_b = torch.cuda.Event()
+        in_b.record(cs)
+        m_a.step_eager()                                             # step A (inputs uploaded before)
+        done_a = torch.cuda.Event()
+        done_a.record(main)
+        with torch.cuda.stream(cs):
+            cs.wait_event(done_a)
+            host_out[0].copy_(buf_a[:n_state], non_blocking=True)     # step A's result
+            buf_a.copy_(host_in, non_blocking=True)                  # the next step A's inputs
+        main.wait_event(in_b)
+        m_b.step_eager()                                             # step B
+        main.wait_stream(cs)
 
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
-        body()
+        buf_a.copy_(host_in, non_blocking=True)
+        pair()
     torch.cuda.current_stream().wait_stream(side)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
-        body()
-    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        pair()
+    pairs = max(1, steps // 2)
+    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(pairs)]
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(pairs)]
     torch.cuda.synchronize()
-    for i in range(steps):
+    for i in range(pairs):
         flush.zero_()
         s_ev[i].record(stream)
         g.replay()
+        if i == pairs - 1:
+            host_out[1].copy_(buf_b[:n_state], non_blocking=True)     # the last step B's result
         e_ev[i].record(stream)
     torch.cuda.synchronize()
-    ms = sum(s.elapsed_time(e) for s, e in zip(s_ev, e_ev)) / steps
-    # eager (no graph) host-driven calls, for reference
+    ms = sum(s.elapsed_time(e) for s, e in zip(s_ev, e_ev)) / (2 * pairs)
+
+    # the copies alone (one upload and one read-back), what the pipeline hides
+    cp = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        buf_a.copy_(host_in, non_blocking=True)
+        host_out[0].copy_(buf_a[:n_state], non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        cp.append(a.elapsed_time(b))
+    copy_ms = sorted(cp)[len(cp) // 2]
+
+    # eager host-driven calls on one stream and one window (copy in, step, copy out), for reference
+    def body():
+        buf_a.copy_(host_in, non_blocking=True)
+        m_a.step_eager()
+        host_out[0].copy_(buf_a[:n_state], non_blocking=True)
+
     t0 = time.perf_counter()
     for i in range(steps):
         body()
@@ -400,6 +505,10 @@ def run_e2e(mp, steps, stream, flush):
     eager_ms = (time.perf_counter() - t0) * 1e3 / steps
     return {"value": round(mp.scene.n_pixels / (ms / 1e3) / 1e6, 2), "unit": UNIT,
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": round(ms, 4),
+            "pipelining": "two device windows; each step's copies overlap the other window's step",
+            "copies_alone_ms_per_step": round(copy_ms, 4),
+            "state": "the window's parameters as the device-resident timed steps left them, uploaded every step",
+            "l2": "flushed (256 MB write) before every pair of steps, outside the timed events; the two steps of a pair use separate windows",
             "eager_wall_ms_per_step": round(eager_ms, 3)}
 
 
