@@ -221,7 +221,7 @@ template <int TW, int TH, int B>
 __device__ __forceinline__ void stage_batch(const Scene &sc, const CompositeArgs &a, const ViewDev &v, uint32_t b0,
                                             uint32_t e, float oxf, float oyf, Staged *buf)
 {
-#pragma unroll 1
+#pragma unroll
     for (int r = 0; r < (B + kFwdThreads - 1) / kFwdThreads; ++r) {
         const int k = r * kFwdThreads + threadIdx.x;
         if (k < B && b0 + k < e) {
