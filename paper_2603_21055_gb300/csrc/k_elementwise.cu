@@ -187,6 +187,7 @@ struct AdamDesc {
     int64_t n;
     float lr;
     int32_t mode;
+    int32_t vec;                    // n % 4 == 0 and all four arrays 16-byte aligned
     int64_t block0;                 // first CTA of this tensor
 };
 
@@ -195,6 +196,17 @@ struct AdamBatch {
     float b1, b2, eps;
     AdamDesc t[SGAD_ADAM_MAX_TENSORS];
 };
+
+// One Adam update of element (p, g, m, v) with the bias corrections' reciprocals.
+__device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, float b1, float b2, float eps, float lr,
+                                         float ic1, float ic2, bool log_mode)
+{
+    const float gi = log_mode ? g * p : g;
+    m = b1 * m + (1.0f - b1) * gi;
+    v = b2 * v + (1.0f - b2) * gi * gi;
+    const float stp = lr * (m * ic1) / (sqrtf(v * ic2) + eps);
+    p = log_mode ? p * expf(-stp) : p - stp;
+}
 
 __global__ void __launch_bounds__(256) k_adam_multi(const __grid_constant__ AdamBatch B, const int32_t *step)
 {
@@ -208,18 +220,32 @@ __global__ void __launch_bounds__(256) k_adam_multi(const __grid_constant__ Adam
     }
     const AdamDesc &d = B.t[lo];
     const float s = (float)(*step + 1);
-    const float c1 = 1.0f - powf(B.b1, s), c2 = 1.0f - powf(B.b2, s);
+    const float ic1 = 1.0f / (1.0f - powf(B.b1, s)), ic2 = 1.0f / (1.0f - powf(B.b2, s));
+    const bool log_mode = d.mode == SGAD_ADAM_LOG;
     const int64_t base = ((int64_t)blockIdx.x - d.block0) * kAdamChunk;
     const int64_t end = base + kAdamChunk < d.n ? base + kAdamChunk : d.n;
+    if (d.vec) {                      // four elements per thread and access
+        for (int64_t i = base + 4 * (int64_t)threadIdx.x; i < end; i += 4 * (int64_t)blockDim.x) {
+            float4 p = *reinterpret_cast<const float4 *>(d.p + i);
+            const float4 g = *reinterpret_cast<const float4 *>(d.g + i);
+            float4 m = *reinterpret_cast<const float4 *>(d.m + i);
+            float4 v = *reinterpret_cast<const float4 *>(d.v + i);
+            adam_one(p.x, g.x, m.x, v.x, B.b1, B.b2, B.eps, d.lr, ic1, ic2, log_mode);
+            adam_one(p.y, g.y, m.y, v.y, B.b1, B.b2, B.eps, d.lr, ic1, ic2, log_mode);
+            adam_one(p.z, g.z, m.z, v.z, B.b1, B.b2, B.eps, d.lr, ic1, ic2, log_mode);
+            adam_one(p.w, g.w, m.w, v.w, B.b1, B.b2, B.eps, d.lr, ic1, ic2, log_mode);
+            *reinterpret_cast<float4 *>(d.m + i) = m;
+            *reinterpret_cast<float4 *>(d.v + i) = v;
+            *reinterpret_cast<float4 *>(d.p + i) = p;
+        }
+        return;
+    }
     for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x) {
-        const float pi = d.p[i];
-        const float gi = d.mode == SGAD_ADAM_LOG ? d.g[i] * pi : d.g[i];
-        const float mi = B.b1 * d.m[i] + (1.0f - B.b1) * gi;
-        const float vi = B.b2 * d.v[i] + (1.0f - B.b2) * gi * gi;
-        d.m[i] = mi;
-        d.v[i] = vi;
-        const float stp = d.lr * (mi / c1) / (sqrtf(vi / c2) + B.eps);
-        d.p[i] = d.mode == SGAD_ADAM_LOG ? expf(logf(pi) - stp) : pi - stp;
+        float p = d.p[i], m = d.m[i], v = d.v[i];
+        adam_one(p, d.g[i], m, v, B.b1, B.b2, B.eps, d.lr, ic1, ic2, log_mode);
+        d.m[i] = m;
+        d.v[i] = v;
+        d.p[i] = p;
     }
 }
 
@@ -243,6 +269,9 @@ cudaError_t launch_adam_multi(int n_t, const sgad_adam_tensor *t, float b1, floa
         d.n = t[i].n;
         d.lr = t[i].lr;
         d.mode = t[i].mode;
+        const uintptr_t al = reinterpret_cast<uintptr_t>(d.p) | reinterpret_cast<uintptr_t>(d.g) |
+                             reinterpret_cast<uintptr_t>(d.m) | reinterpret_cast<uintptr_t>(d.v);
+        d.vec = (d.n % 4 == 0 && (al & 15u) == 0) ? 1 : 0;
         d.block0 = blocks;
         blocks += (t[i].n + kAdamChunk - 1) / kAdamChunk;
     }
