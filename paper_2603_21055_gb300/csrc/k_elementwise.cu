@@ -26,7 +26,9 @@ __global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ Scene 
     const float dir_z = k.R[6] * rx + k.R[7] * ry + k.R[8];
     const float sum = k.depth[j] + k.offset[j];
     const float sgn = sum > 0.0f ? 1.0f : (sum < 0.0f ? -1.0f : 0.0f);
-    const float o = world[g].w1.x;
+    // the opacity as the projection computed it (same expression: bit-identical), from the
+    // 4-byte logit instead of the 32-byte world record
+    const float o = 1.0f / (1.0f + expf(-k.logit[j]));
     k.d_offset[j] = sc.freeze_offset ? 0.0f : sgn * (dir_x * a.x + dir_y * a.y + dir_z * a.z);
     k.d_scale[j] = a.w;
     k.d_logit[j] = b.x * o * (1.0f - o);
@@ -65,6 +67,7 @@ struct LossView {
     uint32_t *nvalid;
     uint32_t hw;
     uint32_t block0;
+    int32_t vec;                    // hw % 4 == 0 and every plane 16-byte aligned
 };
 
 struct LossBatch {
@@ -104,22 +107,59 @@ __global__ void __launch_bounds__(256) k_l1_grad(const __grid_constant__ LossBat
     const uint32_t nv = v.nvalid ? *v.nvalid : 0u;
     const float inv_dep = nv > 0 ? B.wdep / (float)nv : 0.0f;
     float l = 0.f;
-    for (size_t i = base + threadIdx.x; i < end; i += blockDim.x) {
-        const bool keep = !v.alpha || v.alpha[i] > B.min_alpha;     // silhouette mask
+    if (v.vec) {                     // four pixels per thread and access
+        for (size_t i = base + 4 * threadIdx.x; i < end; i += 4 * blockDim.x) {
+            const float4 al = v.alpha ? *reinterpret_cast<const float4 *>(v.alpha + i) : make_float4(1.f, 1.f, 1.f, 1.f);
+            const bool keep[4] = {!v.alpha || al.x > B.min_alpha, !v.alpha || al.y > B.min_alpha,
+                                  !v.alpha || al.z > B.min_alpha, !v.alpha || al.w > B.min_alpha};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float d = v.rgb[c * hw + i] - v.trgb[c * hw + i];
-            if (keep) l += fabsf(d) * inv_rgb;
-            v.drgb[c * hw + i] = keep ? sgnf(d) * inv_rgb : 0.0f;
-        }
-        if (v.ddep) {
-            float gd = 0.f;
-            if (keep && v.tdep && v.tdep[i] > 0.0f && inv_dep > 0.0f) {
-                const float d = v.depth[i] - v.tdep[i];
-                l += fabsf(d) * inv_dep;
-                gd = sgnf(d) * inv_dep;
+            for (int c = 0; c < 3; ++c) {
+                const float4 r = *reinterpret_cast<const float4 *>(v.rgb + c * hw + i);
+                const float4 t = *reinterpret_cast<const float4 *>(v.trgb + c * hw + i);
+                const float d[4] = {r.x - t.x, r.y - t.y, r.z - t.z, r.w - t.w};
+                float gq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (keep[q]) l += fabsf(d[q]) * inv_rgb;
+                    gq[q] = keep[q] ? sgnf(d[q]) * inv_rgb : 0.0f;
+                }
+                *reinterpret_cast<float4 *>(v.drgb + c * hw + i) = make_float4(gq[0], gq[1], gq[2], gq[3]);
             }
-            v.ddep[i] = gd;
+            if (v.ddep) {
+                float gd[4] = {0.f, 0.f, 0.f, 0.f};
+                if (v.tdep && inv_dep > 0.0f) {
+                    const float4 dp = *reinterpret_cast<const float4 *>(v.depth + i);
+                    const float4 td = *reinterpret_cast<const float4 *>(v.tdep + i);
+                    const float dv[4] = {dp.x, dp.y, dp.z, dp.w}, tv[4] = {td.x, td.y, td.z, td.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (keep[q] && tv[q] > 0.0f) {
+                            const float d = dv[q] - tv[q];
+                            l += fabsf(d) * inv_dep;
+                            gd[q] = sgnf(d) * inv_dep;
+                        }
+                }
+                *reinterpret_cast<float4 *>(v.ddep + i) = make_float4(gd[0], gd[1], gd[2], gd[3]);
+            }
+        }
+    } else {
+        for (size_t i = base + threadIdx.x; i < end; i += blockDim.x) {
+            const bool keep = !v.alpha || v.alpha[i] > B.min_alpha;     // silhouette mask
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float d = v.rgb[c * hw + i] - v.trgb[c * hw + i];
+                if (keep) l += fabsf(d) * inv_rgb;
+                v.drgb[c * hw + i] = keep ? sgnf(d) * inv_rgb : 0.0f;
+            }
+            if (v.ddep) {
+                float gd = 0.f;
+                if (keep && v.tdep && v.tdep[i] > 0.0f && inv_dep > 0.0f) {
+                    const float d = v.depth[i] - v.tdep[i];
+                    l += fabsf(d) * inv_dep;
+                    gd = sgnf(d) * inv_dep;
+                }
+                v.ddep[i] = gd;
+            }
         }
     }
     if (loss) {
@@ -153,6 +193,11 @@ void launch_l1_batch(int n, const float *const *rgb, const float *const *depth, 
         v.ddep = ddep ? ddep[i] : nullptr;
         v.nvalid = use_depth ? nvalid + i : nullptr;
         v.hw = hw[i];
+        uintptr_t al = reinterpret_cast<uintptr_t>(v.rgb) | reinterpret_cast<uintptr_t>(v.trgb) |
+                       reinterpret_cast<uintptr_t>(v.drgb) | reinterpret_cast<uintptr_t>(v.alpha) |
+                       reinterpret_cast<uintptr_t>(v.ddep);
+        if (v.tdep) al |= reinterpret_cast<uintptr_t>(v.depth) | reinterpret_cast<uintptr_t>(v.tdep);
+        v.vec = (hw[i] % 4 == 0 && (al & 15u) == 0) ? 1 : 0;
         v.block0 = blocks;
         blocks += (hw[i] + kLossChunk - 1) / kLossChunk;
     }
