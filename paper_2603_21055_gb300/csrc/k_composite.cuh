@@ -480,6 +480,28 @@ __device__ __forceinline__ void warp_reduce_scatter10x2(float (&v)[10], float (&
     tu = u[0] + __shfl_xor_sync(kFull, u[0], 1);
 }
 
+// Projection of a Gaussian for the chain rule: the same quantities as project() with a
+// fast reciprocal of the depth (the gradients are compared with tolerances; the
+// decisions of the walk use project()).
+__device__ __forceinline__ Proj project_chain(const float4 w0, const ViewDev &v)
+{
+    Proj p;
+    p.tx = fmaf(v.R[0], w0.x, fmaf(v.R[1], w0.y, fmaf(v.R[2], w0.z, v.t[0])));
+    p.ty = fmaf(v.R[3], w0.x, fmaf(v.R[4], w0.y, fmaf(v.R[5], w0.z, v.t[1])));
+    p.tz = fmaf(v.R[6], w0.x, fmaf(v.R[7], w0.y, fmaf(v.R[8], w0.z, v.t[2])));
+    const float iz = __fdividef(1.0f, p.tz);
+    const float ux = p.tx * iz, uy = p.ty * iz;
+    p.px = fmaf(v.fx, ux, v.cx);
+    p.py = fmaf(v.fy, uy, v.cy);
+    const float j00 = v.fx * iz, j02 = -j00 * ux;
+    const float j11 = v.fy * iz, j12 = -j11 * uy;
+    const float s2 = w0.w * w0.w;
+    p.cxx = fmaf(s2, fmaf(j00, j00, j02 * j02), kDilation);
+    p.cxy = s2 * (j02 * j12);
+    p.cyy = fmaf(s2, fmaf(j11, j11, j12 * j12), kDilation);
+    return p;
+}
+
 // Chain rule of one staged Gaussian from its ten accumulated pair moments (colour (3),
 // depth, G, G dx, G dy, G dx^2, G dx dy, G dy^2 with G = dL/dpower) down to d mu, d s,
 // d opacity and d colour, added to its accumulator.
@@ -488,17 +510,17 @@ __device__ __forceinline__ float3 chain_and_accumulate(const float *A, const Sta
 {
     const float ca = st.b.x, cbb = st.b.y, cc = st.b.z, o = st.b.w;
     const float G = A[4], Gx = A[5], Gy = A[6], Gxx = A[7], Gxy = A[8], Gyy = A[9];
-    const float d_o = G / o;
+    const float d_o = __fdividef(G, o);
     const float da = -0.5f * Gxx, db = -Gxy, dc = -0.5f * Gyy;
     const float dpx = -(ca * Gx + cbb * Gy), dpy = -(cbb * Gx + cc * Gy);
     // conic (a, b, c) = (w, -y, x) / det of Sigma_2D = [[x, y], [y, w]]
     const float x = pr.cxx, y = pr.cxy, wv = pr.cyy;
-    const float det = x * wv - y * y, id2 = 1.0f / (det * det);
+    const float det = x * wv - y * y, id2 = __fdividef(1.0f, det * det);
     const float gx = (-wv * wv * da + y * wv * db - y * y * dc) * id2;
     const float gy = (2.0f * y * wv * da - (det + 2.0f * y * y) * db + 2.0f * x * y * dc) * id2;
     const float gw = (-y * y * da + y * x * db - x * x * dc) * id2;
     // Sigma_2D = s^2 J J^T + 0.3 I
-    const float tz = pr.tz, iz = 1.0f / tz, iz2 = iz * iz;
+    const float tz = pr.tz, iz = __fdividef(1.0f, tz), iz2 = iz * iz;
     const float j00 = v.fx * iz, j02 = -v.fx * pr.tx * iz2;
     const float j11 = v.fy * iz, j12 = -v.fy * pr.ty * iz2;
     const float s2 = s_ * s_;
@@ -719,7 +741,7 @@ __device__ __forceinline__ void bwd_tile(const Scene &sc, const CompositeArgs &a
                 for (int q = 0; q < 10; ++q) any |= A[q] != 0.f;
                 if (any) {
                     w0 = a.world[sg[k]].w0;
-                    gt = chain_and_accumulate(A, sm[k], project(w0, v), w0.w, v, a.gacc, sg[k]);
+                    gt = chain_and_accumulate(A, sm[k], project_chain(w0, v), w0.w, v, a.gacc, sg[k]);
                 }
             }
             if (POSE && v.d_pose) pose_reduce(gt, w0, s_pose);
@@ -883,7 +905,7 @@ __device__ __forceinline__ void bwdp_tile(const Scene &sc, const CompositeArgs &
                 for (int q = 0; q < 10; ++q) any |= A[q] != 0.f;
                 if (any) {
                     w0 = a.world[sg[k]].w0;
-                    gt = chain_and_accumulate(A, sm[k], project(w0, v), w0.w, v, a.gacc, sg[k]);
+                    gt = chain_and_accumulate(A, sm[k], project_chain(w0, v), w0.w, v, a.gacc, sg[k]);
                 }
             }
             if (POSE && v.d_pose) pose_reduce(gt, w0, s_pose);
@@ -1013,7 +1035,7 @@ __device__ __forceinline__ void bwdl_reduce(const ViewDev &v, const CompositeArg
     st.a = S.sa[lane];
     st.b = S.sb[lane];
     st.c = S.sc[lane];
-    const float3 gt = chain_and_accumulate(A, st, project(w0, v), w0.w, v, a.gacc, g);
+    const float3 gt = chain_and_accumulate(A, st, project_chain(w0, v), w0.w, v, a.gacc, g);
     if (POSE) {
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
