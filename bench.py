@@ -401,71 +401,25 @@ def split_of(sp):
 
 
 def run_e2e(mp, steps, stream, flush):
-    """Same metric through the public API with host buffers: the window's keyframe planes,
-    targets and loss slot live in one pinned host buffer laid out like the device copy of
-    splat.upload_window; every step copies it in (one copy), runs the iteration on a
-    Mapper over those device views (the tuned options of `mp`), and reads the updated
-    parameters and the loss back (one copy). Two device windows alternate so that a
-    step's copies overlap the other window's iteration: one CUDA graph replay runs two
-    steps (A, B) on the compute stream while a copy stream reads back the previous B,
-    uploads B, then (after A) reads back A and uploads the next A; the replay ends when
-    the copies have. Every step's upload and read-back are inside the timed region (the
-    last read-back of B after the last replay, inside the last timing)."""
+    """Same metric through the public API with host buffers: mapping.StreamedWindows
+    uploads the window from pinned host memory every step and reads the updated
+    parameters and the loss back (one copy each way), two device copies of the window
+    alternating so that a step's copies overlap the other copy's step; one CUDA graph
+    replay runs two steps. The uploaded window is the one the device-resident run has left
+    (its iterations have moved the parameters and with them the work per step), so both
+    measure the same state. Every step's upload and read-back are inside the timed region
+    (the last read-back after the last replay, inside the last timing)."""
     import dataclasses
     import torch
-    from paper_2603_21055_gb300 import splat
-    from paper_2603_21055_gb300.mapping import Mapper
-    # the window as the device-resident run has left it (its iterations have moved the
-    # parameters and with them the work per step), so both measure the same state
+    from paper_2603_21055_gb300.mapping import StreamedWindows
     scene = dataclasses.replace(mp.scene, keyframes=[
         dataclasses.replace(k, offset=d.offset.cpu().numpy(), rgb=d.rgb.cpu().numpy(), logit=d.logit.cpu().numpy(),
                             scale=d.scale.cpu().numpy()) for k, d in zip(mp.scene.keyframes, mp.kfs)])
-    win = []
-    for _ in range(2):
-        buf, n_state, kfs, trgb, tdep, loss = splat.upload_window(scene)
-        m = Mapper(scene, kfs=kfs, targets=(trgb, tdep), loss=loss, options=mp.sp.options)
-        for _ in range(3):
-            m.step_eager()
-            torch.cuda.synchronize()
-            if m.ensure_capacity():
-                break
-        assert m.ensure_capacity(), "key capacity could not be met"
-        win.append((buf, m))
-    (buf_a, m_a), (buf_b, m_b) = win
-    host_in = buf_a.cpu().pin_memory()
-    host_out = [torch.empty(n_state, dtype=torch.float32, pin_memory=True) for _ in range(2)]
-    bi = host_in.numel() * host_in.element_size()
-    bo = host_out[0].numel() * host_out[0].element_size()
-    cs = torch.cuda.Stream()
-
-    def pair():
-        main = torch.cuda.current_stream()
-        cs.wait_stream(main)
-        with torch.cuda.stream(cs):
-            host_out[1].copy_(buf_b[:n_state], non_blocking=True)     # the previous step B's result
-            buf_b.copy_(host_in, non_blocking=True)                  # this step B's inputs
-        in_b = torch.cuda.Event()
-        in_b.record(cs)
-        m_a.step_eager()                                             # step A (inputs uploaded before)
-        done_a = torch.cuda.Event()
-        done_a.record(main)
-        with torch.cuda.stream(cs):
-            cs.wait_event(done_a)
-            host_out[0].copy_(buf_a[:n_state], non_blocking=True)     # step A's result
-            buf_a.copy_(host_in, non_blocking=True)                  # the next step A's inputs
-        main.wait_event(in_b)
-        m_b.step_eager()                                             # step B
-        main.wait_stream(cs)
-
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        buf_a.copy_(host_in, non_blocking=True)
-        pair()
-    torch.cuda.current_stream().wait_stream(side)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        pair()
+    sw = StreamedWindows(scene, options=mp.sp.options)
+    assert sw.ensure_capacity(), "key capacity could not be met"
+    sw.capture()
+    bi = sw.host_in.numel() * sw.host_in.element_size()
+    bo = sw.host_out[0].numel() * sw.host_out[0].element_size()
     pairs = max(1, steps // 2)
     s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(pairs)]
     e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(pairs)]
@@ -473,39 +427,37 @@ def run_e2e(mp, steps, stream, flush):
     for i in range(pairs):
         flush.zero_()
         s_ev[i].record(stream)
-        g.replay()
+        sw.replay()
         if i == pairs - 1:
-            host_out[1].copy_(buf_b[:n_state], non_blocking=True)     # the last step B's result
+            sw.finish()
         e_ev[i].record(stream)
     torch.cuda.synchronize()
     ms = sum(s.elapsed_time(e) for s, e in zip(s_ev, e_ev)) / (2 * pairs)
 
     # the copies alone (one upload and one read-back), what the pipeline hides
+    buf_a, m_a = sw.windows[0]
     cp = []
     for _ in range(5):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        buf_a.copy_(host_in, non_blocking=True)
-        host_out[0].copy_(buf_a[:n_state], non_blocking=True)
+        buf_a.copy_(sw.host_in, non_blocking=True)
+        sw.host_out[0].copy_(buf_a[:sw.n_state], non_blocking=True)
         b.record(stream)
         torch.cuda.synchronize()
         cp.append(a.elapsed_time(b))
     copy_ms = sorted(cp)[len(cp) // 2]
 
     # eager host-driven calls on one stream and one window (copy in, step, copy out), for reference
-    def body():
-        buf_a.copy_(host_in, non_blocking=True)
-        m_a.step_eager()
-        host_out[0].copy_(buf_a[:n_state], non_blocking=True)
-
     t0 = time.perf_counter()
     for i in range(steps):
-        body()
+        buf_a.copy_(sw.host_in, non_blocking=True)
+        m_a.step_eager()
+        sw.host_out[0].copy_(buf_a[:sw.n_state], non_blocking=True)
     torch.cuda.synchronize()
     eager_ms = (time.perf_counter() - t0) * 1e3 / steps
     return {"value": round(mp.scene.n_pixels / (ms / 1e3) / 1e6, 2), "unit": UNIT,
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": round(ms, 4),
-            "pipelining": "two device windows; each step's copies overlap the other window's step",
+            "pipelining": "mapping.StreamedWindows: two device windows; each step's copies overlap the other window's step",
             "copies_alone_ms_per_step": round(copy_ms, 4),
             "state": "the window's parameters as the device-resident timed steps left them, uploaded every step",
             "l2": "flushed (256 MB write) before every pair of steps, outside the timed events; the two steps of a pair use separate windows",

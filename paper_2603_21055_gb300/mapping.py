@@ -164,3 +164,93 @@ class Mapper:
             mse = torch.mean((im["rgb"].clamp(0, 1) - t) ** 2).item()
             vals.append(10.0 * math.log10(1.0 / max(mse, 1e-12)))
         return sum(vals) / len(vals)
+
+
+class StreamedWindows:
+    """Mapping iterations on a window held in pinned host memory: every iteration uploads
+    the window (keyframe planes, targets, loss slot: one copy, the layout of
+    splat.upload_window) and reads the updated parameters and the loss back (one copy).
+    Two device copies of the window alternate, so that one iteration's copies run on a
+    copy stream while the other copy's iteration runs; `replay()` runs two iterations (A,
+    then B) as one CUDA graph:
+        copy stream:    read back B (previous)  upload B  | read back A  upload A (next)
+        compute stream: iteration A                       | iteration B
+    Every iteration's upload precedes it and its read-back follows it; `finish()` reads
+    back the last B. `host_in` holds the window every iteration starts from;
+    `host_out[0]`, `host_out[1]` the state after the last A and B iterations."""
+
+    def __init__(self, scene, options=None, slack: float = 1.3):
+        self.windows = []
+        for _ in range(2):
+            buf, n_state, kfs, trgb, tdep, loss = splat.upload_window(scene)
+            m = Mapper(scene, kfs=kfs, targets=(trgb, tdep), loss=loss, options=options, slack=slack)
+            self.windows.append((buf, m))
+        self.n_state = n_state
+        self.host_in = self.windows[0][0].cpu().pin_memory()
+        self.host_out = [torch.empty(n_state, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+        self.copy_stream = torch.cuda.Stream()
+        self.graph: Optional[torch.cuda.CUDAGraph] = None
+
+    @property
+    def mappers(self):
+        return [m for _, m in self.windows]
+
+    def ensure_capacity(self, tries: int = 3) -> bool:
+        """Eager iterations on both copies until their key capacity suffices (from the
+        current device contents); drops a captured graph."""
+        ok = True
+        for buf, m in self.windows:
+            for _ in range(tries):
+                m.step_eager()
+                torch.cuda.synchronize()
+                if m.ensure_capacity():
+                    break
+            ok = ok and m.ensure_capacity()
+        self.graph = None
+        return ok
+
+    def _pair(self):
+        (buf_a, m_a), (buf_b, m_b) = self.windows
+        n, cs = self.n_state, self.copy_stream
+        main = torch.cuda.current_stream()
+        cs.wait_stream(main)
+        with torch.cuda.stream(cs):
+            self.host_out[1].copy_(buf_b[:n], non_blocking=True)     # the previous iteration B's result
+            buf_b.copy_(self.host_in, non_blocking=True)             # this iteration B's inputs
+        in_b = torch.cuda.Event()
+        in_b.record(cs)
+        m_a.step_eager()                                             # iteration A (inputs uploaded before)
+        done_a = torch.cuda.Event()
+        done_a.record(main)
+        with torch.cuda.stream(cs):
+            cs.wait_event(done_a)
+            self.host_out[0].copy_(buf_a[:n], non_blocking=True)     # iteration A's result
+            buf_a.copy_(self.host_in, non_blocking=True)             # the next iteration A's inputs
+        main.wait_event(in_b)
+        m_b.step_eager()                                             # iteration B
+        main.wait_stream(cs)
+
+    def capture(self):
+        """Upload A's first inputs, run one pair eagerly on a side stream, then record the
+        pair as a CUDA graph."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.windows[0][0].copy_(self.host_in, non_blocking=True)
+            self._pair()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._pair()
+        self.graph = g
+
+    def replay(self):
+        """Two iterations (A and B) with their copies."""
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def finish(self):
+        """Read back the last iteration B's result (on the current stream)."""
+        buf_b = self.windows[1][0]
+        self.host_out[1].copy_(buf_b[:self.n_state], non_blocking=True)

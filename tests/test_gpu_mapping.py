@@ -176,3 +176,38 @@ def test_packed_window_matches_separate_tensors(scene1):
     host = buf[:n_state].cpu()                                   # the prefix is the updated state
     off = (m2.kfs[0].rgb.data_ptr() - buf.data_ptr()) // 4
     assert torch.equal(host[off:off + m2.kfs[0].rgb.numel()], m2.kfs[0].rgb.flatten().cpu())
+
+
+def test_streamed_windows_upload_compute_and_read_back(scene1):
+    """mapping.StreamedWindows (the end-to-end path): after a replay of its two-iteration
+    graph and the final read-back, both host results are one iteration from the pinned
+    host window: their loss slot equals the loss of the host window's parameters, both
+    copies agree (same history, up to the order of float atomics), and every parameter
+    moved by at most a few Adam steps of its learning rate from the uploaded value."""
+    import torch
+    from paper_2603_21055_gb300 import splat
+    from paper_2603_21055_gb300.mapping import LR, Mapper, StreamedWindows
+    sw = StreamedWindows(scene1)
+    assert sw.ensure_capacity()
+    sw.replay()
+    sw.finish()
+    torch.cuda.synchronize()
+    n = sw.n_state
+    host_in = sw.host_in[:n].clone()
+    outs = [h.clone() for h in sw.host_out]
+    # the loss of the uploaded parameters, from a separate window over the same host data
+    buf, n_state, kfs, trgb, tdep, loss = splat.upload_window(scene1)
+    buf.copy_(sw.host_in.cuda())
+    ref = Mapper(scene1, kfs=kfs, targets=(trgb, tdep), loss=loss, options=sw.mappers[0].sp.options)
+    ref.eval_loss()
+    torch.cuda.synchronize()
+    l_ref = float(ref.loss)
+    for o in outs:
+        assert abs(float(o[n - 64]) - l_ref) <= 1e-5 * abs(l_ref), (float(o[n - 64]), l_ref)
+    close = torch.isclose(outs[0], outs[1], rtol=1e-4, atol=1e-7)
+    assert float(close.float().mean()) >= 0.999
+    lr_max = max(LR.values())
+    d = (outs[0][:n - 64] - host_in[:n - 64]).abs()
+    assert float(d.max()) > 0.0                     # the iteration changed the parameters
+    # scale is stored as s = exp(p): |ds| <= s |dp| with s < 1 m here
+    assert float(d.max()) <= 5 * lr_max, float(d.max())
