@@ -1046,7 +1046,7 @@ __device__ __forceinline__ void bwdl_reduce(const ViewDev &v, const CompositeArg
     }
 }
 
-template <int TW, int TH, bool POSE>
+template <int TW, int TH, bool POSE, bool PLAIN>
 __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &a, int tile, int wb, LocalWarpSmem &S,
                                           int lane)
 {
@@ -1189,9 +1189,11 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
                         const float rom = __fdividef(1.0f, om);     // om >= 0.01: fast reciprocal
                         const float Ti = T * rom;
                         const float cg = st.c.x * gr + st.c.y * gg + st.c.z * gb + st.c.w * gD;
-                        const float dal = Ti * ((cg - Sg) + (1.0f - SA) * gA) - (Tf * rom) * bgdot;
+                        // PLAIN: no alpha gradient and no background (the terms are zero)
+                        const float dal = PLAIN ? Ti * (cg - Sg)
+                                                : Ti * ((cg - Sg) + (1.0f - SA) * gA) - (Tf * rom) * bgdot;
                         Sg = alpha * cg + om * Sg;
-                        SA = alpha + om * SA;
+                        if (!PLAIN) SA = alpha + om * SA;
                         const float G = (st.b.w * ep > kAlphaCap) ? 0.f : dal * alpha;
                         S.pairs[S.base[j] - b0 + __popc(S.row[j] & lane_mask_lt(lane))] = make_float2(G, alpha * Ti);
                         T = Ti;
@@ -1218,7 +1220,7 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
     }
 }
 
-template <int TW, int TH, bool POSE>
+template <int TW, int TH, bool POSE, bool PLAIN>
 __global__ void __launch_bounds__(kLocalThreads, SGAD_BWDL_MINBLOCKS)
     k_composite_bwdl(const __grid_constant__ Scene sc, const CompositeArgs a)
 {
@@ -1234,7 +1236,7 @@ __global__ void __launch_bounds__(kLocalThreads, SGAD_BWDL_MINBLOCKS)
         u = __shfl_sync(kFull, u, 0);
         if (u >= n_units) break;
         const int tile = a.order ? (int)a.order[u >> 3] : a.tile0 + (int)(u >> 3);
-        bwdl_unit<TW, TH, POSE>(sc, a, tile, (int)(u & 7u), S, lane);
+        bwdl_unit<TW, TH, POSE, PLAIN>(sc, a, tile, (int)(u & 7u), S, lane);
     }
 }
 
@@ -1329,22 +1331,30 @@ cudaError_t launch_bwdl(const Scene &sc, const CompositeArgs &a, int grid_blocks
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !configured[dev]) {
-        e = cudaFuncSetAttribute(k_composite_bwdl<TW, TH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_composite_bwdl<TW, TH, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kLocalSmemBytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_composite_bwdl<TW, TH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_composite_bwdl<TW, TH, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kLocalSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_composite_bwdl<TW, TH, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kLocalSmemBytes);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) configured[dev] = 1;
     }
     if (occupancy)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_composite_bwdl<TW, TH, false>, kLocalThreads,
-                                                             kLocalSmemBytes);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, k_composite_bwdl<TW, TH, false, false>,
+                                                             kLocalThreads, kLocalSmemBytes);
     if (grid_blocks <= 0) return cudaSuccess;
+    // without an alpha gradient and with a black background the walk drops those terms
+    bool plain = sc.bg[0] == 0.0f && sc.bg[1] == 0.0f && sc.bg[2] == 0.0f;
+    for (int i = 0; i < sc.n_views && plain; ++i) plain = sc.view[i].g_alpha == nullptr;
     if (a.pose)
-        k_composite_bwdl<TW, TH, true><<<grid_blocks, kLocalThreads, kLocalSmemBytes, st>>>(sc, a);
+        k_composite_bwdl<TW, TH, true, false><<<grid_blocks, kLocalThreads, kLocalSmemBytes, st>>>(sc, a);
+    else if (plain)
+        k_composite_bwdl<TW, TH, false, true><<<grid_blocks, kLocalThreads, kLocalSmemBytes, st>>>(sc, a);
     else
-        k_composite_bwdl<TW, TH, false><<<grid_blocks, kLocalThreads, kLocalSmemBytes, st>>>(sc, a);
+        k_composite_bwdl<TW, TH, false, false><<<grid_blocks, kLocalThreads, kLocalSmemBytes, st>>>(sc, a);
     return cudaGetLastError();
 }
 
