@@ -253,6 +253,7 @@ __device__ __forceinline__ int2 fwd_pixel(int ox, int oy, int warp, int lane)
 // 1/255 box, from the tile masks staged with it), a bit transpose gives every lane the
 // entries whose box covers its pixel, and each lane not yet done walks its own entries in
 // order. Lanes are busy only with (pixel, entry) pairs inside the entry's box.
+template <bool CONTRIB>
 __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0, uint32_t s, int tile,
                                            const CompositeArgs &a, int csh, int rsh, float qx, float qy, int lane,
                                            FwdPixel &px, bool &warp_done, uint32_t &n_pairs, uint32_t &n_evals,
@@ -293,7 +294,7 @@ __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0
             }
         }
         n_pairs += __popc(bits);
-        if (a.contrib) a.contrib[contrib_base(a, tile, s) + (size_t)((b0 - s + c0) >> 5) * 256 + threadIdx.x] = bits;
+        if (CONTRIB) a.contrib[contrib_base(a, tile, s) + (size_t)((b0 - s + c0) >> 5) * 256 + threadIdx.x] = bits;
         if (wmw) {
             const uint32_t wbits = __reduce_or_sync(kFull, bits);
             if (lane == 0) wmw[(b0 - s + c0) >> 2] = wbits;        // chunk (b0 - s + c0) / 32, 8 words each
@@ -305,7 +306,7 @@ __device__ __forceinline__ void walk_batch(const Staged *sm, int nb, uint32_t b0
     }
 }
 
-template <int TW, int TH, int B>
+template <int TW, int TH, int B, bool CONTRIB>
 __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a, int tile, Staged *sm,
                                          uint32_t &n_pairs, uint32_t &n_evals)
 {
@@ -332,7 +333,7 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
         __syncthreads();
         const int nb = (int)min((uint32_t)B, e - b0);
         if (!warp_done)
-            walk_batch(sm, nb, b0, s, tile, a, 8 * (warp % (TW / 8)), 4 * (warp / (TW / 8)), qx, qy, lane, st,
+            walk_batch<CONTRIB>(sm, nb, b0, s, tile, a, 8 * (warp % (TW / 8)), 4 * (warp / (TW / 8)), qx, qy, lane, st,
                        warp_done, n_pairs, n_evals, wmw);
     }
     if (inside) {
@@ -347,7 +348,7 @@ __device__ __forceinline__ void fwd_tile(const Scene &sc, const CompositeArgs &a
     }
 }
 
-template <int TW, int TH, int B>
+template <int TW, int TH, int B, bool CONTRIB>
 __global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks<B>())
     k_composite_fwd(const __grid_constant__ Scene sc, const CompositeArgs a)
 {
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks<B>())
     for (;;) {
         const int tile = next_tile(sc, a, first, &s_tile);
         if (tile < 0) break;
-        fwd_tile<TW, TH, B>(sc, a, tile, sm, n_pairs, n_evals);
+        fwd_tile<TW, TH, B, CONTRIB>(sc, a, tile, sm, n_pairs, n_evals);
     }
     const uint32_t wp = __reduce_add_sync(kFull, n_pairs), we = __reduce_add_sync(kFull, n_evals);
     if ((threadIdx.x & 31) == 0 && we) {
@@ -1261,12 +1262,18 @@ cudaError_t launch_composite_tb(bool fwd, const Scene &sc, const CompositeArgs &
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         if (dev < 0 || dev >= 64 || !configured[dev]) {
-            e = cudaFuncSetAttribute(k_composite_fwd<TW, TH, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_composite_fwd<TW, TH, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_composite_fwd<TW, TH, B, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             if (dev >= 0 && dev < 64) configured[dev] = 1;
         }
-        k_composite_fwd<TW, TH, B><<<grid_blocks, kFwdThreads, smem, st>>>(sc, a);
+        if (a.contrib)   // the pair-parallel backward's per-pixel contribution words
+            k_composite_fwd<TW, TH, B, true><<<grid_blocks, kFwdThreads, smem, st>>>(sc, a);
+        else
+            k_composite_fwd<TW, TH, B, false><<<grid_blocks, kFwdThreads, smem, st>>>(sc, a);
     } else if constexpr (B <= 512) {
         constexpr size_t smem = bwd_smem_bytes<B>();
         static int configured[64] = {};
@@ -1298,10 +1305,10 @@ cudaError_t occupancy_tb(bool fwd, int *blocks_per_sm)
 {
     if (fwd) {
         constexpr size_t smem = fwd_smem_bytes<B>();
-        const cudaError_t e = cudaFuncSetAttribute(k_composite_fwd<TW, TH, B>,
+        const cudaError_t e = cudaFuncSetAttribute(k_composite_fwd<TW, TH, B, false>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_composite_fwd<TW, TH, B>, kFwdThreads,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_composite_fwd<TW, TH, B, false>, kFwdThreads,
                                                              smem);
     }
     if constexpr (B <= 512)
