@@ -312,6 +312,8 @@ def run_ours(args):
         mp.sp.options.bwd_algorithm, "k_composite_bwd")
     fp32 = measured_fp32_tflops()
     roof = roofline(stages, stats, scene, peaks, peak_src, bwd_kernel=bwd_kernel, fp32=fp32)
+    stage_roofs = {k: roofline(stages, stats, scene, peaks, peak_src, bwd_kernel=bwd_kernel, fp32=fp32, name=k)
+                   for k in stages}
     path = path_roofline(stages, stats, scene, peaks, fp32)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -328,6 +330,7 @@ def run_ours(args):
                    "parallelism": "independent keyframe window per GPU" if world > 1 else "1 GPU"},
         "stage_ms": {k: round(v, 4) for k, v in stages.items()},
         "roofline": roof,
+        "stage_rooflines": stage_roofs,
         "path_roofline": path,
         "fp32_peak": fp32,
         "ssim_term": ssim,
@@ -508,13 +511,15 @@ def path_roofline(stages, stats, scene, peaks, fp32):
             "frac": round(t_roof / t_ms, 4), "fwd_bwd_mpix_s": round(scene.n_pixels / (t_ms / 1e3) / 1e6, 2)}
 
 
-def roofline(stages, stats, scene, peaks, src, bwd_kernel="k_composite_bwdp", fp32=None):
-    """Roofline of the dominant kernel. The compositing kernels are bound by FP32
-    arithmetic (peak = the device's FP32 FMA throughput measured by the library's own
-    probe, else SMs x 128 FP32 lanes x 2 flop x max SM clock); the rest by HBM."""
+def roofline(stages, stats, scene, peaks, src, bwd_kernel="k_composite_bwdp", fp32=None, name=None):
+    """Roofline of one stage's kernel (default: the dominant one). The compositing kernels
+    are bound by FP32 arithmetic (peak = the device's FP32 FMA throughput measured by the
+    library's own probe, else SMs x 128 FP32 lanes x 2 flop x max SM clock); the rest by
+    HBM."""
     if not stages:
         return None
-    name = max(stages, key=stages.get)
+    if name is None:
+        name = max(stages, key=stages.get)
     ms = stages[name]
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
