@@ -309,13 +309,19 @@ __device__ __forceinline__ void stage(const Proj &p, const float4 w1, float z, S
     s.b = make_float4(__fmul_rn(p.cyy, id), -__fmul_rn(p.cxy, id), __fmul_rn(p.cxx, id), o);
     s.c = make_float4(w1.y, w1.z, w1.w, z);
     // alpha >= 1/255 needs d^T Sigma^-1 d <= 2 ln(255 o); its bounding box has half
-    // extents sqrt(2 ln(255 o) Sigma_ii). Padded so FP32 rounding never cuts a pixel.
-    const float l = logf(255.0f * o);
+    // extents sqrt(2 ln(255 o) Sigma_ii). The box only prunes evaluations (the alpha test
+    // decides), so it may be larger than needed but never smaller: the fast logarithm is
+    // raised by 2e-6, above its documented error for arguments up to 255 (2^-21.41
+    // absolute on [0.5, 2], 3 ulp of a result below 5.6 elsewhere), and the fast square
+    // roots (x rsqrt(x), a few ulp) sit inside the 0.01-pixel pad that also covers the
+    // FP32 rounding of the conic.
+    const float l = __logf(255.0f * o) + 2e-6f;
     if (!(l > 0.0f)) {
         s.a = make_float4(p.px, p.py, -1.0f, -1.0f);
     } else {
         const float e = 2.0f * l * 1.0001f;
-        s.a = make_float4(p.px, p.py, sqrtf(e * p.cxx) + 0.01f, sqrtf(e * p.cyy) + 0.01f);
+        const float ex = e * p.cxx, ey = e * p.cyy;     // > 0: cxx, cyy >= the dilation
+        s.a = make_float4(p.px, p.py, ex * rsqrtf(ex) + 0.01f, ey * rsqrtf(ey) + 0.01f);
     }
 }
 
