@@ -12,8 +12,9 @@
 // the power of two at or above its entry count (at most 4,096), picks each entry's
 // bucket; a shared-memory atomic per entry gives both the bucket counts and each entry's
 // slot in its bucket; after a scan of the counts every entry is written to its bucket,
-// and each bucket is put in exact order (depth, then index) by one thread's insertion
-// sort. Buckets are small because the bucket width follows the tile's own depth range
+// and then to its place in the list: the bucket's start plus the number of the bucket's
+// entries below it in exact order (depth, then index), one thread per bucketed position.
+// Buckets are small because the bucket width follows the tile's own depth range
 // (room workload: at most ~20 entries). A tile with a bucket of more than kBucketMax
 // entries (many equal or nearly equal depths), or with more entries than the bucket
 // path holds, is listed and sorted afterwards by the exact radix sort below.
@@ -469,22 +470,19 @@ __global__ void __launch_bounds__(kBucketThreads, 3)
         }
     }
     __syncthreads();
-    // each bucket in exact 64-bit order (depth, then index)
-    for (int b = threadIdx.x; b < nbins; b += kBucketThreads) {
-        const int lo = (int)start[b], hi = b + 1 < nbins ? (int)start[b + 1] : n;
-        for (int i = lo + 1; i < hi; ++i) {
-            const uint64_t x = ks[i];
-            int j = i - 1;
-            while (j >= lo && ks[j] > x) {
-                ks[j + 1] = ks[j];
-                --j;
-            }
-            ks[j + 1] = x;
-        }
-    }
-    __syncthreads();
+    // exact 64-bit order (depth, then index) inside each bucket: an entry's place is its
+    // bucket's start plus the number of the bucket's entries below it (the entries of a
+    // tile are distinct, so the places are too), written straight to the list. Threads
+    // take consecutive bucketed positions, so the lanes of one bucket read the same words.
     uint64_t *out = entries + s0;
-    for (int i = threadIdx.x; i < n; i += kBucketThreads) out[i] = ks[i];
+    for (int i = threadIdx.x; i < n; i += kBucketThreads) {
+        const uint64_t key = ks[i];
+        const uint32_t b = ((uint32_t)(key >> 32) - mn) >> shift;
+        const int lo = (int)start[b], hi = b + 1 < (uint32_t)nbins ? (int)start[b + 1] : n;
+        int r = lo;
+        for (int j = lo; j < hi; ++j) r += ks[j] < key ? 1 : 0;
+        out[r] = key;
+    }
 }
 
 template <int kPer>
