@@ -1185,7 +1185,11 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
                     st.b = S.sb[j];
                     st.c = S.sc[j];
                     float dx, dy, ep, alpha;
-                    if (gauss_alpha(st, qx, qy, dx, dy, ep, alpha)) {
+                    const bool hit = gauss_alpha(st, qx, qy, dx, dy, ep, alpha);
+                    // evaluated for every candidate and kept by selects (no branch): a
+                    // candidate that misses writes its own pair slot, which the moment
+                    // loop never reads (it takes the hits only)
+                    {
                         const float om = __fsub_rn(1.0f, alpha);
                         const float rom = __fdividef(1.0f, om);     // om >= 0.01: fast reciprocal
                         const float Ti = T * rom;
@@ -1193,12 +1197,12 @@ __device__ __forceinline__ void bwdl_unit(const Scene &sc, const CompositeArgs &
                         // PLAIN: no alpha gradient and no background (the terms are zero)
                         const float dal = PLAIN ? Ti * (cg - Sg)
                                                 : Ti * ((cg - Sg) + (1.0f - SA) * gA) - (Tf * rom) * bgdot;
-                        Sg = alpha * cg + om * Sg;
-                        if (!PLAIN) SA = alpha + om * SA;
+                        Sg = hit ? alpha * cg + om * Sg : Sg;
+                        if (!PLAIN) SA = hit ? alpha + om * SA : SA;
                         const float G = (st.b.w * ep > kAlphaCap) ? 0.f : dal * alpha;
                         S.pairs[S.base[j] - b0 + __popc(S.row[j] & lane_mask_lt(lane))] = make_float2(G, alpha * Ti);
-                        T = Ti;
-                        done |= 1u << j;
+                        T = hit ? Ti : T;
+                        done |= (hit ? 1u : 0u) << j;
                     }
                 }
             }

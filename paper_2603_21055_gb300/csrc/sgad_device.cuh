@@ -335,11 +335,13 @@ __device__ __forceinline__ bool gauss_alpha(const Staged &s, float qx, float qy,
     dy = __fsub_rn(s.a.y, qy);
     const float quad = __fmaf_rn(s.b.x, __fmul_rn(dx, dx), __fmul_rn(s.b.z, __fmul_rn(dy, dy)));
     const float power = __fsub_rn(__fmul_rn(-0.5f, quad), __fmul_rn(s.b.y, __fmul_rn(dx, dy)));
-    if (power > 0.0f || power < kPowerSkip) return false;
+    // the range test and the floor combined without an early return (the exponential is
+    // taken either way; the decisions are those of the two tests in turn)
+    const bool in_range = !(power > 0.0f) && !(power < kPowerSkip);
     ep = __expf(power);
     const float raw = __fmul_rn(s.b.w, ep);
     alpha = fminf(kAlphaCap, raw);
-    return alpha >= kAlphaFloor;
+    return in_range && alpha >= kAlphaFloor;
 }
 
 // Workspace layout (byte offsets, 256-aligned sections). Shared by the host API and the
