@@ -127,6 +127,32 @@ def test_background_and_zero_opacity(scene1):
         assert np.all(res["grads"][0][q] == 0)
 
 
+@pytest.mark.parametrize("algo", ["pairs", "warp_reduce", "warp_local"])
+def test_background_and_alpha_gradient(crop, algo):
+    """The general compositing adjoint, where Gaussians contribute: a grey background
+    (the T_final * background term of every colour channel) and a gradient on the alpha
+    image (the alpha suffix sums), against the oracle rendering with the same background;
+    for the warp-local backward also the alpha gradient alone on a black background. Both
+    under the default schedule and the capped persistent one."""
+    rng = np.random.default_rng(17)
+    cases = [(0.25, 0.5, 0.75)] + ([(0.0, 0.0, 0.0)] if algo == "warp_local" else [])
+    for bg in cases:
+        o = oracle.opts(bg=bg)
+        ref = oracle.render(crop, o)
+        _, g = l1_grads(crop, ref)
+        for x, v in zip(g, crop.views):
+            x["alpha"] = (rng.choice([-1.0, 1.0], size=(v.height, v.width)) / (v.width * v.height)).astype(np.float32)
+        og = oracle.backward(crop, [{k: v.astype(np.float64) for k, v in x.items()} for x in g], o)
+        for split in (dict(), dict(bwd_schedule="persistent", fwd_schedule="persistent", max_blocks=3)):
+            res = gpu_run(crop, grads_in=g, bg=bg, bwd_algorithm=algo, **split)
+            worst, n_near = compare_images(res, ref)
+            e = compare_grads(res, og)
+            print("bg %s %s %s: img %.2e near px %d grad ratio %.3f"
+                  % (bg, algo, "capped persistent" if split else "tiles", worst, n_near, e))
+            print(grad_stats_line("bg %s %s" % (bg, algo)))
+            assert e <= 1.0
+
+
 def test_fixed_keyframe_and_frozen_offset(crop):
     """Sec. 3.2: neighbour keyframes are fixed; Table 9 Mode3 freezes delta. A fixed
     keyframe renders identically and gets no gradient; freezing delta zeroes only
