@@ -480,6 +480,7 @@ __global__ void __launch_bounds__(kBucketThreads, 3)
         const uint32_t b = ((uint32_t)(key >> 32) - mn) >> shift;
         const int lo = (int)start[b], hi = b + 1 < (uint32_t)nbins ? (int)start[b + 1] : n;
         int r = lo;
+#pragma unroll 4
         for (int j = lo; j < hi; ++j) r += ks[j] < key ? 1 : 0;
         out[r] = key;
     }
