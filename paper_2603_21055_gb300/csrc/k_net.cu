@@ -181,7 +181,7 @@ __device__ __forceinline__ void conv_epilogue(const ConvArgs &a, size_t p, const
 //   warps 2-5          epilogue: wait for a full accumulator, read their 32 rows (warp
 //                      w reads lanes 32 (w % 4) ...), release the accumulator, store.
 // Every wait is bounded; a wait that gives up records a status and ends the block's loop.
-constexpr int kStages = 2;
+constexpr int kStages = 3;
 constexpr int kSlabUnits = 136;        // 16-byte units per staged (row, chunk) slab: 130 used, 128-byte aligned
 
 template <int CI, int CO>
