@@ -9,7 +9,7 @@ each image row spans a full 128-pixel tile and a ragged 22-pixel one (the weight
 gradient's 128-pixel K blocks the same); and two frames of 240 x 630 pixels (2,400 row
 tiles of 128 pixels, the last of each row ragged, and as many weight-gradient K blocks),
 several times the persistent grids, so that every block of the convolutions
-walks its two-stage TMA ring and flips its double TMEM accumulator many times and every
+walks its three-stage TMA ring and flips its double TMEM accumulator many times and every
 weight-gradient block cycles through its three load stages.
 """
 import numpy as np
