@@ -16,8 +16,8 @@ Protocol (readings of the workload; the paper has no learned part):
     Supp. A learning rates.
   * The plain initialisation is delta = 0 and opacity logit 0 (opacity 0.5).
   * Targets: delta and logit of every keyframe after 100 plain mapping iterations.
-  * The learned arm keeps the plain zero-offset initialisation as fallback and as judge of
-    the net's error: after inference it renders the window with the prediction, with zero
+  * The learned arm keeps the plain zero-offset initialisation as fallback and as the check
+    on the net's error: after inference it renders the window with the prediction, with zero
     offsets and the predicted opacities, and with the plain initialisation, and maps from
     the one with the lowest Eq. 1 loss.
   * Evaluation on held-out rooms: wall time (CUDA events) from the window's arrival on the
@@ -149,7 +149,7 @@ def plain_targets(fr, idx, iters: int = 100):
 
 
 def learned_init(mp, net, rgb_b, dep_b, off_b, lg_b, plain):
-    """Learned initialisation with the plain zero-offset one as fallback and judge: runs the
+    """Learned initialisation with the plain zero-offset one as fallback and check: runs the
     net on the window's RGB-D (rgb_b (n, 3, H, W), dep_b (n, H, W)) into off_b / lg_b, then
     renders the window with three initialisations, in this order of preference: the
     prediction; zero offsets with the predicted opacities; and the plain initialisation the

@@ -6,8 +6,8 @@ import numpy as np
 
 import oracle
 
-IMAGE_ATOL = 1e-4          # spec tolerance for rendered images
-GRAD_RTOL = 1e-3           # spec tolerance for gradients (relative)
+IMAGE_ATOL = 1e-4          # tolerance for rendered images (absolute)
+GRAD_RTOL = 1e-3           # tolerance for gradients (relative)
 
 
 def gpu_run(scene, grads_in=None, tile=(16, 16), sort_smem_cap=0, freeze_offset=False, bg=(0.0, 0.0, 0.0),

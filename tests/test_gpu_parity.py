@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
 seeded float32 inputs.
 
-Bars (the benchmark spec): sort keys, tile lists and contributor counts bit-exact; images within
+Bars: sort keys, tile lists and contributor counts bit-exact; images within
 1e-4 absolute; gradients within 1e-3 relative (floor 1e-6 x max|grad|). Items whose FP64
 decision lies within 1e-5 relative of its threshold may legitimately go either way in
 FP32; they are set aside and counted (see oracle/sgad_oracle.h).
